@@ -1,0 +1,177 @@
+"""Pins of the oracle's reduced-basis neural operator (Sec. 3.3-3.4), CPU only.
+
+* KL projection returns exactly the whitened normals of a synthesised field.
+* POD: M-orthonormal basis, reconstruction error = tail eigenvalue sum,
+  rank-one data gives one mode.
+* MLP: forward-mode control Jacobian against finite differences in z; the
+  analytic DINO-loss gradient against finite differences in the weights;
+  GELU derivatives against finite differences.
+* Reduced loss (Sec. 3.4): full-space loss minus reduced loss does not depend
+  on the network.
+* Reduced quadratic QoI (Sec. 3.3): decoded Q equals 1/2 ||phi + c||^2 + const.
+* Jacobian data (Sec. 3.4, implicit function theorem): Phi^T M J^-1 G against
+  finite differences of the projected state.
+* Adam against a hand-unrolled first step.
+"""
+import numpy as np
+import pytest
+
+from oracle import dino, field, pde, philox
+from synthetic_inputs import controls, glorot_uniform_mlp
+
+
+def test_kl_projection_returns_normals():
+    n, r_m = 12, 30
+    xi = philox.field_normals(9, 0, 3, n * n)
+    m = field.synthesize(xi.reshape(3, n, n), n, 0.1, 1.0, 0.0)
+    W, order = dino.kl_projection_matrix(n, r_m)
+    got = m.reshape(3, -1) @ W
+    np.testing.assert_allclose(got, xi[:, order[:r_m]], atol=1e-12)
+    lam = field.kl_eigenvalues(n, 0.1, 1.0).ravel()[order]
+    assert np.all(np.diff(lam) >= 0)
+    assert order[0] == 0 and set(order[1:3]) == {1, n}
+
+
+def test_pod_properties():
+    rng = np.random.default_rng(0)
+    d, Ns, h = 50, 30, 0.1
+    U = rng.standard_normal((Ns, 6)) @ rng.standard_normal((6, d)) + 0.01 * rng.standard_normal((Ns, d))
+    Phi, ubar, ev = dino.pod(U, 5, h)
+    np.testing.assert_allclose(h * h * Phi.T @ Phi, np.eye(5), atol=1e-10)
+    D = U - ubar
+    R = D - (h * h * (D @ Phi)) @ Phi.T
+    np.testing.assert_allclose(h * h * np.sum(R * R), np.sum(ev[5:]), rtol=1e-8)
+    v = rng.standard_normal(d)
+    U1 = np.outer(rng.standard_normal(Ns), v) + 3.0
+    Phi1, ubar1, ev1 = dino.pod(U1, 1, h)
+    assert ev1[1] < 1e-10 * ev1[0]
+    np.testing.assert_allclose(np.abs(Phi1[:, 0]), np.abs(v) / (h * np.linalg.norm(v)), rtol=1e-10)
+    assert Phi1[np.argmax(np.abs(Phi1[:, 0])), 0] > 0
+
+
+def test_gelu_derivatives():
+    x = np.linspace(-4, 4, 17)
+    d = 1e-6
+    np.testing.assert_allclose((dino.gelu(x + d) - dino.gelu(x - d)) / (2 * d), dino.gelu_d1(x), atol=1e-9)
+    np.testing.assert_allclose((dino.gelu_d1(x + d) - dino.gelu_d1(x - d)) / (2 * d), dino.gelu_d2(x), atol=1e-9)
+    np.testing.assert_allclose(dino.gelu(np.array([0.0, 1.0])), [0.0, 0.8413447460685429], rtol=1e-14)
+
+
+def _small_net(r_m=3, d_z=2, widths=(5, 6, 4), r_u=3, seed=1):
+    Ws, bs = glorot_uniform_mlp([r_m + d_z, *widths, r_u], seed=seed)
+    rng = np.random.default_rng(seed)
+    bs = [0.1 * rng.standard_normal(b.shape) for b in bs]
+    return dino.MLP(Ws, bs, r_m)
+
+
+def test_forward_jacobian_finite_difference():
+    net = _small_net()
+    rng = np.random.default_rng(3)
+    xi, z = rng.standard_normal((4, 3)), rng.uniform(-1, 1, (4, 2))
+    J = net.forward(xi, z)["J"]
+    step = 1e-6
+    for j in range(2):
+        e = np.zeros(2)
+        e[j] = step
+        fd = (net.forward(xi, z + e, jacobian=False)["phi"] - net.forward(xi, z - e, jacobian=False)["phi"]) / (2 * step)
+        np.testing.assert_allclose(J[:, :, j], fd, rtol=1e-7, atol=1e-9)
+
+
+@pytest.mark.parametrize("w_j", [1.0, 0.0])
+def test_loss_gradient_finite_difference(w_j):
+    net = _small_net()
+    rng = np.random.default_rng(5)
+    B = 4
+    xi, z = rng.standard_normal((B, 3)), rng.uniform(-1, 1, (B, 2))
+    y, Y = rng.standard_normal((B, 3)), rng.standard_normal((B, 3, 2))
+    loss, dW, db = net.loss_and_grad(xi, z, y, Y, w_j=w_j)
+    step = 1e-6
+    for l in range(len(net.Ws)):
+        for (i, j) in [(0, 0), (1, net.Ws[l].shape[1] - 1), (net.Ws[l].shape[0] - 1, 1)]:
+            a, b = net.copy(), net.copy()
+            a.Ws[l][i, j] += step
+            b.Ws[l][i, j] -= step
+            fd = (a.loss_and_grad(xi, z, y, Y, w_j)[0] - b.loss_and_grad(xi, z, y, Y, w_j)[0]) / (2 * step)
+            np.testing.assert_allclose(dW[l][i, j], fd, rtol=1e-7, atol=1e-9)
+        a, b = net.copy(), net.copy()
+        a.bs[l][0] += step
+        b.bs[l][0] -= step
+        fd = (a.loss_and_grad(xi, z, y, Y, w_j)[0] - b.loss_and_grad(xi, z, y, Y, w_j)[0]) / (2 * step)
+        np.testing.assert_allclose(db[l][0], fd, rtol=1e-7, atol=1e-9)
+
+
+def test_reduced_loss_equivalence_and_reduced_qoi():
+    rng = np.random.default_rng(8)
+    d, Ns, r_u, h, d_z = 40, 25, 3, 0.2, 2
+    U = rng.standard_normal((Ns, 5)) @ rng.standard_normal((5, d))
+    Phi, ubar, _ = dino.pod(U, r_u, h)
+    B = 3
+    u = U[:B]
+    du = rng.standard_normal((B, d, d_z))
+    xi = rng.standard_normal((B, 3))
+    z = rng.uniform(-1, 1, (B, d_z))
+    y = h * h * (u - ubar) @ Phi
+    Y = h * h * np.einsum("dr,bdj->brj", Phi, du)
+    gaps = []
+    for seed in (1, 2):
+        net = _small_net(r_u=r_u, seed=seed)
+        st = net.forward(xi, z)
+        uw = st["phi"] @ Phi.T + ubar
+        duw = np.einsum("dr,brj->bdj", Phi, st["J"])
+        full = (h * h * np.sum((uw - u) ** 2) + h * h * np.sum((duw - du) ** 2)) / B
+        red = net.loss_and_grad(xi, z, y, Y)[0]
+        gaps.append(full - red)
+    np.testing.assert_allclose(gaps[0], gaps[1], rtol=1e-10)
+    # reduced QoI equals the decoded one
+    ut = rng.standard_normal(d)
+    net = _small_net(r_u=r_u, seed=4)
+    Q1, g1, _, _ = dino.eval_surrogate(net, xi, z, Phi, ubar, ut, h, decode=True)
+    Q2, g2, _, _ = dino.eval_surrogate(net, xi, z, Phi, ubar, ut, h, decode=False)
+    np.testing.assert_allclose(Q1, Q2, rtol=1e-10)
+    np.testing.assert_allclose(g1, g2, rtol=1e-10)
+    # and the surrogate gradient is the z-derivative of its Q
+    step = 1e-6
+    for j in range(d_z):
+        e = np.zeros(d_z)
+        e[j] = step
+        qp = dino.eval_surrogate(net, xi, z + e, Phi, ubar, ut, h)[0]
+        qm = dino.eval_surrogate(net, xi, z - e, Phi, ubar, ut, h)[0]
+        np.testing.assert_allclose(g1[:, j], (qp - qm) / (2 * step), rtol=1e-6, atol=1e-10)
+
+
+def test_jacobian_data_finite_difference():
+    n = 17
+    prob = pde.Problem(n=n, L=3)
+    G = field.control_sources(n, prob.L, prob.width)
+    m = field.sample_fields(3, 0, 1, n)[0]
+    z = controls(4, 1, prob.d_z)[0]
+    kx, ky = pde.face_coefficients(m)
+    f = (G @ z).reshape(n, n)
+    u, chol = pde.newton_solve(kx, ky, f, prob.r, prob.h)
+    dudz = pde.state_jacobian_columns(chol, pde.interior_rows(G, n), n)
+    step = 1e-5
+    for k in (0, 4, 8):
+        zp, zm = z.copy(), z.copy()
+        zp[k] += step
+        zm[k] -= step
+        up = pde.newton_solve(kx, ky, (G @ zp).reshape(n, n), prob.r, prob.h)[0]
+        um = pde.newton_solve(kx, ky, (G @ zm).reshape(n, n), prob.r, prob.h)[0]
+        fd = ((up - um) / (2 * step))[1:-1, 1:-1].ravel()
+        np.testing.assert_allclose(dudz[:, k], fd, rtol=1e-6, atol=1e-9 * np.abs(fd).max())
+
+
+def test_adam_first_step():
+    p = [np.array([1.0, -2.0])]
+    g = [np.array([0.5, -0.1])]
+    opt = dino.Adam(p)
+    out = opt.step(p, g, 1e-3)
+    # first step: m_hat = g, v_hat = g^2 -> p - lr * g / (|g| + eps)
+    np.testing.assert_allclose(out[0], p[0] - 1e-3 * g[0] / (np.abs(g[0]) + 1e-8), rtol=1e-14)
+    assert dino.lr_schedule(99, 200) == 1e-3 and dino.lr_schedule(100, 200) == 2.5e-4
+
+
+def test_bf16_rounding():
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -3.14159])
+    r = dino.round_bf16(x)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -7
+    assert abs(r[3] + 3.14159) < 2 ** -7 * 4
