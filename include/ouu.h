@@ -1,0 +1,163 @@
+/* ouu.h -- C ABI of the GB300 (sm_103a) SAA risk + gradient library for
+ * PDE-constrained optimisation under uncertainty (arXiv 2305.20053, Luo,
+ * O'Leary-Roseberry, Chen, Ghattas).
+ *
+ * Problem (Sec. 2, Eq. for min_z rho(Q)(z) + P(z)): the state u(m, z) solves the
+ * semilinear elliptic equation of Sec. 4.2,
+ *      -div(e^m grad u) + r u^3 = sum_j z_j f_j   on (0,1)^2,  u = 0 on the boundary,
+ * with m a Matern Gaussian random field (Sec. 2, C = (-gamma Lap + delta I)^-2),
+ * f_j Gaussian sources on an L x L lattice (Sec. 4.2), and the tracking QoI
+ * Q(u) = 1/2 ||u - sin(pi x) sin(pi y)||^2_{L2} (Sec. 4.2, with a factor 1/2).
+ * The risk of Q over N fixed samples of m is the sample average approximation of
+ * Sec. 2.2 (mean + kappa * variance, or the smoothed CVaR of Sec. 2.1 in its
+ * Rockafellar-Uryasev form), and its gradient in z is the chain rule of Sec. 2.3
+ * with one adjoint solve per sample (plain backend) or automatic differentiation
+ * through the reduced-basis neural operator of Sec. 3.3 (MR-DINO backend).
+ *
+ * Discretisation: n x n vertex grid, h = 1/(n-1), n = 2^k + 1 (5 <= n <= 1025);
+ * grid arrays are row-major [iy * n + ix] over all n*n nodes (x fastest);
+ * controls are indexed j = jy * L + jx (x fastest).
+ *
+ * Conventions for every call:
+ *  - Pointers named *_dev are device pointers allocated by the caller, who owns
+ *    them; they must stay valid until the work queued on the problem's stream has
+ *    completed.  Pointers named *_host / *_out are host memory.
+ *  - All device work is ordered on the CUDA stream given at creation.  Calls that
+ *    return host results synchronise that stream before returning.
+ *  - The library allocates its workspaces at creation (ouu_create_problem,
+ *    ouu_dino_create); the per-call paths allocate nothing.
+ *  - Every call returns an ouu_status; on failure, ouu_last_error() gives a
+ *    message for the calling thread.  Calls on one handle are not re-entrant;
+ *    distinct handles may be used concurrently on distinct streams.
+ */
+#ifndef OUU_H
+#define OUU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OUU_OK = 0,
+  OUU_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported grid */
+  OUU_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  OUU_ERR_OOM = 3,           /* workspace allocation at creation failed */
+  OUU_ERR_NOT_CONVERGED = 4, /* some sample hit newton_maxit (per-sample status set) */
+  OUU_ERR_NONFINITE = 5,     /* NaN/Inf met in a residual or input */
+  OUU_ERR_STATE = 6          /* handle not ready for this call (e.g. DINO bases not built) */
+} ouu_status;
+
+typedef enum { OUU_RISK_MEAN_VAR = 0, OUU_RISK_CVAR_SMOOTH = 1 } ouu_risk_kind;
+typedef enum { OUU_BACKEND_PDE = 0, OUU_BACKEND_DINO = 1 } ouu_backend;
+
+/* Per-sample status words written by the solve calls. */
+enum { OUU_SAMPLE_OK = 0, OUU_SAMPLE_NOT_CONVERGED = 1, OUU_SAMPLE_NONFINITE = 2 };
+
+typedef struct {
+  int n;               /* nodes per side, 2^k + 1 */
+  double reaction_r;   /* r in the state equation (Sec. 4.2) */
+  double gamma, delta; /* prior operator -gamma Lap + delta I (Sec. 2) */
+  double m_mean;       /* constant prior mean mbar */
+  int lattice_L;       /* L x L sources, d_Z = L^2 */
+  double bump_width;   /* source width sigma (Sec. 4.2) */
+  double newton_rtol;  /* stop when ||R||_2 <= rtol ||f||_2, then one more step */
+  int newton_maxit;
+  double cg_rtol;      /* relative residual of each inner MG-PCG solve (FP32) */
+  int cg_maxit;
+  int max_samples;     /* capacity: largest n_samples of any later call */
+} ouu_problem_desc;
+
+typedef struct {
+  ouu_risk_kind kind;
+  double kappa;        /* mean + kappa * variance */
+  double beta, eps;    /* smoothed CVaR level and smoothing width (Sec. 2.1) */
+  double t;            /* CVaR auxiliary variable when t_optimal == 0 */
+  int t_optimal;       /* 1: t = argmin_t rho(z, t) (bisection on d rho / dt) */
+} ouu_risk_desc;
+
+typedef struct {
+  int newton_min, newton_max;   /* Newton steps over samples (state solve) */
+  double newton_mean;
+  int cg_total;                 /* inner CG iterations summed over samples and solves */
+  int adjoint_solves;           /* adjoint solves performed (samples with nonzero weight) */
+  int n_not_converged;
+  float ms_state;               /* device time of the batched state solve (CUDA events on the stream) */
+  float ms_weights;             /* risk weights / t* */
+  float ms_adjoint;             /* batched adjoint solve */
+  float ms_reduce;              /* weighted adjoint sum and G^T */
+  float ms_total;               /* whole evaluation on the device */
+} ouu_eval_stats;
+
+typedef struct ouu_problem* ouu_problem_t;
+typedef struct ouu_dino* ouu_dino_t;
+
+/* Fills *desc with the defaults of the 129 x 129 workload: r = 1, gamma = 0.1,
+ * delta = 1, mbar = 0, L = 10, sigma = 0.05, newton_rtol = 1e-10, newton_maxit = 30,
+ * cg_rtol = 1e-6, cg_maxit = 200, max_samples = 4096. */
+void ouu_default_problem_desc(ouu_problem_desc* desc);
+
+/* Creates a problem handle bound to `cuda_stream` (a cudaStream_t, or NULL for the
+ * legacy default stream) on the current device and allocates its workspace for
+ * up to desc->max_samples samples.  Errors: INVALID_ARG (grid not 2^k+1, L < 1,
+ * widths <= 0), OOM, CUDA. */
+ouu_status ouu_create_problem(const ouu_problem_desc* desc, void* cuda_stream, ouu_problem_t* out);
+ouu_status ouu_destroy_problem(ouu_problem_t p);
+
+/* Draws the Gaussian random fields of samples first_index .. first_index+n_samples-1
+ * (Sec. 2: m ~ N(mbar, (-gamma Lap + delta I)^-2), homogeneous Neumann) by their
+ * Karhunen-Loeve expansion (Sec. 3.3) in the DCT-II eigenbasis of the discrete
+ * Neumann Laplacian: m = mbar + n sum_{k1,k2} lambda^-1 xi v_k1(ix) v_k2(iy),
+ * lambda = delta + gamma (mu_k1 + mu_k2), mu_k = 4 n^2 sin^2(pi k / 2n).
+ * The standard normals xi come from Philox4x32-10 (key = seed, counter =
+ * (mode pair, sample index, tag)) and Box-Muller, so any subset of samples is
+ * reproducible.  Output m_dev: [n_samples][n][n] float64, device.  FP64. */
+ouu_status ouu_sample_fields(ouu_problem_t p, uint64_t seed, int64_t first_index, int n_samples,
+                             double* m_dev);
+
+/* Solves the state equation (Sec. 4.2) for each sample by Newton's method with an
+ * FP64 residual and geometric-multigrid-preconditioned CG (FP32) for each Newton
+ * step, and evaluates the QoI.  m_dev: [n_samples][n][n] fields; z_dev: controls,
+ * sample i uses z_dev + i * z_stride (z_stride = 0: one shared control of d_Z
+ * entries).  Outputs (device): u_dev [n_samples][n][n] (boundary zero), q_dev
+ * [n_samples], status_dev [n_samples] (OUU_SAMPLE_*).  u_dev may be NULL when the
+ * states are not needed.  Returns NOT_CONVERGED / NONFINITE if any sample failed. */
+ouu_status ouu_pde_solve_batch(ouu_problem_t p, const double* m_dev, int n_samples, const double* z_dev,
+                               int64_t z_stride, double* u_dev, double* q_dev, int32_t* status_dev);
+
+/* Adjoint solves (Sec. 2.3): J(u_i) lambda_i = dQ/du(u_i) = h^2 (u_i - u_t) with
+ * J = A_h(m_i) + 3 r diag(u_i^2) (symmetric), by FP32 MG-PCG inside FP64
+ * iterative refinement to a relative residual of 1e-12, and the per-sample
+ * gradient grad_z Q_i = G^T lambda_i (G: the source matrix, since dR/dz = -G).
+ * Inputs: m_dev, u_dev (states from ouu_pde_solve_batch).  Outputs (device, each
+ * may be NULL): lambda_dev [n_samples][n][n], gradq_dev [n_samples][d_Z]. */
+ouu_status ouu_adjoint_batch(ouu_problem_t p, const double* m_dev, const double* u_dev, int n_samples,
+                             double* lambda_dev, double* gradq_dev);
+
+/* Risk measure and its gradient over the sample average of Sec. 2.2 at the
+ * control z_host[d_Z] for the n_samples fields in m_dev, for n_risks risk measures
+ * at once (1 <= n_risks <= 4).  Backend PDE: one batched state solve, the risk
+ * weights, then one adjoint solve per sample whose weight is nonzero in some
+ * risk, accumulating sum_i w_i lambda_i and applying G^T once.  Backend DINO:
+ * the MR-DINO surrogate (`dino` must be non-NULL and trained), see
+ * ouu_dino_eval.  Outputs (host): risk_out[n_risks], grad_z_out[n_risks][d_Z],
+ * grad_t_out[n_risks] (d rho / dt for CVaR, 0 for mean+var), t_out[n_risks]
+ * (t used; may be NULL), stats (may be NULL).  Synchronises the stream. */
+ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ouu_dino_t dino, const double* m_dev,
+                             int n_samples, const ouu_risk_desc* risks, int n_risks, const double* z_host,
+                             double* risk_out, double* grad_z_out, double* grad_t_out, double* t_out,
+                             ouu_eval_stats* stats);
+
+/* Thread-local message of the last failed call ("" if none).  Copies at most
+ * len-1 bytes plus a terminating zero into buf; returns the full length. */
+size_t ouu_last_error(char* buf, size_t len);
+
+/* Number of samples one persistent launch keeps in flight (one per CTA). */
+int ouu_problem_slots(ouu_problem_t p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OUU_H */

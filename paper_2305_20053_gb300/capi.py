@@ -1,0 +1,190 @@
+"""Thin ctypes binding of libouu.so (the C ABI declared in include/ouu.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (their data pointers are passed
+through); host results come back as numpy arrays.  If the library has not been
+built, loading raises immediately: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libouu.so")
+
+OUU_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE", 6: "STATE"}
+RISK_MEAN_VAR = 0
+RISK_CVAR_SMOOTH = 1
+BACKEND_PDE = 0
+BACKEND_DINO = 1
+
+
+class OuuError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("reaction_r", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("delta", ctypes.c_double), ("m_mean", ctypes.c_double), ("lattice_L", ctypes.c_int),
+                ("bump_width", ctypes.c_double), ("newton_rtol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
+                ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int), ("max_samples", ctypes.c_int)]
+
+
+class RiskDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("kappa", ctypes.c_double), ("beta", ctypes.c_double),
+                ("eps", ctypes.c_double), ("t", ctypes.c_double), ("t_optimal", ctypes.c_int)]
+
+
+class EvalStats(ctypes.Structure):
+    _fields_ = [("newton_min", ctypes.c_int), ("newton_max", ctypes.c_int), ("newton_mean", ctypes.c_double),
+                ("cg_total", ctypes.c_int), ("adjoint_solves", ctypes.c_int), ("n_not_converged", ctypes.c_int),
+                ("ms_state", ctypes.c_float), ("ms_weights", ctypes.c_float), ("ms_adjoint", ctypes.c_float),
+                ("ms_reduce", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_dp = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); mirrors include/ouu.h
+SIGNATURES = {
+    "ouu_default_problem_desc": (None, [ctypes.POINTER(ProblemDesc)]),
+    "ouu_create_problem": (_i, [ctypes.POINTER(ProblemDesc), _vp, ctypes.POINTER(_vp)]),
+    "ouu_destroy_problem": (_i, [_vp]),
+    "ouu_sample_fields": (_i, [_vp, _u64, _i64, _i, _vp]),
+    "ouu_pde_solve_batch": (_i, [_vp, _vp, _i, _vp, _i64, _vp, _vp, _vp]),
+    "ouu_adjoint_batch": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
+    "ouu_risk_and_grad": (_i, [_vp, _i, _vp, _vp, _i, ctypes.POINTER(RiskDesc), _i, _dp, _dp, _dp, _dp, _dp,
+                               ctypes.POINTER(EvalStats)]),
+    "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
+    "ouu_problem_slots": (_i, [_vp]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libouu.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} not found: build it with __graft_entry__.build() "
+                          "or `python -m paper_2305_20053_gb300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    load().ouu_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def check(status):
+    if status != OUU_OK:
+        raise OuuError(status, last_error())
+
+
+def dev_ptr(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def problem_desc(**kw) -> ProblemDesc:
+    d = ProblemDesc()
+    load().ouu_default_problem_desc(ctypes.byref(d))
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def risk_desc(kind, kappa=1.0, beta=0.95, eps=1e-4, t=0.0, t_optimal=1) -> RiskDesc:
+    return RiskDesc(kind, kappa, beta, eps, t, t_optimal)
+
+
+class Problem:
+    """Owns an ouu_problem_t.  Methods are one-to-one with the C calls."""
+
+    def __init__(self, stream=None, **desc):
+        import torch
+        self.desc = problem_desc(**desc)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(load().ouu_create_problem(ctypes.byref(self.desc), _stream_handle(self.stream), ctypes.byref(h)))
+        self.handle = h
+        self.n = self.desc.n
+        self.d_z = self.desc.lattice_L ** 2
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ouu_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def slots(self) -> int:
+        return load().ouu_problem_slots(self.handle)
+
+    def ouu_sample_fields(self, seed, first_index, n_samples, m_dev):
+        import torch
+        check(load().ouu_sample_fields(self.handle, seed, first_index, n_samples, dev_ptr(m_dev, torch.float64)))
+
+    def ouu_pde_solve_batch(self, m_dev, n_samples, z_dev, z_stride, u_dev, q_dev, status_dev):
+        import torch
+        check(load().ouu_pde_solve_batch(self.handle, dev_ptr(m_dev, torch.float64), n_samples,
+                                         dev_ptr(z_dev, torch.float64), z_stride, dev_ptr(u_dev, torch.float64),
+                                         dev_ptr(q_dev, torch.float64), dev_ptr(status_dev, torch.int32)))
+
+    def ouu_adjoint_batch(self, m_dev, u_dev, n_samples, lambda_dev, gradq_dev):
+        import torch
+        check(load().ouu_adjoint_batch(self.handle, dev_ptr(m_dev, torch.float64), dev_ptr(u_dev, torch.float64),
+                                       n_samples, dev_ptr(lambda_dev, torch.float64),
+                                       dev_ptr(gradq_dev, torch.float64)))
+
+    def ouu_risk_and_grad(self, backend, dino, m_dev, n_samples, risks, z_host):
+        """Returns (risk[n_risks], grad_z[n_risks, d_Z], grad_t[n_risks], t[n_risks], stats)."""
+        import torch
+        nr = len(risks)
+        arr = (RiskDesc * nr)(*risks)
+        z = np.ascontiguousarray(z_host, dtype=np.float64)
+        risk = np.zeros(nr)
+        grad = np.zeros((nr, self.d_z))
+        gt = np.zeros(nr)
+        t = np.zeros(nr)
+        st = EvalStats()
+        P = lambda a: a.ctypes.data_as(_dp)
+        check(load().ouu_risk_and_grad(self.handle, backend, dino.handle if dino is not None else None,
+                                       dev_ptr(m_dev, torch.float64), n_samples, arr, nr, P(z), P(risk), P(grad),
+                                       P(gt), P(t), ctypes.byref(st)))
+        return risk, grad, gt, t, st

@@ -1,0 +1,170 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "ouu.h"
+#include "pde_core.cuh"
+
+// ------------------------------------------------------------------ errors
+void ouu_set_error(const std::string& msg);
+
+#define OUU_CUDA_TRY(expr)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      ouu_set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));               \
+      return OUU_ERR_CUDA;                                                              \
+    }                                                                                   \
+  } while (0)
+
+#define OUU_CHECK_ARG(cond, msg)                                                        \
+  do {                                                                                  \
+    if (!(cond)) {                                                                      \
+      ouu_set_error(msg);                                                               \
+      return OUU_ERR_INVALID_ARG;                                                       \
+    }                                                                                   \
+  } while (0)
+
+// ------------------------------------------------------------------ CTA context
+// One CTA cooperates on one sample: warps own grid rows, lanes own columns.
+struct CtaCtx {
+  double* red;   // shared scratch of >= 33 doubles
+  __device__ __forceinline__ int row0() const { return threadIdx.x >> 5; }
+  __device__ __forceinline__ int rowstep() const { return blockDim.x >> 5; }
+  __device__ __forceinline__ int col0() const { return threadIdx.x & 31; }
+  __device__ __forceinline__ int colstep() const { return 32; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ double sum_d(double v) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      double s = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+  }
+  // FP32 partial sums per thread and per warp, FP64 across warps.
+  __device__ double sum_f(float v) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = (double)v;
+    __syncthreads();
+    if (w == 0) {
+      double s = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+  }
+};
+
+// ------------------------------------------------------------------ solver launch data
+#define OUU_SMEM_MAX_N 65      // multigrid levels with n_l <= this live in shared memory
+#define OUU_SOLVER_THREADS 1024
+#define OUU_MAX_RISKS 4
+
+// Bytes of one array of a multigrid level (n x n floats, padded to 16 bytes).
+__host__ __device__ inline int64_t ouu_level_array_bytes(int n) {
+  return (((int64_t)n * n * 4 + 15) / 16) * 16;
+}
+
+struct SlotLayout {
+  int64_t bytes;                         // bytes per slot
+  int64_t E, f, tmp, lam, acc;           // FP64 arrays (offsets in bytes)
+  int64_t kx, ky, D, x, r, z, p, q, t;   // level-0 FP32 arrays
+  int64_t lev[OUU_MAX_LEVELS];           // global coarse level blocks (6 arrays), -1 if in smem
+  int64_t smem_lev[OUU_MAX_LEVELS];      // shared-memory offsets of smem levels, -1 if global
+  int64_t smem_bytes;
+};
+
+struct PdeArgs {
+  int n, nlev, L, n_samples;
+  double rr, gscale, newton_rtol, cg_rtol, refine_rtol;
+  int newton_maxit, cg_maxit, refine_maxit;
+  const double* m;            // [N][n*n]
+  const double* z;            // z for sample i at z + i * z_stride
+  int64_t z_stride;
+  const double* gx;           // [L][n]
+  const double* gy;           // [L][n]
+  const double* ut;           // [n*n]
+  double* u;                  // [N][n*n]: output of the state kernel, input of the adjoint kernel
+  double* q;                  // [N]
+  int32_t* status;            // [N]
+  int32_t* iters;             // [N][3]: newton steps, cg iterations, refinement steps
+  int* solved;                // adjoint kernel: count of samples solved (may be null)
+  // adjoint kernel
+  const double* w;            // [n_w][N] risk weights (null: per-sample outputs only)
+  int n_w;
+  double* lam_out;            // [N][n*n] or null
+  double* grad_out;           // [N][L*L] or null
+  char* slots;
+  SlotLayout lay;
+  int* counter;
+};
+
+void launch_pde_state(const PdeArgs& a, int nslots, cudaStream_t s);
+void launch_pde_adjoint(const PdeArgs& a, int nslots, cudaStream_t s);
+
+// Sum the per-slot FP64 accumulators [slot][n_w][n*n] into s_out [n_w][n*n], then
+// grad[r][j] = scale * sum_{iy,ix} gy[jy][iy] gx[jx][ix] s[r][iy*n+ix].
+void launch_reduce_slots_and_gradient(const char* slots, const SlotLayout& lay, int nslots, int n, int L,
+                                      int n_w, const double* gx, const double* gy, double gscale,
+                                      double* s_out, double* grad, cudaStream_t st);
+
+// ------------------------------------------------------------------ risk weights
+struct RiskDev {
+  int kind;
+  double kappa, beta, eps, t;
+  int t_optimal;
+};
+
+// One CTA: per-risk weights w[r][i], value[r], dt[r], t[r] from q[N].
+// out layout: value[r], dt[r], t[r] at out[3r+0..2].
+void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w,
+                         double* out, cudaStream_t s);
+
+// ------------------------------------------------------------------ fields
+void launch_sample_fields(int n, uint64_t seed, int64_t first, int count, const double* invlam,
+                          const double* V, double m_mean, double* m, cudaStream_t s);
+
+// ------------------------------------------------------------------ handle
+struct ouu_problem {
+  ouu_problem_desc desc;
+  cudaStream_t stream;
+  int device, num_sms, n, nlev, L, dz, nslots;
+  double h, gscale;
+  double* d_gx = nullptr;     // [L][n]
+  double* d_gy = nullptr;     // [L][n]
+  double* d_ut = nullptr;     // [n*n]
+  double* d_V = nullptr;      // DCT-II [n][n]
+  double* d_invlam = nullptr; // [n*n] 1/lambda
+  char* d_slots = nullptr;
+  SlotLayout lay;
+  int* d_counter = nullptr;
+  // per-call buffers (capacity max_samples)
+  double* d_u = nullptr;
+  double* d_q = nullptr;
+  int32_t* d_status = nullptr;
+  int32_t* d_iters = nullptr;
+  double* d_w = nullptr;      // [OUU_MAX_RISKS][max_samples]
+  double* d_s = nullptr;      // [OUU_MAX_RISKS][n*n]
+  double* d_out = nullptr;    // results: [OUU_MAX_RISKS][3] + grads [OUU_MAX_RISKS][dz] + misc
+  RiskDev* d_risks = nullptr;
+  double* d_z = nullptr;      // [dz] shared control of the current evaluation
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // evaluation phase timers
+  double* h_out = nullptr;    // pinned mirror of d_out
+  int32_t* h_stat = nullptr;  // pinned: per-sample status/iters copy (max_samples * 4)
+};
+
+int ouu_num_levels(int n);
