@@ -203,6 +203,7 @@ __device__ double op_apply_dot(const C& c, const MgLevel& L, const float* p, flo
 struct CgResult {
   int iters;
   double rel;       // final ||r|| / ||b||
+  double scale;     // the solution of J x = b is scale * x (b is normalised to unit norm)
 };
 
 // Solves J x = b for x (x overwritten) with the V-cycle as preconditioner.  On entry
@@ -216,13 +217,22 @@ __device__ CgResult pcg_solve(const C& c, Hierarchy& H, float* x, float* p, floa
   const int n = L.n;
   float* r = L.b;
   float* z = L.x;
-  CgResult res{0, 1.0};
-  if (!(bnorm > 0.0)) {
-    OUU_FOR_INTERIOR(c, n, iy, ix) x[iy * n + ix] = 0.f;
-    c.sync();
-    res.rel = 0.0;
+  CgResult res{0, 1.0, 0.0};
+  // Normalise b to unit norm (keeps FP32 dot products far from underflow when b is
+  // a late refinement residual) and start from x = 0.
+  const float inv = bnorm > 0.0 ? (float)(1.0 / bnorm) : 0.f;
+  OUU_FOR_INTERIOR(c, n, iy, ix) {
+    const int k = iy * n + ix;
+    r[k] *= inv;
+    x[k] = 0.f;
+  }
+  c.sync();
+  if (!(bnorm > 0.0) || !(bnorm < INFINITY)) {
+    res.rel = bnorm > 0.0 ? 1.0 : 0.0;
     return res;
   }
+  res.scale = bnorm;
+  bnorm = 1.0;
   mg_vcycle(c, H);
   float acc = 0.f;
   OUU_FOR_INTERIOR(c, n, iy, ix) {
@@ -233,12 +243,13 @@ __device__ CgResult pcg_solve(const C& c, Hierarchy& H, float* x, float* p, floa
   double rz = c.sum_f(acc);
   for (int it = 1; it <= maxit; ++it) {
     const double pq = op_apply_dot(c, L, p, q);
+    if (!(pq > 0.0)) break;   // breakdown (exact solution reached, or not SPD): keep x
     const double alpha = rz / pq;
     const float af = (float)alpha;
     float rr = 0.f;
     OUU_FOR_INTERIOR(c, n, iy, ix) {
       const int k = iy * n + ix;
-      x[k] = (it == 1 ? 0.f : x[k]) + af * p[k];
+      x[k] += af * p[k];
       const float rv = r[k] - af * q[k];
       r[k] = rv;
       rr += rv * rv;
@@ -401,6 +412,10 @@ __device__ NewtonResult newton_solve(const C& c, Hierarchy& H, double rr, const 
   double rn = sqrt(newton_residual(c, n, ih2, rr, E, f, u, L0.b));
   const double fnorm = rn;   // u = 0: R = -f
   c.sync();
+  if (!(rn == rn) || isinf(rn)) {   // non-finite coefficients or forcing
+    res.status = 2;
+    return res;
+  }
   if (!(fnorm > 0.0)) return res;
   bool extra = false;
   for (int it = 0;; ++it) {
@@ -415,7 +430,7 @@ __device__ NewtonResult newton_solve(const C& c, Hierarchy& H, double rr, const 
     setup_jacobian(c, H, rr, u);
     CgResult cg = pcg_solve(c, H, x, p, q, rn, cg_rtol, cg_maxit);
     res.cg_iters += cg.iters;
-    double step = 1.0;
+    double step = cg.scale;
     axpy_interior(c, n, step, x, u);
     c.sync();
     double rn_new = sqrt(newton_residual(c, n, ih2, rr, E, f, u, L0.b));
@@ -449,6 +464,10 @@ __device__ NewtonResult refine_solve(const C& c, Hierarchy& H, double rr, const 
   double rn = sqrt(linear_residual(c, n, ih2, rr, E, u, b, lam, L0.b));
   c.sync();
   const double bnorm = rn;
+  if (!(rn == rn) || isinf(rn)) {
+    res.status = 2;
+    return res;
+  }
   if (!(bnorm > 0.0)) return res;
   for (int it = 0;; ++it) {
     if (!(rn == rn) || isinf(rn)) { res.status = 2; break; }
@@ -456,7 +475,7 @@ __device__ NewtonResult refine_solve(const C& c, Hierarchy& H, double rr, const 
     if (it >= maxit) { res.status = 1; break; }
     CgResult cg = pcg_solve(c, H, x, p, q, rn, cg_rtol, cg_maxit);
     res.cg_iters += cg.iters;
-    axpy_interior(c, n, 1.0, x, lam);
+    axpy_interior(c, n, cg.scale, x, lam);
     c.sync();
     rn = sqrt(linear_residual(c, n, ih2, rr, E, u, b, lam, L0.b));
     c.sync();
