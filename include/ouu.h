@@ -150,6 +150,31 @@ ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ouu_dino_t di
                              double* risk_out, double* grad_z_out, double* grad_t_out, double* t_out,
                              ouu_eval_stats* stats);
 
+/* Allocation-free variant of ouu_pde_solve_batch.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory when
+ * they call in -- code under a device-memory budget or pool that forbids new
+ * cudaMalloc calls, or a plug-in handed a stream and buffers by a host
+ * application that owns every device allocation -- and that therefore cannot
+ * create a problem handle (ouu_create_problem allocates its workspace).
+ * It runs the same per-sample Newton / MG-PCG state solve and QoI as
+ * ouu_pde_solve_batch, with the same results, for the problem described by
+ * *desc (desc->max_samples is ignored); m_dev, z_dev, z_stride, u_dev, q_dev and
+ * status_dev mean what they mean there, and all five pointers are required.
+ * All scratch (tables, per-CTA solver slots, the work counter) lives in one
+ * file-scope device array of 8 MiB that every GPU which loads the library holds
+ * until the process exits; grids that do not fit one solver slot in it
+ * (n > 257) are rejected with OUU_ERR_INVALID_ARG.  The call makes no cudaMalloc,
+ * cudaFree or other allocating call.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  The array keeps the last call's
+ * contents; each call clears what must start at zero.  All calls share the one
+ * array, so calls whose GPU work overlaps (other streams, other threads) race:
+ * serialise them.  Synchronises `cuda_stream` (a cudaStream_t or NULL) before
+ * returning, like ouu_pde_solve_batch. */
+ouu_status ouu_pde_solve_batch_noalloc(const ouu_problem_desc* desc, const double* m_dev, int n_samples,
+                                       const double* z_dev, int64_t z_stride, double* u_dev, double* q_dev,
+                                       int32_t* status_dev, void* cuda_stream);
+
 /* Thread-local message of the last failed call ("" if none).  Copies at most
  * len-1 bytes plus a terminating zero into buf; returns the full length. */
 size_t ouu_last_error(char* buf, size_t len);

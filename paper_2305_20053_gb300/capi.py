@@ -64,6 +64,7 @@ SIGNATURES = {
     "ouu_adjoint_batch": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
     "ouu_risk_and_grad": (_i, [_vp, _i, _vp, _vp, _i, ctypes.POINTER(RiskDesc), _i, _dp, _dp, _dp, _dp, _dp,
                                ctypes.POINTER(EvalStats)]),
+    "ouu_pde_solve_batch_noalloc": (_i, [ctypes.POINTER(ProblemDesc), _vp, _i, _vp, _i64, _vp, _vp, _vp, _vp]),
     "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "ouu_problem_slots": (_i, [_vp]),
 }
@@ -188,3 +189,13 @@ class Problem:
                                        dev_ptr(m_dev, torch.float64), n_samples, arr, nr, P(z), P(risk), P(grad),
                                        P(gt), P(t), ctypes.byref(st)))
         return risk, grad, gt, t, st
+
+
+def ouu_pde_solve_batch_noalloc(desc, m_dev, n_samples, z_dev, z_stride, u_dev, q_dev, status_dev, stream=None):
+    """Allocation-free batched state solve (no problem handle; fixed device scratch)."""
+    import torch
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    check(load().ouu_pde_solve_batch_noalloc(ctypes.byref(desc), dev_ptr(m_dev, torch.float64), n_samples,
+                                             dev_ptr(z_dev, torch.float64), z_stride, dev_ptr(u_dev, torch.float64),
+                                             dev_ptr(q_dev, torch.float64), dev_ptr(status_dev, torch.int32),
+                                             _stream_handle(stream)))
