@@ -1,0 +1,35 @@
+/* ouu_kernels.h -- kernel-level entry points of libouu.so used by the numerics
+ * tests of individual CUDA kernels (the product calls are in ouu.h).
+ *
+ * ouu_kernel_gemm_bf16: D[M x N] = A[M x K] * B[N x K]^T on the tcgen05 tensor
+ * cores (TMA-fed, BF16 operands, FP32 accumulation in tensor memory), with the
+ * fused epilogue `mode` applied to the accumulator acc at row r, column c:
+ *   0 LINEAR     : y = alpha * acc + bias[c]
+ *   1 GELU       : a = acc + bias[c]; out_f32 = a; BF16 outputs = gelu(a)   (exact erf GELU)
+ *   2 DGELU_SCALE: y = acc * gelu'(aux[(r / aux_rdiv) * ld_aux + c]); out2 = bf16(acc)
+ * These are the dense layers of the reduced-basis network of Sec. 3.3 (forward
+ * values, forward-mode control-Jacobian tangents, and their adjoints).
+ * A, B: device BF16 row-major with leading dimensions lda, ldb (multiples of 8,
+ * 16-byte aligned bases).  Outputs (each may be NULL): out_f32 [M][ld_f32]
+ * (overwritten, or incremented when accumulate != 0), out_bf16 [M][ld_bf16],
+ * out_t_bf16 transposed [N][ld_t], out2_bf16 [M][ld2].  err_dev: device int set
+ * to 1 if a pipeline wait timed out (the kernel then returns without hanging).
+ * Launches on `stream`; returns INVALID_ARG for bad sizes/alignment. */
+#ifndef OUU_KERNELS_H
+#define OUU_KERNELS_H
+
+#include "ouu.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+ouu_status ouu_kernel_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int mode,
+                                float alpha, const float* bias, const float* aux, int ld_aux, int aux_rdiv,
+                                float* out_f32, int ld_f32, int accumulate, void* out_bf16, int ld_bf16,
+                                void* out_t_bf16, int ld_t, void* out2_bf16, int ld2, int* err_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OUU_KERNELS_H */

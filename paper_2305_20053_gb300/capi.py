@@ -65,6 +65,8 @@ SIGNATURES = {
     "ouu_risk_and_grad": (_i, [_vp, _i, _vp, _vp, _i, ctypes.POINTER(RiskDesc), _i, _dp, _dp, _dp, _dp, _dp,
                                ctypes.POINTER(EvalStats)]),
     "ouu_pde_solve_batch_noalloc": (_i, [ctypes.POINTER(ProblemDesc), _vp, _i, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "ouu_kernel_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _i, _i, _vp, _i, _i,
+                                  _vp, _i, _vp, _i, _vp, _i, _vp, _vp]),
     "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "ouu_problem_slots": (_i, [_vp]),
 }
@@ -199,3 +201,18 @@ def ouu_pde_solve_batch_noalloc(desc, m_dev, n_samples, z_dev, z_stride, u_dev, 
                                              dev_ptr(z_dev, torch.float64), z_stride, dev_ptr(u_dev, torch.float64),
                                              dev_ptr(q_dev, torch.float64), dev_ptr(status_dev, torch.int32),
                                              _stream_handle(stream)))
+
+
+def ouu_kernel_gemm_bf16(A, B, M, N, K, mode=0, alpha=1.0, bias=None, aux=None, aux_rdiv=1, out_f32=None,
+                         accumulate=0, out_bf16=None, out_t_bf16=None, out2_bf16=None, err=None, stream=None):
+    """D = A B^T on the tensor cores with a fused epilogue (kernel-level test entry)."""
+    import torch
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    ld = lambda t: 0 if t is None else t.stride(0)
+    check(load().ouu_kernel_gemm_bf16(dev_ptr(A, torch.bfloat16), A.stride(0), dev_ptr(B, torch.bfloat16),
+                                      B.stride(0), M, N, K, mode, alpha, dev_ptr(bias, torch.float32),
+                                      dev_ptr(aux, torch.float32), ld(aux), aux_rdiv, dev_ptr(out_f32, torch.float32),
+                                      ld(out_f32), accumulate, dev_ptr(out_bf16, torch.bfloat16), ld(out_bf16),
+                                      dev_ptr(out_t_bf16, torch.bfloat16), ld(out_t_bf16),
+                                      dev_ptr(out2_bf16, torch.bfloat16), ld(out2_bf16), dev_ptr(err, torch.int32),
+                                      _stream_handle(stream)))

@@ -1,0 +1,43 @@
+// BF16 tensor-core GEMM for sm_103a: TMA (SWIZZLE_128B) -> shared memory ->
+// tcgen05.mma (kind::f16, FP32 accumulator in tensor memory) -> tcgen05.ld ->
+// fused epilogue -> global.   D[M x N] = A[M x K] * B[N x K]^T, A and B K-major.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "ouu_internal.cuh"
+
+enum EpiMode {
+  EPI_LINEAR = 0,       // y = alpha * acc + bias[c]
+  EPI_GELU = 1,         // a = acc + bias[c]; out_f32 = a; bf16 outputs = gelu(a)
+  EPI_DGELU_SCALE = 2,  // y = acc * gelu'(aux[(r / aux_rdiv) * ld_aux + c]); out2 = bf16(acc)
+};
+
+struct EpiParams {
+  int mode;
+  float alpha;
+  const float* bias;              // [N] or null
+  float* out_f32;                 // [M][ld_f32] or null
+  int ld_f32;
+  int accumulate;                 // out_f32 += y instead of =
+  __nv_bfloat16* out_bf16;        // [M][ld_bf16] or null
+  int ld_bf16;
+  __nv_bfloat16* out_t_bf16;      // transposed: [N][ld_t] (element (r, c) at c * ld_t + r) or null
+  int ld_t;
+  __nv_bfloat16* out2_bf16;       // [M][ld2]: bf16(acc) before scaling (EPI_DGELU_SCALE) or null
+  int ld2;
+  const float* aux;               // pre-activations for gelu' (EPI_DGELU_SCALE)
+  int ld_aux;
+  int aux_rdiv;
+};
+
+// Tensor map of a row-major BF16 matrix [rows][ld] (K = inner, contiguous), box 64 x box_rows.
+// Returns false when the driver entry point is unavailable or the encode fails
+// (base must be 16-byte aligned and ld a multiple of 8).
+bool ouu_tmap_bf16(CUtensorMap* map, const void* base, uint64_t k, uint64_t rows, uint64_t ld, uint32_t box_rows);
+
+// Launch D = A B^T with A = [M][K] (lda), B = [N][K] (ldb), both BF16 row-major.
+// bn: N tile (64, 128 or 256).  err: device int set non-zero when a wait times out.
+ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
+                         const EpiParams& ep, int* err, cudaStream_t s);

@@ -1,0 +1,114 @@
+"""Numerics of the tcgen05/TMA BF16 GEMM against a plain fp32 PyTorch matmul of the
+same BF16 operands (products are exact in FP32; only the summation order differs).
+
+Reference in float64 of the same BF16 operands.  Tolerances, relative to the
+largest entry of each row: FP32 outputs 1e-5 + 5e-7 sqrt(K) (FP32 summation of
+K exact products); BF16 outputs one BF16 ulp (2^-8) plus that.
+"""
+import math
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2305_20053_gb300 import build, capi
+    build.build()
+    capi.load()
+    torch.backends.cuda.matmul.allow_tf32 = False
+
+
+def _bf(shape, ld=None, seed=0, scale=1.0):
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    rows, k = shape
+    ld = ld or (k + 7) // 8 * 8
+    buf = torch.zeros(rows, ld, device="cuda", dtype=torch.bfloat16)
+    buf[:, :k] = (scale * torch.randn(rows, k, device="cuda", generator=g)).to(torch.bfloat16)
+    return buf
+
+
+def _ref(A, B, K):
+    return (A[:, :K].double() @ B[:, :K].double().T).float()
+
+
+def _tol(K):
+    return 1e-5 + 5e-7 * math.sqrt(K)
+
+
+def _gelu_d1(x):
+    return 0.5 * (1 + torch.erf(x / math.sqrt(2))) + x * torch.exp(-0.5 * x * x) / math.sqrt(2 * math.pi)
+
+
+def _close(x, ref, tol):
+    scale = ref.abs().amax(dim=1, keepdim=True).clamp_min(1e-30)
+    err = ((x - ref).abs() / scale).max().item()
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("M,N,K,lda", [(300, 400, 304, 304), (4096, 200, 16641, 16704), (1, 16, 8, 8),
+                                       (513, 100, 200, 200), (400, 304, 25856, 25856)])
+def test_linear_bias_transposed(M, N, K, lda):
+    from paper_2305_20053_gb300 import capi
+    A = _bf((M, K), lda, seed=1)
+    B = _bf((N, K), None, seed=2)
+    bias = torch.randn(N, device="cuda")
+    out = torch.full((M, N), 7.0, device="cuda")
+    ob = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+    ot = torch.empty(N, M + 3, device="cuda", dtype=torch.bfloat16)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    capi.ouu_kernel_gemm_bf16(A, B, M, N, K, mode=0, alpha=0.5, bias=bias, out_f32=out, out_bf16=ob,
+                              out_t_bf16=ot, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = 0.5 * _ref(A, B, K) + bias
+    _close(out, ref, _tol(K))
+    _close(ob.float(), ref, 2 ** -8 + _tol(K))
+    _close(ot[:, :M].float().T, ref, 2 ** -8 + _tol(K))
+    # accumulate into the existing output
+    capi.ouu_kernel_gemm_bf16(A, B, M, N, K, mode=0, alpha=1.0, out_f32=out, accumulate=1, err=err)
+    torch.cuda.synchronize()
+    _close(out, ref + _ref(A, B, K), 2 * _tol(K))
+
+
+def test_gelu_layer():
+    from paper_2305_20053_gb300 import capi
+    M, N, K = 256, 400, 400
+    A = _bf((M, K), seed=3)
+    B = _bf((N, K), seed=4, scale=1.0 / 20)
+    bias = 0.1 * torch.randn(N, device="cuda")
+    a = torch.empty(M, N, device="cuda")
+    h = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+    ht = torch.empty(N, M, device="cuda", dtype=torch.bfloat16)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    capi.ouu_kernel_gemm_bf16(A, B, M, N, K, mode=1, bias=bias, out_f32=a, out_bf16=h, out_t_bf16=ht, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = _ref(A, B, K) + bias
+    _close(a, ref, _tol(K))
+    g = torch.nn.functional.gelu(ref)
+    assert (h.float() - g).abs().max().item() <= 2 ** -8 * g.abs().max().item() + 1e-4
+    assert torch.equal(ht.T, h)
+
+
+def test_tangent_scaling_epilogue():
+    from paper_2305_20053_gb300 import capi
+    B_, dz, N, K = 12, 100, 400, 400
+    M = B_ * dz
+    A = _bf((M, K), seed=5)
+    W = _bf((N, K), seed=6, scale=1.0 / 20)
+    aux = torch.randn(B_, N, device="cuda")
+    hd = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+    ad = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+    out = torch.empty(M, N, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    capi.ouu_kernel_gemm_bf16(A, W, M, N, K, mode=2, aux=aux, aux_rdiv=dz, out_f32=out, out_bf16=hd,
+                              out2_bf16=ad, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    acc = _ref(A, W, K)
+    scale = _gelu_d1(aux).repeat_interleave(dz, dim=0)
+    _close(out, acc * scale, 2 * _tol(K))
+    _close(ad.float(), acc, 2 ** -8 + _tol(K))
