@@ -175,6 +175,92 @@ ouu_status ouu_pde_solve_batch_noalloc(const ouu_problem_desc* desc, const doubl
                                        const double* z_dev, int64_t z_stride, double* u_dev, double* q_dev,
                                        int32_t* status_dev, void* cuda_stream);
 
+/* ------------------------------------------------------------------ MR-DINO
+ * Reduced-basis neural operator of Sec. 3.3: u_w(m, z) = Phi phi_w(m_r, z) + ubar,
+ * m_r the whitened coordinates of m on the r_m leading Karhunen-Loeve modes of
+ * the prior (Sec. 3.3, KLE; mode order: decreasing prior variance, ties by
+ * (k1 + k2, k1)), Phi the r_u leading modes of the mass-weighted POD of training
+ * states (Sec. 3.3, M = h^2 I on interior nodes, Phi^T M Phi = I), phi_w a dense
+ * net [m_r; z] -> width -> width -> width -> r_u with exact-erf GELU and a linear
+ * output layer.  The control Jacobian d_z phi_w is carried in forward mode
+ * (Sec. 3.2); training minimises the reduced-space DINO loss of Sec. 3.4,
+ *   (1/B) sum_i ||phi_i - y_i||^2 + jac_weight ||d_z phi_i - Y_i||_F^2,
+ * y_i = Phi^T M (u_i - ubar), Y_i = Phi^T M d_z u_i, by Adam (beta = 0.9, 0.999,
+ * eps = 1e-8).  GEMMs run on the tcgen05 tensor cores in BF16 with FP32
+ * accumulation; FP32 master weights and Adam moments.
+ *
+ * Parameter vector (FP32, flat): [W0, b0, W1, b1, W2, b2, W3, b3], W_l row-major
+ * [out][in]; W0 is width x (r_m + d_Z) with the KL inputs first, W3 is r_u x width. */
+typedef struct {
+  int n;              /* grid of the states (nodes per side), 2^k + 1 */
+  int lattice_L;      /* d_Z = L^2 controls */
+  int r_m, r_u;       /* reduced ranks of m (KL) and u (POD), <= 256 */
+  int width;          /* hidden width (three hidden layers), multiple of 8 */
+  int max_batch;      /* largest training batch (also the Jacobian chunk of ouu_dino_eval) */
+  int max_eval;       /* largest n_samples of an evaluation */
+  double gamma, delta, m_mean;   /* prior of m (defines the KL basis) */
+  double jac_weight;  /* weight of the Jacobian loss term: 1 = MR-DINO, 0 = MR-NO */
+} ouu_dino_desc;
+
+/* Defaults of the 129 x 129 workload: L = 10, r_m = r_u = 200, width 400,
+ * max_batch 256, max_eval 4096, gamma 0.1, delta 1, mbar 0, jac_weight 1. */
+void ouu_default_dino_desc(ouu_dino_desc* desc);
+
+/* Allocates the network, its Adam state and all work buffers on the current
+ * device; parameters start at zero (set them with ouu_dino_set_params).  Builds
+ * the KL projection rows for the prior in *desc. */
+ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stream, ouu_dino_t* out);
+ouu_status ouu_dino_destroy(ouu_dino_t d);
+/* Number of FP32 entries of the flat parameter vector. */
+size_t ouu_dino_num_params(ouu_dino_t d);
+/* Copies the parameters in (host FP32, n = ouu_dino_num_params) and resets Adam. */
+ouu_status ouu_dino_set_params(ouu_dino_t d, const float* params_host, size_t n);
+ouu_status ouu_dino_get_params(ouu_dino_t d, float* params_host, size_t n);
+
+/* Installs the POD basis: phi_dev [r_u][n*n] (zero on the boundary) and
+ * ubar_dev [n*n], both FP64 device.  Also forms c = Phi^T M (ubar - u_t) and the
+ * constant of the reduced QoI (Sec. 3.3: Q(u_w) = 1/2 ||phi + c||^2 + const). */
+ouu_status ouu_dino_set_bases(ouu_dino_t d, const double* phi_dev, const double* ubar_dev);
+/* Builds the basis from n_states training states u_dev [n_states][n][n] (FP64
+ * device): ubar = mean, snapshot Gram C = (U - ubar) M (U - ubar)^T (FP64), its
+ * eigenpairs by cyclic parallel Jacobi (FP64), Phi = (U - ubar)^T V Lambda^-1/2
+ * for the r_u largest eigenvalues, each mode's largest-magnitude entry positive.
+ * eig_host (nullable): the n_states eigenvalues, descending.  Then as set_bases. */
+ouu_status ouu_dino_build_bases(ouu_dino_t d, const double* u_dev, int n_states, double* eig_host);
+/* Copies the installed basis out (FP64 device, layouts as in set_bases). */
+ouu_status ouu_dino_get_bases(ouu_dino_t d, double* phi_dev, double* ubar_dev);
+
+/* Network inputs: xi_dev [n][r_m] FP32 = whitened KL coordinates of m_dev
+ * [n][n*n] (BF16 tensor-core projection, FP32 accumulation). */
+ouu_status ouu_dino_project_fields(ouu_dino_t d, const double* m_dev, int n_samples, float* xi_dev);
+/* Output targets: y_dev [n][r_u] FP32 = Phi^T M (u_i - ubar) (FP32). */
+ouu_status ouu_dino_project_states(ouu_dino_t d, const double* u_dev, int n_samples, float* y_dev);
+/* Jacobian targets (Sec. 3.4, implicit function theorem, forward route since
+ * d_Z < r_u): jy_dev [n][d_Z][r_u] FP32, jy[i][j] = Phi^T M J(u_i)^-1 g_j, by d_Z
+ * linearised solves per sample sharing one operator set-up (MG-PCG, FP32,
+ * relative residual cg_rtol of `p`).  u_dev: states of (m_dev, z_i). */
+ouu_status ouu_dino_jacobian_data(ouu_problem_t p, ouu_dino_t d, const double* m_dev, const double* u_dev,
+                                  int n_samples, float* jy_dev);
+
+/* One Adam step on the minibatch idx_dev[0..batch-1] (device int32 indices into
+ * the data arrays): xi_dev [*][r_m], z_dev [*][d_Z], y_dev [*][r_u],
+ * jy_dev [*][d_Z][r_u] (all FP32 device).  loss_out (host, nullable): the loss
+ * of this batch before the step (synchronises when given). */
+ouu_status ouu_dino_train_step(ouu_dino_t d, const float* xi_dev, const float* z_dev, const float* y_dev,
+                               const float* jy_dev, const int32_t* idx_dev, int batch, float lr, double* loss_out);
+/* Loss and its gradient (host FP32, flat parameter layout) on a minibatch, no update. */
+ouu_status ouu_dino_loss_grad(ouu_dino_t d, const float* xi_dev, const float* z_dev, const float* y_dev,
+                              const float* jy_dev, const int32_t* idx_dev, int batch, float* grad_host,
+                              double* loss_out);
+
+/* Surrogate evaluation at the shared control z_host[d_Z] for the fields m_dev
+ * [n_samples][n][n]: KL projection, network, reduced QoI.  Outputs (device, each
+ * nullable): phi_dev [n][r_u] FP32, jphi_dev [n][d_Z][r_u] FP32 (forward-mode
+ * d_z phi), q_dev [n] FP64 (Q(u_w) by the reduced form), gradq_dev [n][d_Z]
+ * FP64 (grad_z Q by reverse mode through the network).  Synchronises. */
+ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_samples, const double* z_host, float* phi_dev,
+                         float* jphi_dev, double* q_dev, double* gradq_dev);
+
 /* Thread-local message of the last failed call ("" if none).  Copies at most
  * len-1 bytes plus a terminating zero into buf; returns the full length. */
 size_t ouu_last_error(char* buf, size_t len);

@@ -47,6 +47,16 @@ def kl_projection_matrix(n, r_m, gamma=0.1, delta=1.0):
     return W, order
 
 
+def project_fields(m_flat, W, m_mean=0.0, bf16=False):
+    """Whitened KL coordinates xi_hat = (m - mbar) @ W.  With bf16=True both factors
+    are rounded to bfloat16 first (the tensor-core projection's operands); the sum
+    stays float64."""
+    a = np.asarray(m_flat, dtype=np.float64) - m_mean
+    if bf16:
+        a, W = round_bf16(a), round_bf16(W)
+    return a @ W
+
+
 # ----------------------------------------------------------------------------- POD
 def pod(U_int, r_u, h):
     """Mass-weighted POD of snapshots U_int (Ns, d) with M = h^2 I.

@@ -41,6 +41,13 @@ class RiskDesc(ctypes.Structure):
                 ("eps", ctypes.c_double), ("t", ctypes.c_double), ("t_optimal", ctypes.c_int)]
 
 
+class DinoDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("lattice_L", ctypes.c_int), ("r_m", ctypes.c_int), ("r_u", ctypes.c_int),
+                ("width", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_eval", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("delta", ctypes.c_double), ("m_mean", ctypes.c_double),
+                ("jac_weight", ctypes.c_double)]
+
+
 class EvalStats(ctypes.Structure):
     _fields_ = [("newton_min", ctypes.c_int), ("newton_max", ctypes.c_int), ("newton_mean", ctypes.c_double),
                 ("cg_total", ctypes.c_int), ("adjoint_solves", ctypes.c_int), ("n_not_converged", ctypes.c_int),
@@ -65,6 +72,21 @@ SIGNATURES = {
     "ouu_risk_and_grad": (_i, [_vp, _i, _vp, _vp, _i, ctypes.POINTER(RiskDesc), _i, _dp, _dp, _dp, _dp, _dp,
                                ctypes.POINTER(EvalStats)]),
     "ouu_pde_solve_batch_noalloc": (_i, [ctypes.POINTER(ProblemDesc), _vp, _i, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "ouu_default_dino_desc": (None, [ctypes.POINTER(DinoDesc)]),
+    "ouu_dino_create": (_i, [ctypes.POINTER(DinoDesc), _vp, ctypes.POINTER(_vp)]),
+    "ouu_dino_destroy": (_i, [_vp]),
+    "ouu_dino_num_params": (ctypes.c_size_t, [_vp]),
+    "ouu_dino_set_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+    "ouu_dino_get_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+    "ouu_dino_set_bases": (_i, [_vp, _vp, _vp]),
+    "ouu_dino_build_bases": (_i, [_vp, _vp, _i, _dp]),
+    "ouu_dino_get_bases": (_i, [_vp, _vp, _vp]),
+    "ouu_dino_project_fields": (_i, [_vp, _vp, _i, _vp]),
+    "ouu_dino_project_states": (_i, [_vp, _vp, _i, _vp]),
+    "ouu_dino_jacobian_data": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "ouu_dino_train_step": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, ctypes.c_float, _dp]),
+    "ouu_dino_loss_grad": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(ctypes.c_float), _dp]),
+    "ouu_dino_eval": (_i, [_vp, _vp, _i, _dp, _vp, _vp, _vp, _vp]),
     "ouu_kernel_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _i, _i, _vp, _i, _i,
                                   _vp, _i, _vp, _i, _vp, _i, _vp, _vp]),
     "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
@@ -216,3 +238,118 @@ def ouu_kernel_gemm_bf16(A, B, M, N, K, mode=0, alpha=1.0, bias=None, aux=None, 
                                       dev_ptr(out_t_bf16, torch.bfloat16), ld(out_t_bf16),
                                       dev_ptr(out2_bf16, torch.bfloat16), ld(out2_bf16), dev_ptr(err, torch.int32),
                                       _stream_handle(stream)))
+
+
+def dino_desc(**kw) -> DinoDesc:
+    d = DinoDesc()
+    load().ouu_default_dino_desc(ctypes.byref(d))
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+class Dino:
+    """Owns an ouu_dino_t (the MR-DINO network).  Methods are one-to-one with the C calls."""
+
+    def __init__(self, stream=None, **desc):
+        import torch
+        self.desc = dino_desc(**desc)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(load().ouu_dino_create(ctypes.byref(self.desc), _stream_handle(self.stream), ctypes.byref(h)))
+        self.handle = h
+        self.n_params = load().ouu_dino_num_params(h)
+        self.d_z = self.desc.lattice_L ** 2
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ouu_dino_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ouu_dino_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        check(load().ouu_dino_set_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+
+    def ouu_dino_get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        check(load().ouu_dino_get_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+        return p
+
+    def ouu_dino_set_bases(self, phi_dev, ubar_dev):
+        import torch
+        check(load().ouu_dino_set_bases(self.handle, dev_ptr(phi_dev, torch.float64), dev_ptr(ubar_dev, torch.float64)))
+
+    def ouu_dino_build_bases(self, u_dev, n_states):
+        eig = np.zeros(n_states)
+        import torch
+        check(load().ouu_dino_build_bases(self.handle, dev_ptr(u_dev, torch.float64), n_states,
+                                          eig.ctypes.data_as(_dp)))
+        return eig
+
+    def ouu_dino_get_bases(self, phi_dev, ubar_dev):
+        import torch
+        check(load().ouu_dino_get_bases(self.handle, dev_ptr(phi_dev, torch.float64), dev_ptr(ubar_dev, torch.float64)))
+
+    def ouu_dino_project_fields(self, m_dev, n, xi_dev):
+        import torch
+        check(load().ouu_dino_project_fields(self.handle, dev_ptr(m_dev, torch.float64), n,
+                                             dev_ptr(xi_dev, torch.float32)))
+
+    def ouu_dino_project_states(self, u_dev, n, y_dev):
+        import torch
+        check(load().ouu_dino_project_states(self.handle, dev_ptr(u_dev, torch.float64), n,
+                                             dev_ptr(y_dev, torch.float32)))
+
+    def ouu_dino_jacobian_data(self, problem, m_dev, u_dev, n, jy_dev):
+        import torch
+        check(load().ouu_dino_jacobian_data(problem.handle, self.handle, dev_ptr(m_dev, torch.float64),
+                                            dev_ptr(u_dev, torch.float64), n, dev_ptr(jy_dev, torch.float32)))
+
+    def ouu_dino_train_step(self, xi, z, y, jy, idx, batch, lr, want_loss=False):
+        import torch
+        loss = np.zeros(1)
+        check(load().ouu_dino_train_step(self.handle, dev_ptr(xi, torch.float32), dev_ptr(z, torch.float32),
+                                         dev_ptr(y, torch.float32), dev_ptr(jy, torch.float32),
+                                         dev_ptr(idx, torch.int32), batch, lr,
+                                         loss.ctypes.data_as(_dp) if want_loss else None))
+        return float(loss[0]) if want_loss else None
+
+    def ouu_dino_loss_grad(self, xi, z, y, jy, idx, batch):
+        import torch
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = np.zeros(1)
+        check(load().ouu_dino_loss_grad(self.handle, dev_ptr(xi, torch.float32), dev_ptr(z, torch.float32),
+                                        dev_ptr(y, torch.float32), dev_ptr(jy, torch.float32),
+                                        dev_ptr(idx, torch.int32), batch,
+                                        g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), loss.ctypes.data_as(_dp)))
+        return float(loss[0]), g
+
+    def ouu_dino_eval(self, m_dev, n, z_host, phi_dev=None, jphi_dev=None, q_dev=None, gradq_dev=None):
+        import torch
+        z = np.ascontiguousarray(z_host, dtype=np.float64)
+        check(load().ouu_dino_eval(self.handle, dev_ptr(m_dev, torch.float64), n, z.ctypes.data_as(_dp),
+                                   dev_ptr(phi_dev, torch.float32), dev_ptr(jphi_dev, torch.float32),
+                                   dev_ptr(q_dev, torch.float64), dev_ptr(gradq_dev, torch.float64)))
+
+
+def flatten_params(Ws, bs):
+    """Flat FP32 parameter vector [W0, b0, W1, b1, ...] (W row-major [out][in])."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32)])
+                           for W, b in zip(Ws, bs)])
+
+
+def unflatten_params(p, widths):
+    """Inverse of flatten_params for layer widths [n_in, h1, ..., n_out]."""
+    Ws, bs, o = [], [], 0
+    for fi, fo in zip(widths[:-1], widths[1:]):
+        Ws.append(np.asarray(p[o:o + fi * fo], np.float64).reshape(fo, fi))
+        o += fi * fo
+        bs.append(np.asarray(p[o:o + fo], np.float64))
+        o += fo
+    return Ws, bs

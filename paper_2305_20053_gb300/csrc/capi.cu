@@ -4,6 +4,7 @@
 #include <cstring>
 #include <vector>
 
+#include "dino.cuh"
 #include "ouu_internal.cuh"
 
 static thread_local std::string g_last_error;
@@ -392,8 +393,46 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
   OUU_CUDA_TRY(cudaStreamSynchronize(p->stream));   // h_out / rd are reused below
   if (backend == OUU_BACKEND_DINO) {
     OUU_CHECK_ARG(dino != nullptr, "DINO backend needs a trained network");
-    ouu_set_error("DINO backend not available in this build");
-    return OUU_ERR_STATE;
+    OUU_CHECK_ARG(dino->n == p->n && dino->dz == p->dz, "problem and network grids differ");
+    OUU_CHECK_ARG(n_samples <= dino->maxE, "n_samples exceeds the network's max_eval");
+    if (!dino->bases_ready) {
+      ouu_set_error("network bases not built");
+      return OUU_ERR_STATE;
+    }
+    cudaStream_t ds = dino->stream;
+    OUU_CUDA_TRY(cudaEventRecord(p->ev[0], ds));
+    if (ouu_status st = dino_eval_core(dino, m_dev, n_samples, z_host, true)) return st;
+    OUU_CUDA_TRY(cudaEventRecord(p->ev[1], ds));
+    launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, ds);
+    OUU_CUDA_TRY(cudaEventRecord(p->ev[2], ds));
+    dino_weighted_grads(dino, p->d_w, n_samples, n_risks, d_grad);
+    OUU_CUDA_TRY(cudaEventRecord(p->ev[3], ds));
+    OUU_CUDA_TRY(cudaGetLastError());
+    const size_t ob = (size_t)(OUU_MAX_RISKS * (3 + dz) + 8) * 8;
+    OUU_CUDA_TRY(cudaMemcpyAsync(p->h_out, p->d_out, ob, cudaMemcpyDeviceToHost, ds));
+    int gemm_err = 0;
+    OUU_CUDA_TRY(cudaMemcpyAsync(p->h_stat, dino->d_err, 4, cudaMemcpyDeviceToHost, ds));
+    OUU_CUDA_TRY(cudaStreamSynchronize(ds));
+    gemm_err = p->h_stat[0];
+    if (gemm_err) {
+      cudaMemsetAsync(dino->d_err, 0, 4, ds);
+      ouu_set_error("tensor-core GEMM pipeline wait timed out");
+      return OUU_ERR_CUDA;
+    }
+    for (int r = 0; r < n_risks; ++r) {
+      risk_out[r] = p->h_out[3 * r + 0];
+      grad_t_out[r] = p->h_out[3 * r + 1];
+      if (t_out) t_out[r] = p->h_out[3 * r + 2];
+      std::memcpy(grad_z_out + (size_t)r * dz, p->h_out + 3 * OUU_MAX_RISKS + (size_t)r * dz, (size_t)dz * 8);
+    }
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+      cudaEventElapsedTime(&stats->ms_state, p->ev[0], p->ev[1]);
+      cudaEventElapsedTime(&stats->ms_weights, p->ev[1], p->ev[2]);
+      cudaEventElapsedTime(&stats->ms_reduce, p->ev[2], p->ev[3]);
+      cudaEventElapsedTime(&stats->ms_total, p->ev[0], p->ev[3]);
+    }
+    return OUU_OK;
   }
   OUU_CHECK_ARG(backend == OUU_BACKEND_PDE, "unknown backend");
   PdeArgs a = base_args(p, n_samples);
@@ -467,5 +506,25 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
     ouu_set_error("non-finite residual in some sample");
     return OUU_ERR_NONFINITE;
   }
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_jacobian_data(ouu_problem_t p, ouu_dino_t d, const double* m_dev, const double* u_dev,
+                                             int n_samples, float* jy_dev) {
+  OUU_CHECK_ARG(p && d && m_dev && u_dev && jy_dev, "null argument");
+  OUU_CHECK_ARG(p->n == d->n && p->dz == d->dz, "problem and network grids differ");
+  OUU_CHECK_ARG(n_samples >= 0 && n_samples <= p->desc.max_samples, "n_samples outside [0, max_samples]");
+  if (!d->bases_ready) {
+    ouu_set_error("network bases not built");
+    return OUU_ERR_STATE;
+  }
+  if (n_samples == 0) return OUU_OK;
+  PdeArgs a = base_args(p, n_samples);
+  a.m = m_dev;
+  a.u = const_cast<double*>(u_dev);
+  OUU_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, 4, p->stream));
+  launch_pde_jacobian_data(a, solver_grid(p, n_samples), d->d_phi, d->ru, jy_dev, p->stream);
+  OUU_CUDA_TRY(cudaGetLastError());
+  OUU_CUDA_TRY(cudaStreamSynchronize(p->stream));
   return OUU_OK;
 }

@@ -1,0 +1,867 @@
+// MR-DINO: reduced-basis neural operator with forward-mode control Jacobian
+// (Sec. 3.2-3.4): KL projection, dense GELU net, DINO loss and its gradient,
+// Adam, and the surrogate risk evaluation.  Dense contractions run on the
+// tcgen05 GEMM (tc_gemm.cu); the kernels here are the element-wise glue.
+//
+// Training rows are stacked: rows [0, B) carry the values of the B samples,
+// rows B + b*dz + j carry the tangent d/dz_j of sample b, so one GEMM moves a
+// layer's values or tangents, and one GEMM over all B + B*dz rows forms the
+// weight gradient of the value and Jacobian terms together.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "dino.cuh"
+
+static int pad8(int x) { return (x + 7) / 8 * 8; }
+static int pad64(int x) { return (x + 63) / 64 * 64; }
+
+static __device__ __forceinline__ float gelu_d1(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
+}
+static __device__ __forceinline__ float gelu_d2(float x) {
+  return 0.3989422804014327f * expf(-0.5f * x * x) * (2.f - x * x);
+}
+
+#define GRID_STRIDE(e, total) \
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (total); e += (int64_t)gridDim.x * blockDim.x)
+
+static int grid_for(int64_t total, int threads = 256) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((total + threads - 1) / threads, 152 * 16));
+}
+
+// ------------------------------------------------------------------ element-wise kernels
+__global__ void k_cast_fields_bf16(const double* __restrict__ m, int nn, int nnp, double mean, int count,
+                                   __nv_bfloat16* __restrict__ out) {
+  GRID_STRIDE(e, (int64_t)count * nnp) {
+    const int64_t s = e / nnp;
+    const int k = (int)(e - s * nnp);
+    out[e] = __float2bfloat16(k < nn ? (float)(m[s * nn + k] - mean) : 0.f);
+  }
+}
+
+// x0[b] = [xi[src]; z[src]; 0-pad], src = idx ? idx[b] : b (z_stride 0: one shared z).
+__global__ void k_build_x0(const float* __restrict__ xi, const int* __restrict__ idx, const float* __restrict__ z,
+                           int64_t z_stride, int rm, int dz, int in0p, int B, __nv_bfloat16* __restrict__ x0,
+                           __nv_bfloat16* __restrict__ x0t) {
+  GRID_STRIDE(e, (int64_t)B * in0p) {
+    const int b = (int)(e / in0p), k = (int)(e % in0p);
+    const int64_t src = idx ? idx[b] : b;
+    float v = 0.f;
+    if (k < rm) v = xi[src * rm + k];
+    else if (k < rm + dz) v = z[src * z_stride + (k - rm)];
+    const __nv_bfloat16 bv = __float2bfloat16(v);
+    x0[e] = bv;
+    if (x0t) x0t[(int64_t)k * B + b] = bv;
+  }
+}
+
+// First-layer tangents: hdot_1[(b, j), n] = gelu'(a_1[b, n]) * W0[n, rm + j].
+__global__ void k_tangent1(const float* __restrict__ a1, const float* __restrict__ W0, int in0, int rm, int dz,
+                           int wd, int wdp, int B, __nv_bfloat16* __restrict__ hs_t) {
+  GRID_STRIDE(e, (int64_t)B * dz * wd) {
+    const int64_t t = e / wd;
+    const int n = (int)(e % wd);
+    const int b = (int)(t / dz), j = (int)(t % dz);
+    hs_t[t * wdp + n] = __float2bfloat16(gelu_d1(a1[(int64_t)b * wd + n]) * W0[(int64_t)n * in0 + rm + j]);
+  }
+}
+
+// out[c][r] = in[r][c] for r < rows, c < cols (32 x 32 tiles).
+__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int64_t ld_in, int rows, int cols,
+                                 __nv_bfloat16* __restrict__ out, int64_t ld_out) {
+  __shared__ __nv_bfloat16 tile[32][34];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[(int64_t)r * ld_in + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(int64_t)c * ld_out + r] = tile[threadIdx.x][k];
+  }
+}
+
+static void transpose_bf16(const __nv_bfloat16* in, int64_t ld_in, int rows, int cols, __nv_bfloat16* out,
+                           int64_t ld_out, cudaStream_t s) {
+  dim3 g((cols + 31) / 32, (rows + 31) / 32), b(32, 8);
+  k_transpose_bf16<<<g, b, 0, s>>>(in, ld_in, rows, cols, out, ld_out);
+}
+
+// DINO loss of Sec. 3.4 and its gradient w.r.t. the stacked outputs.
+// Value rows: e = phi - y; tangent rows (b, j): e = d phi / d z_j - Y_b[:, j].
+#define LOSS_BLOCKS 256
+__global__ void k_loss_out(const float* __restrict__ out, int ldo, const float* __restrict__ y,
+                           const float* __restrict__ jy, const int* __restrict__ idx, int B, int dz, int ru, float wj,
+                           __nv_bfloat16* __restrict__ go, int ldgo, float* __restrict__ gov, double* part) {
+  __shared__ double red[40];
+  double acc = 0.0;
+  GRID_STRIDE(e, (int64_t)(B + (int64_t)B * dz) * ru) {
+    const int64_t row = e / ru;
+    const int r = (int)(e % ru);
+    float ev, g;
+    if (row < B) {
+      const int64_t src = idx[row];
+      ev = out[row * ldo + r] - y[src * ru + r];
+      g = 2.f * ev / B;
+      acc += (double)ev * ev / B;
+      gov[row * ru + r] = g;
+    } else {
+      const int64_t t = row - B;
+      const int64_t b = t / dz, j = t % dz;
+      const int64_t src = idx[b];
+      ev = out[row * ldo + r] - jy[(src * dz + j) * ru + r];
+      g = 2.f * wj * ev / B;
+      acc += (double)wj * ev * ev / B;
+    }
+    go[row * ldgo + r] = __float2bfloat16(g);
+  }
+  CtaCtx c{red};
+  const double s = c.sum_d(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sum_parts(const double* part, int n, double* out) {
+  __shared__ double red[40];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+  CtaCtx c{red};
+  const double s = c.sum_d(a);
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+// Backward through a GELU layer for the stacked rows.
+// value row b:   ga[b, n] = s'(a) gh[b, n] + s''(a) sum_j ghdot[(b, j), n] adot[(b, j), n]
+// tangent (b,j): gadot[(b, j), n] = s'(a[b, n]) ghdot[(b, j), n]
+// adot = AD (layers 2, 3) or W0[n, rm + j] (layer 1).
+__global__ void k_bwd_layer(const float* __restrict__ gh, const float* __restrict__ a,
+                            const __nv_bfloat16* __restrict__ ad, int wdp, const float* __restrict__ W0, int in0,
+                            int rm, int dz, int wd, int B, __nv_bfloat16* __restrict__ ga, float* __restrict__ gav) {
+  GRID_STRIDE(e, (int64_t)(B + (int64_t)B * dz) * wd) {
+    const int64_t row = e / wd;
+    const int n = (int)(e % wd);
+    if (row < B) {
+      const float av = a[row * wd + n];
+      float s = 0.f;
+      for (int j = 0; j < dz; ++j) {
+        const int64_t t = row * dz + j;
+        const float adot = ad ? __bfloat162float(ad[t * wdp + n]) : W0[(int64_t)n * in0 + rm + j];
+        s += gh[(B + t) * wd + n] * adot;
+      }
+      const float g = gelu_d1(av) * gh[row * wd + n] + gelu_d2(av) * s;
+      ga[row * wdp + n] = __float2bfloat16(g);
+      gav[row * wd + n] = g;
+    } else {
+      const int64_t b = (row - B) / dz;
+      ga[row * wdp + n] = __float2bfloat16(gelu_d1(a[b * wd + n]) * gh[row * wd + n]);
+    }
+  }
+}
+
+// dW0[n, rm + j] += sum_b s'(a_1[b, n]) ghdot_1[(b, j), n]  (first-layer tangent term).
+__global__ void k_dw0z(const float* __restrict__ a1, const float* __restrict__ gh, int B, int dz, int wd, int rm,
+                       int in0, float* __restrict__ dW0) {
+  GRID_STRIDE(e, (int64_t)dz * wd) {
+    const int j = (int)(e / wd), n = (int)(e % wd);
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += gelu_d1(a1[(int64_t)b * wd + n]) * gh[(B + (int64_t)b * dz + j) * wd + n];
+    dW0[(int64_t)n * in0 + rm + j] += s;
+  }
+}
+
+// out[c] = sum_r X[r][c]
+__global__ void k_colsum(const float* __restrict__ X, int rows, int cols, int ld, float* __restrict__ out) {
+  GRID_STRIDE(c, cols) {
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += X[(int64_t)r * ld + c];
+    out[c] = s;
+  }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  GRID_STRIDE(i, n) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// BF16 copies of one weight matrix W [out][in]: Wb [out][inp], WTb [in][outp].
+__global__ void k_weight_bf16(const float* __restrict__ W, int out, int in, int inp, int outp,
+                              __nv_bfloat16* __restrict__ Wb, __nv_bfloat16* __restrict__ WTb) {
+  GRID_STRIDE(e, (int64_t)out * inp) {
+    const int o = (int)(e / inp), i = (int)(e % inp);
+    const __nv_bfloat16 v = __float2bfloat16(i < in ? W[(int64_t)o * in + i] : 0.f);
+    Wb[e] = v;
+    if (i < in) WTb[(int64_t)i * outp + o] = v;
+  }
+}
+
+// Reduced QoI (Sec. 3.3): Q_i = 1/2 ||phi_i + c||^2 + const and the reverse-mode seed phi_i + c.
+__global__ void k_qoi_seed(const float* __restrict__ phi, int ldp, const double* __restrict__ c, double qconst, int N,
+                           int ru, double* __restrict__ Q, __nv_bfloat16* __restrict__ seed, int lds) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  double s = 0.0;
+  for (int r = lane; r < ru; r += 32) {
+    const double v = (double)phi[(int64_t)warp * ldp + r] + c[r];
+    s += v * v;
+    if (seed) seed[(int64_t)warp * lds + r] = __float2bfloat16((float)v);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) Q[warp] = 0.5 * s + qconst;
+}
+
+// out[r][j] = sum_i w[r][i] gq[i][j]
+__global__ void k_weighted_grads(const double* __restrict__ w, const float* __restrict__ gq, int ldg, int N, int dz,
+                                 double* __restrict__ out) {
+  __shared__ double red[40];
+  const int r = blockIdx.y, j = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s += w[(int64_t)r * N + i] * (double)gq[(int64_t)i * ldg + j];
+  CtaCtx c{red};
+  const double t = c.sum_d(s);
+  if (threadIdx.x == 0) out[r * dz + j] = t;
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ in, int ld_in, int rows, int cols, double* __restrict__ out) {
+  GRID_STRIDE(e, (int64_t)rows * cols) {
+    const int64_t r = e / cols;
+    const int c = (int)(e % cols);
+    out[e] = in[r * ld_in + c];
+  }
+}
+
+__global__ void k_copy_rows_f32(const float* __restrict__ in, int ld_in, int rows, int cols, float* __restrict__ out,
+                                int ld_out) {
+  GRID_STRIDE(e, (int64_t)rows * cols) {
+    const int64_t r = e / cols;
+    const int c = (int)(e % cols);
+    out[r * ld_out + c] = in[r * ld_in + c];
+  }
+}
+
+// y[i][r] = h^2 sum_p Phi[r][p] (u_i[p] - ubar[p])  (FP32, 32 x 32 output tiles).
+__global__ void k_project_states(const double* __restrict__ u, const double* __restrict__ ubar,
+                                 const float* __restrict__ phi, int nn, int ru, int N, float h2, float* __restrict__ y) {
+  __shared__ float su[32][33], sp[32][33];
+  const int i0 = blockIdx.y * 32, r0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int p0 = 0; p0 < nn; p0 += 32) {
+    for (int k = ty; k < 32; k += 8) {
+      const int i = i0 + k, r = r0 + k, p = p0 + tx;
+      su[k][tx] = (i < N && p < nn) ? (float)(u[(int64_t)i * nn + p] - ubar[p]) : 0.f;
+      sp[k][tx] = (r < ru && p < nn) ? phi[(int64_t)r * nn + p] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int pp = 0; pp < 32; ++pp) {
+      const float b = sp[tx][pp];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += su[ty + 8 * q][pp] * b;
+    }
+    __syncthreads();
+  }
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + ty + 8 * q, r = r0 + tx;
+    if (i < N && r < ru) y[(int64_t)i * ru + r] = h2 * acc[q];
+  }
+}
+
+// c[r] = h^2 sum_p Phi[r][p] (ubar[p] - ut[p]) and sum_p h^2 (ubar - ut)^2 (FP64).
+__global__ void k_reduced_qoi_terms(const double* __restrict__ phi64, const double* __restrict__ ubar,
+                                    const double* __restrict__ ut, int n, int ru, double* __restrict__ c,
+                                    double* __restrict__ norm2) {
+  __shared__ double red[40];
+  CtaCtx cc{red};
+  const double h2 = 1.0 / ((double)(n - 1) * (n - 1));
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
+    const int iy = p / n, ix = p % n;
+    if (iy == 0 || ix == 0 || iy == n - 1 || ix == n - 1) continue;
+    const double d = ubar[p] - ut[p];
+    s += r < ru ? phi64[(int64_t)r * n * n + p] * d : d * d;
+  }
+  const double t = cc.sum_d(s);
+  if (threadIdx.x == 0) {
+    if (r < ru) c[r] = h2 * t;
+    else *norm2 = h2 * t;
+  }
+}
+
+__global__ void k_phi_to_f32(const double* __restrict__ in, int64_t count, float* __restrict__ out) {
+  GRID_STRIDE(e, count) out[e] = (float)in[e];
+}
+
+// ------------------------------------------------------------------ host helpers
+#define DINO_TRY(expr)                        \
+  do {                                        \
+    ouu_status st_ = (expr);                  \
+    if (st_ != OUU_OK) return st_;            \
+  } while (0)
+
+static EpiParams epi(int mode) {
+  EpiParams e;
+  std::memset(&e, 0, sizeof(e));
+  e.mode = mode;
+  e.alpha = 1.f;
+  e.aux_rdiv = 1;
+  return e;
+}
+
+static ouu_status gemm(ouu_dino* d, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
+                       int K, const EpiParams& ep) {
+  return ouu_gemm_bf16(A, lda, B, ldb, M, N, K, ep, d->d_err, d->stream);
+}
+
+extern "C" void ouu_default_dino_desc(ouu_dino_desc* d) {
+  if (!d) return;
+  d->n = 129;
+  d->lattice_L = 10;
+  d->r_m = 200;
+  d->r_u = 200;
+  d->width = 400;
+  d->max_batch = 256;
+  d->max_eval = 4096;
+  d->gamma = 0.1;
+  d->delta = 1.0;
+  d->m_mean = 0.0;
+  d->jac_weight = 1.0;
+}
+
+static void free_dino(ouu_dino* d) {
+  if (!d) return;
+  void* ptrs[] = {d->d_params, d->d_grad, d->d_adam_m, d->d_adam_v, d->d_phi, d->d_phi64, d->d_ubar, d->d_ut,
+                  d->d_c, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
+                  d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->Mbf, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
+                  d->Ge, d->GQe, d->Qe, d->d_zf, d->d_err, d->d_gov};
+  for (void* p : ptrs) cudaFree(p);
+  for (int l = 0; l < 4; ++l) {
+    cudaFree(d->A[l]);
+    cudaFree(d->HS[l]);
+    cudaFree(d->HST[l]);
+    cudaFree(d->AD[l]);
+    cudaFree(d->Ae[l]);
+    cudaFree(d->Wb[l]);
+    cudaFree(d->WTb[l]);
+  }
+  cudaFreeHost(d->h_pin);
+  delete d;
+}
+
+extern "C" ouu_status ouu_dino_destroy(ouu_dino_t d) {
+  if (!d) return OUU_OK;
+  cudaStreamSynchronize(d->stream);
+  free_dino(d);
+  return OUU_OK;
+}
+
+extern "C" size_t ouu_dino_num_params(ouu_dino_t d) { return d ? d->n_params : 0; }
+
+extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stream, ouu_dino_t* out) {
+  OUU_CHECK_ARG(desc && out, "null argument");
+  *out = nullptr;
+  const int n = desc->n;
+  OUU_CHECK_ARG(n >= 5 && n <= 1025 && (((n - 1) & (n - 2)) == 0), "n must be 2^k + 1");
+  OUU_CHECK_ARG(desc->lattice_L >= 1 && desc->lattice_L <= 64, "lattice_L must be in [1, 64]");
+  OUU_CHECK_ARG(desc->r_m >= 1 && desc->r_m <= n * n && desc->r_u >= 1 && desc->r_u <= 256, "bad ranks");
+  OUU_CHECK_ARG(desc->width >= 8 && desc->width % 8 == 0 && desc->width <= 2048, "width: multiple of 8");
+  OUU_CHECK_ARG(desc->max_batch >= 8 && desc->max_batch % 8 == 0, "max_batch: positive multiple of 8");
+  OUU_CHECK_ARG(desc->max_eval >= 1, "max_eval must be positive");
+  OUU_CHECK_ARG(desc->gamma > 0 && desc->delta > 0 && desc->jac_weight >= 0, "bad prior or loss weight");
+  ouu_dino* d = new ouu_dino();
+  d->desc = *desc;
+  d->stream = (cudaStream_t)cuda_stream;
+  d->n = n;
+  d->nn = n * n;
+  d->nnp = pad64(n * n);
+  d->dz = desc->lattice_L * desc->lattice_L;
+  d->rm = desc->r_m;
+  d->ru = desc->r_u;
+  d->wd = desc->width;
+  d->in0 = d->rm + d->dz;
+  d->maxB = desc->max_batch;
+  d->maxE = desc->max_eval;
+  d->R = d->maxB * d->dz;
+  d->BR = d->maxB + d->R;
+  d->h = 1.0 / (n - 1);
+  const int ins[4] = {d->in0, d->wd, d->wd, d->wd}, outs[4] = {d->wd, d->wd, d->wd, d->ru};
+  size_t off = 0;
+  for (int l = 0; l < 4; ++l) {
+    d->in_l[l] = ins[l];
+    d->out_l[l] = outs[l];
+    d->inp_l[l] = pad8(ins[l]);
+    d->outp_l[l] = pad8(outs[l]);
+    d->offW[l] = off;
+    off += (size_t)ins[l] * outs[l];
+    d->offb[l] = off;
+    off += outs[l];
+  }
+  d->n_params = off;
+  const int wdp = d->wd, rup = pad8(d->ru), in0p = d->inp_l[0], dzp = pad8(d->dz);
+  const size_t BR = d->BR, maxB = d->maxB, E = d->maxE;
+  d->chunkE = (int)std::max<int64_t>(8, std::min<int64_t>(E, (256ll << 20) / ((int64_t)d->nnp * 2)));
+  bool ok = true;
+  auto al = [&](void** p, size_t bytes) {
+    if (ok && cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) ok = false;
+    if (ok) cudaMemset(*p, 0, std::max<size_t>(bytes, 16));
+  };
+  al((void**)&d->d_params, off * 4);
+  al((void**)&d->d_grad, off * 4);
+  al((void**)&d->d_adam_m, off * 4);
+  al((void**)&d->d_adam_v, off * 4);
+  for (int l = 0; l < 4; ++l) {
+    al((void**)&d->Wb[l], (size_t)outs[l] * d->inp_l[l] * 2);
+    al((void**)&d->WTb[l], (size_t)ins[l] * d->outp_l[l] * 2);
+  }
+  al((void**)&d->d_phi, (size_t)d->ru * d->nn * 4);
+  al((void**)&d->d_phi64, (size_t)d->ru * d->nn * 8);
+  al((void**)&d->d_ubar, (size_t)d->nn * 8);
+  al((void**)&d->d_ut, (size_t)d->nn * 8);
+  al((void**)&d->d_c, (size_t)d->ru * 8 + 16);
+  al((void**)&d->d_wkl, (size_t)d->rm * d->nnp * 2);
+  al((void**)&d->d_kl_order, (size_t)d->rm * 4);
+  al((void**)&d->X0, maxB * in0p * 2);
+  al((void**)&d->X0T, (size_t)in0p * maxB * 2);
+  for (int l = 1; l <= 3; ++l) {
+    al((void**)&d->A[l], maxB * d->wd * 4);
+    al((void**)&d->HS[l], BR * wdp * 2);
+    al((void**)&d->HST[l], (size_t)d->wd * BR * 2);
+    if (l >= 2) al((void**)&d->AD[l], (size_t)d->R * wdp * 2);
+  }
+  al((void**)&d->OUT, BR * rup * 4);
+  al((void**)&d->GO, BR * rup * 2);
+  al((void**)&d->GOT, (size_t)d->ru * BR * 2);
+  al((void**)&d->d_gov, maxB * d->ru * 4);
+  al((void**)&d->GH, BR * d->wd * 4);
+  al((void**)&d->GA, BR * wdp * 2);
+  al((void**)&d->GAT, (size_t)d->wd * BR * 2);
+  al((void**)&d->GAv, maxB * d->wd * 4);
+  al((void**)&d->GA1T, (size_t)d->wd * maxB * 2);
+  al((void**)&d->d_loss_part, LOSS_BLOCKS * 8);
+  al((void**)&d->d_loss, 16);
+  al((void**)&d->Mbf, (size_t)d->chunkE * d->nnp * 2);
+  al((void**)&d->XIe, E * d->rm * 4);
+  al((void**)&d->X0e, E * in0p * 2);
+  for (int l = 1; l <= 3; ++l) al((void**)&d->Ae[l], E * d->wd * 4);
+  al((void**)&d->He0, E * wdp * 2);
+  al((void**)&d->He1, E * wdp * 2);
+  al((void**)&d->OUTe, E * rup * 4);
+  al((void**)&d->Ge, E * rup * 2);
+  al((void**)&d->GQe, E * dzp * 4);
+  al((void**)&d->Qe, E * 8);
+  al((void**)&d->d_zf, std::max<size_t>(maxB, 1) * d->dz * 4 + 64);
+  al((void**)&d->d_err, 16);
+  if (ok && cudaMallocHost((void**)&d->h_pin, (size_t)(4 * 3 + 4 * d->dz + 64) * 8 + 4096) != cudaSuccess) ok = false;
+  if (!ok) {
+    cudaGetLastError();
+    free_dino(d);
+    ouu_set_error("device allocation failed in ouu_dino_create");
+    return OUU_ERR_OOM;
+  }
+  // KL projection rows: mode order by (lambda, k1 + k2, k1); row j = (lambda_q / n) v_k1(ix) v_k2(iy).
+  {
+    std::vector<double> mu(n), V((size_t)n * n);
+    for (int k = 0; k < n; ++k) {
+      const double sn = std::sin(M_PI * k / (2.0 * n));
+      mu[k] = 4.0 * n * n * (sn * sn);
+      const double s = k == 0 ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
+      for (int j = 0; j < n; ++j) V[(size_t)k * n + j] = s * std::cos(M_PI * k * (j + 0.5) / n);
+    }
+    std::vector<int> q(n * n);
+    std::iota(q.begin(), q.end(), 0);
+    auto lam = [&](int qq) { return desc->delta + desc->gamma * (mu[qq % n] + mu[qq / n]); };
+    std::stable_sort(q.begin(), q.end(), [&](int a, int b) {
+      const double la = lam(a), lb = lam(b);
+      if (la != lb) return la < lb;
+      const int sa = a % n + a / n, sb = b % n + b / n;
+      if (sa != sb) return sa < sb;
+      return a % n < b % n;
+    });
+    std::vector<__nv_bfloat16> rows((size_t)d->rm * d->nnp, __float2bfloat16(0.f));
+    for (int j = 0; j < d->rm; ++j) {
+      const int qq = q[j], k1 = qq % n, k2 = qq / n;
+      const double sc = lam(qq) / n;
+      for (int iy = 0; iy < n; ++iy)
+        for (int ix = 0; ix < n; ++ix)
+          rows[(size_t)j * d->nnp + iy * n + ix] = __float2bfloat16((float)(sc * V[(size_t)k2 * n + iy] * V[(size_t)k1 * n + ix]));
+    }
+    OUU_CUDA_TRY(cudaMemcpy(d->d_wkl, rows.data(), rows.size() * 2, cudaMemcpyHostToDevice));
+    OUU_CUDA_TRY(cudaMemcpy(d->d_kl_order, q.data(), (size_t)d->rm * 4, cudaMemcpyHostToDevice));
+    std::vector<double> ut(d->nn);
+    for (int iy = 0; iy < n; ++iy)
+      for (int ix = 0; ix < n; ++ix)
+        ut[(size_t)iy * n + ix] = std::sin(M_PI * (ix / (double)(n - 1))) * std::sin(M_PI * (iy / (double)(n - 1)));
+    OUU_CUDA_TRY(cudaMemcpy(d->d_ut, ut.data(), (size_t)d->nn * 8, cudaMemcpyHostToDevice));
+  }
+  OUU_CUDA_TRY(cudaDeviceSynchronize());
+  *out = d;
+  return OUU_OK;
+}
+
+static void refresh_bf16_weights(ouu_dino* d) {
+  for (int l = 0; l < 4; ++l) {
+    const int64_t tot = (int64_t)d->out_l[l] * d->inp_l[l];
+    k_weight_bf16<<<grid_for(tot), 256, 0, d->stream>>>(d->d_params + d->offW[l], d->out_l[l], d->in_l[l],
+                                                         d->inp_l[l], d->outp_l[l], d->Wb[l], d->WTb[l]);
+  }
+}
+
+extern "C" ouu_status ouu_dino_set_params(ouu_dino_t d, const float* params_host, size_t n) {
+  OUU_CHECK_ARG(d && params_host, "null argument");
+  OUU_CHECK_ARG(n == d->n_params, "parameter count mismatch");
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_params, params_host, n * 4, cudaMemcpyHostToDevice, d->stream));
+  OUU_CUDA_TRY(cudaMemsetAsync(d->d_adam_m, 0, n * 4, d->stream));
+  OUU_CUDA_TRY(cudaMemsetAsync(d->d_adam_v, 0, n * 4, d->stream));
+  d->adam_t = 0;
+  refresh_bf16_weights(d);
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_get_params(ouu_dino_t d, float* params_host, size_t n) {
+  OUU_CHECK_ARG(d && params_host, "null argument");
+  OUU_CHECK_ARG(n == d->n_params, "parameter count mismatch");
+  OUU_CUDA_TRY(cudaMemcpyAsync(params_host, d->d_params, n * 4, cudaMemcpyDeviceToHost, d->stream));
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OUU_OK;
+}
+
+// Installs Phi (FP64 copy already in d_phi64) and ubar: FP32 copy, c and the constant.
+ouu_status dino_install_bases(ouu_dino* d) {
+  const int64_t cnt = (int64_t)d->ru * d->nn;
+  k_phi_to_f32<<<grid_for(cnt), 256, 0, d->stream>>>(d->d_phi64, cnt, d->d_phi);
+  k_reduced_qoi_terms<<<d->ru + 1, 256, 0, d->stream>>>(d->d_phi64, d->d_ubar, d->d_ut, d->n, d->ru, d->d_c,
+                                                         d->d_c + d->ru);
+  OUU_CUDA_TRY(cudaGetLastError());
+  std::vector<double> c(d->ru + 1);
+  OUU_CUDA_TRY(cudaMemcpyAsync(c.data(), d->d_c, (d->ru + 1) * 8, cudaMemcpyDeviceToHost, d->stream));
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  double cc = 0.0;
+  for (int r = 0; r < d->ru; ++r) cc += c[r] * c[r];
+  d->qconst = 0.5 * (c[d->ru] - cc);
+  d->bases_ready = 1;
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_set_bases(ouu_dino_t d, const double* phi_dev, const double* ubar_dev) {
+  OUU_CHECK_ARG(d && phi_dev && ubar_dev, "null argument");
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_phi64, phi_dev, (size_t)d->ru * d->nn * 8, cudaMemcpyDeviceToDevice, d->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_ubar, ubar_dev, (size_t)d->nn * 8, cudaMemcpyDeviceToDevice, d->stream));
+  return dino_install_bases(d);
+}
+
+extern "C" ouu_status ouu_dino_get_bases(ouu_dino_t d, double* phi_dev, double* ubar_dev) {
+  OUU_CHECK_ARG(d && d->bases_ready, "bases not built");
+  if (phi_dev)
+    OUU_CUDA_TRY(cudaMemcpyAsync(phi_dev, d->d_phi64, (size_t)d->ru * d->nn * 8, cudaMemcpyDeviceToDevice, d->stream));
+  if (ubar_dev)
+    OUU_CUDA_TRY(cudaMemcpyAsync(ubar_dev, d->d_ubar, (size_t)d->nn * 8, cudaMemcpyDeviceToDevice, d->stream));
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OUU_OK;
+}
+
+static ouu_status check_err(ouu_dino* d) {
+  int e = 0;
+  OUU_CUDA_TRY(cudaMemcpyAsync(&e, d->d_err, 4, cudaMemcpyDeviceToHost, d->stream));
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  if (e) {
+    cudaMemsetAsync(d->d_err, 0, 4, d->stream);
+    ouu_set_error("tensor-core GEMM pipeline wait timed out");
+    return OUU_ERR_CUDA;
+  }
+  return OUU_OK;
+}
+
+// KL coordinates of `count` fields (chunked BF16 cast + tensor-core projection).
+static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi) {
+  for (int s0 = 0; s0 < count; s0 += d->chunkE) {
+    const int cnt = std::min(d->chunkE, count - s0);
+    k_cast_fields_bf16<<<grid_for((int64_t)cnt * d->nnp), 256, 0, d->stream>>>(
+        m + (int64_t)s0 * d->nn, d->nn, d->nnp, d->desc.m_mean, cnt, d->Mbf);
+    EpiParams ep = epi(EPI_LINEAR);
+    ep.out_f32 = xi + (int64_t)s0 * d->rm;
+    ep.ld_f32 = d->rm;
+    DINO_TRY(gemm(d, d->Mbf, d->nnp, d->d_wkl, d->nnp, cnt, d->rm, d->nn, ep));
+  }
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_project_fields(ouu_dino_t d, const double* m_dev, int n_samples, float* xi_dev) {
+  OUU_CHECK_ARG(d && m_dev && xi_dev && n_samples >= 0, "bad argument");
+  if (n_samples == 0) return OUU_OK;
+  DINO_TRY(project_fields(d, m_dev, n_samples, xi_dev));
+  return check_err(d);
+}
+
+extern "C" ouu_status ouu_dino_project_states(ouu_dino_t d, const double* u_dev, int n_samples, float* y_dev) {
+  OUU_CHECK_ARG(d && u_dev && y_dev && n_samples >= 0, "bad argument");
+  OUU_CHECK_ARG(d->bases_ready, "bases not built");
+  if (n_samples == 0) return OUU_OK;
+  dim3 g((d->ru + 31) / 32, (n_samples + 31) / 32), b(32, 8);
+  k_project_states<<<g, b, 0, d->stream>>>(u_dev, d->d_ubar, d->d_phi, d->nn, d->ru, n_samples,
+                                            (float)(d->h * d->h), y_dev);
+  OUU_CUDA_TRY(cudaGetLastError());
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OUU_OK;
+}
+
+// ------------------------------------------------------------------ forward with tangents
+// Stacked forward pass for B samples (rows of xi/z/y chosen by idx): values in
+// A[1..3], HS[1..3] rows [0, B), tangents in HS rows [B, B + B dz), AD[2..3];
+// outputs phi in OUT rows [0, B) and J^T in jout (row (b, j) = d phi_b / d z_j).
+static ouu_status forward_tangent(ouu_dino* d, const float* xi, const float* z, int64_t z_stride, const int* idx,
+                                  int B, float* jout, int ld_jout, bool transposed) {
+  const int wd = d->wd, wdp = d->wd, rup = pad8(d->ru), in0p = d->inp_l[0], dz = d->dz;
+  const int R = B * dz, BR = B + R;
+  k_build_x0<<<grid_for((int64_t)B * in0p), 256, 0, d->stream>>>(xi, idx, z, z_stride, d->rm, dz, in0p, B, d->X0,
+                                                                  transposed ? d->X0T : nullptr);
+  {  // layer 0 values
+    EpiParams ep = epi(EPI_GELU);
+    ep.bias = d->d_params + d->offb[0];
+    ep.out_f32 = d->A[1];
+    ep.ld_f32 = wd;
+    ep.out_bf16 = d->HS[1];
+    ep.ld_bf16 = wdp;
+    if (transposed) {
+      ep.out_t_bf16 = d->HST[1];
+      ep.ld_t = BR;
+    }
+    DINO_TRY(gemm(d, d->X0, in0p, d->Wb[0], d->inp_l[0], B, wd, d->in0, ep));
+  }
+  k_tangent1<<<grid_for((int64_t)R * wd), 256, 0, d->stream>>>(d->A[1], d->d_params + d->offW[0], d->in0, d->rm, dz,
+                                                               wd, wdp, B, d->HS[1] + (int64_t)B * wdp);
+  if (transposed) transpose_bf16(d->HS[1] + (int64_t)B * wdp, wdp, R, wd, d->HST[1] + B, BR, d->stream);
+  for (int l = 1; l <= 2; ++l) {
+    EpiParams ev = epi(EPI_GELU);
+    ev.bias = d->d_params + d->offb[l];
+    ev.out_f32 = d->A[l + 1];
+    ev.ld_f32 = wd;
+    ev.out_bf16 = d->HS[l + 1];
+    ev.ld_bf16 = wdp;
+    if (transposed) {
+      ev.out_t_bf16 = d->HST[l + 1];
+      ev.ld_t = BR;
+    }
+    DINO_TRY(gemm(d, d->HS[l], wdp, d->Wb[l], wdp, B, wd, wd, ev));
+    EpiParams et = epi(EPI_DGELU_SCALE);
+    et.aux = d->A[l + 1];
+    et.ld_aux = wd;
+    et.aux_rdiv = dz;
+    et.out_bf16 = d->HS[l + 1] + (int64_t)B * wdp;
+    et.ld_bf16 = wdp;
+    if (transposed) {
+      et.out_t_bf16 = d->HST[l + 1] + B;
+      et.ld_t = BR;
+    }
+    et.out2_bf16 = d->AD[l + 1];
+    et.ld2 = wdp;
+    DINO_TRY(gemm(d, d->HS[l] + (int64_t)B * wdp, wdp, d->Wb[l], wdp, R, wd, wd, et));
+  }
+  {  // output layer: values and tangents
+    EpiParams ev = epi(EPI_LINEAR);
+    ev.bias = d->d_params + d->offb[3];
+    ev.out_f32 = d->OUT;
+    ev.ld_f32 = rup;
+    DINO_TRY(gemm(d, d->HS[3], wdp, d->Wb[3], wdp, B, d->ru, wd, ev));
+    EpiParams et = epi(EPI_LINEAR);
+    et.out_f32 = jout;
+    et.ld_f32 = ld_jout;
+    DINO_TRY(gemm(d, d->HS[3] + (int64_t)B * wdp, wdp, d->Wb[3], wdp, R, d->ru, wd, et));
+  }
+  return OUU_OK;
+}
+
+// Loss and gradient (into d_grad) for one minibatch.
+static ouu_status loss_and_grad(ouu_dino* d, const float* xi, const float* z, const float* y, const float* jy,
+                                const int* idx, int B) {
+  const int wd = d->wd, wdp = d->wd, rup = pad8(d->ru), dz = d->dz, ru = d->ru;
+  const int R = B * dz, BR = B + R;
+  DINO_TRY(forward_tangent(d, xi, z, dz, idx, B, d->OUT + (int64_t)B * rup, rup, true));
+  k_loss_out<<<LOSS_BLOCKS, 256, 0, d->stream>>>(d->OUT, rup, y, jy, idx, B, dz, ru, (float)d->desc.jac_weight, d->GO,
+                                                 rup, d->d_gov, d->d_loss_part);
+  k_sum_parts<<<1, 256, 0, d->stream>>>(d->d_loss_part, LOSS_BLOCKS, d->d_loss);
+  transpose_bf16(d->GO, rup, BR, ru, d->GOT, BR, d->stream);
+  float* g = d->d_grad;
+  {  // output layer: dW3 = GO^T [h3; hdot3], db3 = sum_b g_phi, GH = GO W3
+    EpiParams e = epi(EPI_LINEAR);
+    e.out_f32 = g + d->offW[3];
+    e.ld_f32 = wd;
+    DINO_TRY(gemm(d, d->GOT, BR, d->HST[3], BR, ru, wd, BR, e));
+    k_colsum<<<grid_for(ru), 256, 0, d->stream>>>(d->d_gov, B, ru, ru, g + d->offb[3]);
+    EpiParams h = epi(EPI_LINEAR);
+    h.out_f32 = d->GH;
+    h.ld_f32 = wd;
+    DINO_TRY(gemm(d, d->GO, rup, d->WTb[3], rup, BR, wd, ru, h));
+  }
+  for (int l = 3; l >= 2; --l) {   // activation l produced by weights l - 1
+    k_bwd_layer<<<grid_for((int64_t)BR * wd), 256, 0, d->stream>>>(d->GH, d->A[l], d->AD[l], wdp, nullptr, 0, 0, dz,
+                                                                   wd, B, d->GA, d->GAv);
+    transpose_bf16(d->GA, wdp, BR, wd, d->GAT, BR, d->stream);
+    EpiParams e = epi(EPI_LINEAR);
+    e.out_f32 = g + d->offW[l - 1];
+    e.ld_f32 = wd;
+    DINO_TRY(gemm(d, d->GAT, BR, d->HST[l - 1], BR, wd, wd, BR, e));
+    k_colsum<<<grid_for(wd), 256, 0, d->stream>>>(d->GAv, B, wd, wd, g + d->offb[l - 1]);
+    EpiParams h = epi(EPI_LINEAR);
+    h.out_f32 = d->GH;
+    h.ld_f32 = wd;
+    DINO_TRY(gemm(d, d->GA, wdp, d->WTb[l - 1], wdp, BR, wd, wd, h));
+  }
+  // first layer: value rows only feed dW0; the tangent term enters dW0's z columns.
+  k_bwd_layer<<<grid_for((int64_t)B * wd), 256, 0, d->stream>>>(d->GH, d->A[1], nullptr, wdp,
+                                                                d->d_params + d->offW[0], d->in0, d->rm, dz, wd, B,
+                                                                d->GA, d->GAv);
+  transpose_bf16(d->GA, wdp, B, wd, d->GA1T, B, d->stream);
+  {
+    EpiParams e = epi(EPI_LINEAR);
+    e.out_f32 = g + d->offW[0];
+    e.ld_f32 = d->in0;
+    DINO_TRY(gemm(d, d->GA1T, B, d->X0T, B, wd, d->in0, B, e));
+  }
+  k_dw0z<<<grid_for((int64_t)dz * wd), 256, 0, d->stream>>>(d->A[1], d->GH, B, dz, wd, d->rm, d->in0,
+                                                            g + d->offW[0]);
+  k_colsum<<<grid_for(wd), 256, 0, d->stream>>>(d->GAv, B, wd, wd, g + d->offb[0]);
+  OUU_CUDA_TRY(cudaGetLastError());
+  return OUU_OK;
+}
+
+static ouu_status check_batch(ouu_dino* d, const float* xi, const float* z, const float* y, const float* jy,
+                              const int32_t* idx, int batch) {
+  OUU_CHECK_ARG(d && xi && z && y && jy && idx, "null argument");
+  OUU_CHECK_ARG(batch >= 8 && batch <= d->maxB && batch % 8 == 0, "batch: multiple of 8 in [8, max_batch]");
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_train_step(ouu_dino_t d, const float* xi_dev, const float* z_dev, const float* y_dev,
+                                          const float* jy_dev, const int32_t* idx_dev, int batch, float lr,
+                                          double* loss_out) {
+  DINO_TRY(check_batch(d, xi_dev, z_dev, y_dev, jy_dev, idx_dev, batch));
+  OUU_CHECK_ARG(lr > 0 && std::isfinite(lr), "lr must be positive");
+  DINO_TRY(loss_and_grad(d, xi_dev, z_dev, y_dev, jy_dev, idx_dev, batch));
+  d->adam_t += 1;
+  const double c1 = 1.0 - std::pow(0.9, d->adam_t), c2 = 1.0 - std::pow(0.999, d->adam_t);
+  k_adam<<<grid_for((int64_t)d->n_params), 256, 0, d->stream>>>(d->d_params, d->d_grad, d->d_adam_m, d->d_adam_v,
+                                                                 (int64_t)d->n_params, lr, 0.9f, 0.999f, 1e-8f,
+                                                                 (float)c1, (float)c2);
+  refresh_bf16_weights(d);
+  OUU_CUDA_TRY(cudaGetLastError());
+  if (loss_out) {
+    OUU_CUDA_TRY(cudaMemcpyAsync(d->h_pin, d->d_loss, 8, cudaMemcpyDeviceToHost, d->stream));
+    DINO_TRY(check_err(d));
+    *loss_out = d->h_pin[0];
+  }
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_loss_grad(ouu_dino_t d, const float* xi_dev, const float* z_dev, const float* y_dev,
+                                         const float* jy_dev, const int32_t* idx_dev, int batch, float* grad_host,
+                                         double* loss_out) {
+  DINO_TRY(check_batch(d, xi_dev, z_dev, y_dev, jy_dev, idx_dev, batch));
+  DINO_TRY(loss_and_grad(d, xi_dev, z_dev, y_dev, jy_dev, idx_dev, batch));
+  if (grad_host)
+    OUU_CUDA_TRY(cudaMemcpyAsync(grad_host, d->d_grad, d->n_params * 4, cudaMemcpyDeviceToHost, d->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->h_pin, d->d_loss, 8, cudaMemcpyDeviceToHost, d->stream));
+  DINO_TRY(check_err(d));
+  if (loss_out) *loss_out = d->h_pin[0];
+  return OUU_OK;
+}
+
+// ------------------------------------------------------------------ evaluation
+// Projection, forward values, reduced QoI (Qe) and, with want_grad, per-sample
+// grad_z Q in GQe by reverse mode: seed phi + c through W3^T, GELU', ... , W0z^T.
+ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad) {
+  const int wd = d->wd, wdp = d->wd, rup = pad8(d->ru), in0p = d->inp_l[0], dz = d->dz, dzp = pad8(d->dz);
+  float* zh = (float*)d->h_pin;
+  for (int j = 0; j < dz; ++j) zh[j] = (float)z_host[j];
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)dz * 4, cudaMemcpyHostToDevice, d->stream));
+  DINO_TRY(project_fields(d, m_dev, N, d->XIe));
+  k_build_x0<<<grid_for((int64_t)N * in0p), 256, 0, d->stream>>>(d->XIe, nullptr, d->d_zf, 0, d->rm, dz, in0p, N,
+                                                                  d->X0e, nullptr);
+  __nv_bfloat16* hin = d->X0e;
+  int ldin = in0p, kin = d->in0;
+  __nv_bfloat16* hbuf[2] = {d->He0, d->He1};
+  for (int l = 0; l < 3; ++l) {
+    EpiParams e = epi(EPI_GELU);
+    e.bias = d->d_params + d->offb[l];
+    e.out_f32 = d->Ae[l + 1];
+    e.ld_f32 = wd;
+    e.out_bf16 = hbuf[l & 1];
+    e.ld_bf16 = wdp;
+    DINO_TRY(gemm(d, hin, ldin, d->Wb[l], d->inp_l[l], N, wd, kin, e));
+    hin = hbuf[l & 1];
+    ldin = wdp;
+    kin = wd;
+  }
+  {
+    EpiParams e = epi(EPI_LINEAR);
+    e.bias = d->d_params + d->offb[3];
+    e.out_f32 = d->OUTe;
+    e.ld_f32 = rup;
+    DINO_TRY(gemm(d, hin, wdp, d->Wb[3], wdp, N, d->ru, wd, e));
+  }
+  k_qoi_seed<<<(N * 32 + 255) / 256, 256, 0, d->stream>>>(d->OUTe, rup, d->d_c, d->qconst, N, d->ru, d->Qe,
+                                                           want_grad ? d->Ge : nullptr, rup);
+  if (want_grad) {
+    const __nv_bfloat16* gin = d->Ge;
+    int ldg = rup, kg = d->ru;
+    for (int l = 3; l >= 1; --l) {   // ga_l = s'(a_l) * (g W_l)
+      EpiParams e = epi(EPI_DGELU_SCALE);
+      e.aux = d->Ae[l];
+      e.ld_aux = wd;
+      e.aux_rdiv = 1;
+      e.out_bf16 = hbuf[l & 1];
+      e.ld_bf16 = wdp;
+      DINO_TRY(gemm(d, gin, ldg, d->WTb[l], d->outp_l[l], N, wd, kg, e));
+      gin = hbuf[l & 1];
+      ldg = wdp;
+      kg = wd;
+    }
+    EpiParams e = epi(EPI_LINEAR);   // grad_z Q = ga_1 W0z
+    e.out_f32 = d->GQe;
+    e.ld_f32 = dzp;
+    DINO_TRY(gemm(d, gin, wdp, d->WTb[0] + (int64_t)d->rm * d->outp_l[0], d->outp_l[0], N, dz, wd, e));
+  }
+  OUU_CUDA_TRY(cudaGetLastError());
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_samples, const double* z_host,
+                                    float* phi_dev, float* jphi_dev, double* q_dev, double* gradq_dev) {
+  OUU_CHECK_ARG(d && m_dev && z_host, "null argument");
+  OUU_CHECK_ARG(d->bases_ready, "bases not built");
+  OUU_CHECK_ARG(n_samples >= 1 && n_samples <= d->maxE, "n_samples outside [1, max_eval]");
+  const int rup = pad8(d->ru), dz = d->dz, dzp = pad8(d->dz);
+  DINO_TRY(dino_eval_core(d, m_dev, n_samples, z_host, gradq_dev != nullptr));
+  if (phi_dev)
+    k_copy_rows_f32<<<grid_for((int64_t)n_samples * d->ru), 256, 0, d->stream>>>(d->OUTe, rup, n_samples, d->ru,
+                                                                                 phi_dev, d->ru);
+  if (q_dev) OUU_CUDA_TRY(cudaMemcpyAsync(q_dev, d->Qe, (size_t)n_samples * 8, cudaMemcpyDeviceToDevice, d->stream));
+  if (gradq_dev)
+    k_f32_to_f64<<<grid_for((int64_t)n_samples * dz), 256, 0, d->stream>>>(d->GQe, dzp, n_samples, dz, gradq_dev);
+  if (jphi_dev) {
+    // forward-mode Jacobian in chunks of max_batch samples (tangent rows go straight to jphi)
+    float* zf = d->d_zf;
+    for (int s0 = 0; s0 < n_samples; s0 += d->maxB) {
+      const int cnt = std::min(d->maxB, n_samples - s0);
+      DINO_TRY(forward_tangent(d, d->XIe + (int64_t)s0 * d->rm, zf, 0, nullptr, cnt,
+                               jphi_dev + (int64_t)s0 * dz * d->ru, d->ru, false));
+    }
+  }
+  OUU_CUDA_TRY(cudaGetLastError());
+  return check_err(d);
+}
+
+void dino_weighted_grads(ouu_dino* d, const double* w, int N, int n_w, double* out) {
+  dim3 g(d->dz, n_w);
+  k_weighted_grads<<<g, 256, 0, d->stream>>>(w, d->GQe, pad8(d->dz), N, d->dz, out);
+}

@@ -1,0 +1,71 @@
+// MR-DINO (reduced-basis derivative-informed neural operator, Sec. 3.3-3.4) handle.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "ouu_internal.cuh"
+#include "tc_gemm.cuh"
+
+#define DINO_LAYERS 4   // three GELU hidden layers + linear output
+
+struct ouu_dino {
+  ouu_dino_desc desc;
+  cudaStream_t stream;
+  int n, nn, nnp, dz, rm, ru, wd, in0;
+  int maxB, maxE, R, BR;
+  double h;
+  // parameters: flat FP32 [W0, b0, W1, b1, W2, b2, W3, b3], W_l row-major [out][in]
+  int in_l[DINO_LAYERS], out_l[DINO_LAYERS], inp_l[DINO_LAYERS], outp_l[DINO_LAYERS];
+  size_t offW[DINO_LAYERS], offb[DINO_LAYERS], n_params;
+  float *d_params = nullptr, *d_grad = nullptr, *d_adam_m = nullptr, *d_adam_v = nullptr;
+  int adam_t = 0;
+  __nv_bfloat16* Wb[DINO_LAYERS] = {};    // [out][inp]
+  __nv_bfloat16* WTb[DINO_LAYERS] = {};   // [in][outp]
+  // bases
+  int bases_ready = 0;
+  float* d_phi = nullptr;          // [ru][nn] FP32, zero on the boundary
+  double* d_phi64 = nullptr;       // [ru][nn] FP64
+  double* d_ubar = nullptr;        // [nn]
+  double* d_ut = nullptr;          // [nn] target state
+  double* d_c = nullptr;           // [ru]  c = h^2 Phi^T (ubar - ut)
+  double qconst = 0.0;
+  __nv_bfloat16* d_wkl = nullptr;  // [rm][nnp] KL projection rows
+  int* d_kl_order = nullptr;       // [rm] flat mode index of each KL coordinate
+  // training buffers (batch <= maxB)
+  __nv_bfloat16 *X0 = nullptr, *X0T = nullptr;
+  float* A[4] = {};                // pre-activations a_1..a_3 (index 1..3) [maxB][wd]
+  __nv_bfloat16* HS[4] = {};       // stacked [h_l; hdot_l]  [BR][wd]   (index 1..3)
+  __nv_bfloat16* HST[4] = {};      // transposed [wd][BR]               (index 1..3)
+  __nv_bfloat16* AD[4] = {};       // tangent pre-activations [R][wd]   (index 2..3)
+  float* OUT = nullptr;            // [BR][ru]  stacked [phi; J^T]
+  __nv_bfloat16 *GO = nullptr, *GOT = nullptr;   // [BR][ru], [ru][BR]
+  float* GH = nullptr;             // [BR][wd]
+  __nv_bfloat16 *GA = nullptr, *GAT = nullptr;   // [BR][wd], [wd][BR]
+  float* GAv = nullptr;            // [maxB][wd]
+  float* d_gov = nullptr;          // [maxB][ru] FP32 gradient of the loss w.r.t. phi
+  __nv_bfloat16* GA1T = nullptr;   // [wd][maxB]
+  double* d_loss_part = nullptr;   // [256]
+  double* d_loss = nullptr;        // [2]
+  // evaluation buffers (n_samples <= maxE)
+  int chunkE = 0;
+  __nv_bfloat16* Mbf = nullptr;    // [chunkE][nnp]
+  float* XIe = nullptr;            // [maxE][rm]
+  __nv_bfloat16* X0e = nullptr;    // [maxE][in0p]
+  float* Ae[4] = {};               // [maxE][wd] (index 1..3)
+  __nv_bfloat16 *He0 = nullptr, *He1 = nullptr;   // ping-pong [maxE][wd]
+  float* OUTe = nullptr;           // [maxE][ru]
+  __nv_bfloat16* Ge = nullptr;     // [maxE][ru] seed phi + c
+  float* GQe = nullptr;            // [maxE][dz]
+  double* Qe = nullptr;            // [maxE]
+  float* d_zf = nullptr;           // [max(maxB, 1) * dz] FP32 controls of the current call
+  double* h_pin = nullptr;         // pinned host scratch
+  int* d_err = nullptr;
+};
+
+// DINO forward/backward pieces used by the C ABI (dino.cu).
+ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad);
+// Completes a basis whose FP64 Phi and ubar are in place (FP32 copy, reduced-QoI terms).
+ouu_status dino_install_bases(ouu_dino* d);
+// Sum_i w[r][i] grad_z Q_i of the last evaluation into out [n_w][d_Z] (device).
+void dino_weighted_grads(ouu_dino* d, const double* w, int N, int n_w, double* out);
+// Jacobian-data solves (pde.cu): jy[i][j][r] = h^2 Phi_r . J(u_i)^-1 g_j.
+void launch_pde_jacobian_data(const PdeArgs& a, int nslots, const float* phi, int ru, float* jy, cudaStream_t s);

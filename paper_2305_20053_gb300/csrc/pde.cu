@@ -5,6 +5,7 @@
 // slots of all resident CTAs stay in the 126 MB L2); multigrid levels of at most
 // 65 x 65 nodes live in shared memory.
 #include "ouu_internal.cuh"
+#include "dino.cuh"
 
 static __device__ void build_hierarchy(const PdeArgs& a, char* slot, unsigned char* smem, Hierarchy& H) {
   H.nlev = a.nlev;
@@ -229,4 +230,64 @@ void launch_reduce_slots_and_gradient(const char* slots, const SlotLayout& lay, 
     cudaFuncSetAttribute((const void*)k_sources_transpose_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);
   k_sources_transpose_apply<<<n_w, 256, sm, st>>>(n, L, gx, gy, gscale, s_out, grad);
+}
+
+// ------------------------------------------------------------------ Jacobian data (Sec. 3.4)
+// For each sample: one operator set-up J(u_i), then d_Z forward linearised solves
+// J w_j = g_j (MG-PCG, FP32) and their projections jy[i][j][r] = h^2 Phi_r . w_j.
+__global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1)
+    k_pde_jacobian_data(PdeArgs a, const float* __restrict__ phi, int ru, float* __restrict__ jy) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[40];
+  __shared__ int s_idx;
+  CtaCtx c{red};
+  zero_smem(smem, a.lay.smem_bytes);
+  char* slot = a.slots + (int64_t)blockIdx.x * a.lay.bytes;
+  Hierarchy H;
+  build_hierarchy(a, slot, smem, H);
+  double* E = (double*)(slot + a.lay.E);
+  float* x = (float*)(slot + a.lay.x);
+  float* p = (float*)(slot + a.lay.p);
+  float* q = (float*)(slot + a.lay.q);
+  const int n = a.n, L = a.L, dz = a.L * a.L;
+  const int64_t nn = (int64_t)n * n;
+  const float h2 = (float)(1.0 / ((double)(n - 1) * (n - 1)));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (;;) {
+    const int i = next_sample(a.counter, &s_idx);
+    if (i >= a.n_samples) break;
+    build_fine_coeffs(c, n, a.m + (int64_t)i * nn, E, H.lev[0]);
+    c.sync();
+    setup_coarse_coeffs(c, H);
+    setup_jacobian(c, H, a.rr, a.u + (int64_t)i * nn);
+    int cg_total = 0;
+    for (int j = 0; j < dz; ++j) {
+      const int jx = j % L, jyy = j / L;
+      float acc = 0.f;
+      OUU_FOR_INTERIOR(c, n, iy, ix) {
+        const float v = (float)(a.gscale * a.gx[jx * n + ix] * a.gy[jyy * n + iy]);
+        H.lev[0].b[iy * n + ix] = v;
+        acc += v * v;
+      }
+      const double bnorm = sqrt(c.sum_f(acc));
+      CgResult cg = pcg_solve(c, H, x, p, q, bnorm, a.cg_rtol, a.cg_maxit);
+      cg_total += cg.iters;
+      const float sc = h2 * (float)cg.scale;
+      for (int r = warp; r < ru; r += nwarps) {
+        const float* pr = phi + (int64_t)r * nn;
+        float s = 0.f;
+        for (int64_t k = lane; k < nn; k += 32) s += pr[k] * x[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) jy[((int64_t)i * dz + j) * ru + r] = sc * s;
+      }
+      c.sync();
+    }
+    if (threadIdx.x == 0) a.iters[3 * i + 1] = cg_total;
+    c.sync();
+  }
+}
+
+void launch_pde_jacobian_data(const PdeArgs& a, int nslots, const float* phi, int ru, float* jy, cudaStream_t s) {
+  set_smem((const void*)k_pde_jacobian_data, a.lay.smem_bytes);
+  k_pde_jacobian_data<<<nslots, OUU_SOLVER_THREADS, (size_t)a.lay.smem_bytes, s>>>(a, phi, ru, jy);
 }
