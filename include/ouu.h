@@ -190,7 +190,9 @@ ouu_status ouu_pde_solve_batch_noalloc(const ouu_problem_desc* desc, const doubl
  * accumulation; FP32 master weights and Adam moments.
  *
  * Parameter vector (FP32, flat): [W0, b0, W1, b1, W2, b2, W3, b3], W_l row-major
- * [out][in]; W0 is width x (r_m + d_Z) with the KL inputs first, W3 is r_u x width. */
+ * [out][in]; W0 is width x (r_m + d_Z) with the KL inputs first, W3 is r_u x width.
+ * The output is phi = s * (W3 h3 + b3) with the fixed scale s of
+ * ouu_dino_set_output_scale. */
 typedef struct {
   int n;              /* grid of the states (nodes per side), 2^k + 1 */
   int lattice_L;      /* d_Z = L^2 controls */
@@ -227,6 +229,12 @@ ouu_status ouu_dino_set_bases(ouu_dino_t d, const double* phi_dev, const double*
  * for the r_u largest eigenvalues, each mode's largest-magnitude entry positive.
  * eig_host (nullable): the n_states eigenvalues, descending.  Then as set_bases. */
 ouu_status ouu_dino_build_bases(ouu_dino_t d, const double* u_dev, int n_states, double* eig_host);
+/* Fixed per-mode output scale s (host FP32 [r_u], positive): the network output is
+ * phi = s * (W3 h3 + b3), a reparametrisation that lets every reduced coordinate
+ * be learned at unit scale (the loss is unchanged).  Starts at 1;
+ * ouu_dino_build_bases sets s_k = sqrt(lambda_k / n_states), the RMS of mode k. */
+ouu_status ouu_dino_set_output_scale(ouu_dino_t d, const float* s_host);
+ouu_status ouu_dino_get_output_scale(ouu_dino_t d, float* s_host);
 /* Copies the installed basis out (FP64 device, layouts as in set_bases). */
 ouu_status ouu_dino_get_bases(ouu_dino_t d, double* phi_dev, double* ubar_dev);
 

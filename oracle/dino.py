@@ -99,15 +99,19 @@ def round_bf16(x):
 
 # ----------------------------------------------------------------------------- network
 class MLP:
-    """Weights Ws[l] (out, in), biases bs[l]; layer 0 input is [xi (r_m); z (d_z)]."""
+    """Weights Ws[l] (out, in), biases bs[l]; layer 0 input is [xi (r_m); z (d_z)].
+    out_scale s (r_u,): a fixed per-mode scaling of the output layer,
+    phi = s * (W h + b), so that every reduced coordinate is learned at unit scale
+    (s_r = RMS of mode r over the training states); None means s = 1."""
 
-    def __init__(self, Ws, bs, r_m):
+    def __init__(self, Ws, bs, r_m, out_scale=None):
         self.Ws = [np.array(W, dtype=np.float64) for W in Ws]
         self.bs = [np.array(b, dtype=np.float64) for b in bs]
         self.r_m = r_m
+        self.s = None if out_scale is None else np.array(out_scale, dtype=np.float64)
 
     def copy(self):
-        return MLP(self.Ws, self.bs, self.r_m)
+        return MLP(self.Ws, self.bs, self.r_m, self.s)
 
     def forward(self, xi, z, jacobian=True, bf16=False):
         """xi (B, r_m), z (B, d_z) or (d_z,).  Returns dict with a_l, h_l, phi, and (if jacobian)
@@ -139,9 +143,10 @@ class MLP:
                     Hd = gelu_d1(a)[:, :, None] * Ad
                     st["Hd"].append(Hd)
             else:
-                st["phi"] = a
+                sc = 1.0 if self.s is None else self.s
+                st["phi"] = sc * a
                 if jacobian:
-                    st["J"] = Ad
+                    st["J"] = (sc if self.s is None else self.s[None, :, None]) * Ad
         return st
 
     def loss_and_grad(self, xi, z, y, Y, w_j=1.0):
@@ -153,6 +158,9 @@ class MLP:
         loss = (np.sum(ephi ** 2) + w_j * np.sum(eJ ** 2)) / B
         g_phi = 2.0 * ephi / B
         G_J = 2.0 * w_j * eJ / B
+        if self.s is not None:          # back through the fixed output scaling
+            g_phi = g_phi * self.s
+            G_J = G_J * self.s[None, :, None]
         nl = len(self.Ws)
         dW = [None] * nl
         db = [None] * nl

@@ -81,6 +81,8 @@ SIGNATURES = {
     "ouu_dino_set_bases": (_i, [_vp, _vp, _vp]),
     "ouu_dino_build_bases": (_i, [_vp, _vp, _i, _dp]),
     "ouu_dino_get_bases": (_i, [_vp, _vp, _vp]),
+    "ouu_dino_set_output_scale": (_i, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "ouu_dino_get_output_scale": (_i, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "ouu_dino_project_fields": (_i, [_vp, _vp, _i, _vp]),
     "ouu_dino_project_states": (_i, [_vp, _vp, _i, _vp]),
     "ouu_dino_jacobian_data": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
@@ -291,6 +293,15 @@ class Dino:
         check(load().ouu_dino_build_bases(self.handle, dev_ptr(u_dev, torch.float64), n_states,
                                           eig.ctypes.data_as(_dp)))
         return eig
+
+    def ouu_dino_set_output_scale(self, s):
+        s = np.ascontiguousarray(s, dtype=np.float32)
+        check(load().ouu_dino_set_output_scale(self.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def ouu_dino_get_output_scale(self):
+        s = np.zeros(self.desc.r_u, dtype=np.float32)
+        check(load().ouu_dino_get_output_scale(self.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return s
 
     def ouu_dino_get_bases(self, phi_dev, ubar_dev):
         import torch

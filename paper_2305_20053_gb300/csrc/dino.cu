@@ -96,7 +96,8 @@ static void transpose_bf16(const __nv_bfloat16* in, int64_t ld_in, int rows, int
 #define LOSS_BLOCKS 256
 __global__ void k_loss_out(const float* __restrict__ out, int ldo, const float* __restrict__ y,
                            const float* __restrict__ jy, const int* __restrict__ idx, int B, int dz, int ru, float wj,
-                           __nv_bfloat16* __restrict__ go, int ldgo, float* __restrict__ gov, double* part) {
+                           const float* __restrict__ oscale, __nv_bfloat16* __restrict__ go, int ldgo,
+                           float* __restrict__ gov, double* part) {
   __shared__ double red[40];
   double acc = 0.0;
   GRID_STRIDE(e, (int64_t)(B + (int64_t)B * dz) * ru) {
@@ -106,7 +107,7 @@ __global__ void k_loss_out(const float* __restrict__ out, int ldo, const float* 
     if (row < B) {
       const int64_t src = idx[row];
       ev = out[row * ldo + r] - y[src * ru + r];
-      g = 2.f * ev / B;
+      g = 2.f * ev / B * oscale[r];     // gradient w.r.t. the unscaled output W3 h3 + b3
       acc += (double)ev * ev / B;
       gov[row * ru + r] = g;
     } else {
@@ -114,7 +115,7 @@ __global__ void k_loss_out(const float* __restrict__ out, int ldo, const float* 
       const int64_t b = t / dz, j = t % dz;
       const int64_t src = idx[b];
       ev = out[row * ldo + r] - jy[(src * dz + j) * ru + r];
-      g = 2.f * wj * ev / B;
+      g = 2.f * wj * ev / B * oscale[r];
       acc += (double)wj * ev * ev / B;
     }
     go[row * ldgo + r] = __float2bfloat16(g);
@@ -206,14 +207,15 @@ __global__ void k_weight_bf16(const float* __restrict__ W, int out, int in, int 
 
 // Reduced QoI (Sec. 3.3): Q_i = 1/2 ||phi_i + c||^2 + const and the reverse-mode seed phi_i + c.
 __global__ void k_qoi_seed(const float* __restrict__ phi, int ldp, const double* __restrict__ c, double qconst, int N,
-                           int ru, double* __restrict__ Q, __nv_bfloat16* __restrict__ seed, int lds) {
+                           int ru, const float* __restrict__ oscale, double* __restrict__ Q,
+                           __nv_bfloat16* __restrict__ seed, int lds) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= N) return;
   double s = 0.0;
   for (int r = lane; r < ru; r += 32) {
     const double v = (double)phi[(int64_t)warp * ldp + r] + c[r];
     s += v * v;
-    if (seed) seed[(int64_t)warp * lds + r] = __float2bfloat16((float)v);
+    if (seed) seed[(int64_t)warp * lds + r] = __float2bfloat16((float)v * oscale[r]);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) Q[warp] = 0.5 * s + qconst;
@@ -343,7 +345,7 @@ static void free_dino(ouu_dino* d) {
   void* ptrs[] = {d->d_params, d->d_grad, d->d_adam_m, d->d_adam_v, d->d_phi, d->d_phi64, d->d_ubar, d->d_ut,
                   d->d_c, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
                   d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->Mbf, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
-                  d->Ge, d->GQe, d->Qe, d->d_zf, d->d_err, d->d_gov};
+                  d->Ge, d->GQe, d->Qe, d->d_zf, d->d_err, d->d_gov, d->d_oscale};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < 4; ++l) {
     cudaFree(d->A[l]);
@@ -428,6 +430,7 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   al((void**)&d->d_ubar, (size_t)d->nn * 8);
   al((void**)&d->d_ut, (size_t)d->nn * 8);
   al((void**)&d->d_c, (size_t)d->ru * 8 + 16);
+  al((void**)&d->d_oscale, (size_t)d->ru * 4);
   al((void**)&d->d_wkl, (size_t)d->rm * d->nnp * 2);
   al((void**)&d->d_kl_order, (size_t)d->rm * 4);
   al((void**)&d->X0, maxB * in0p * 2);
@@ -502,6 +505,8 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
       for (int ix = 0; ix < n; ++ix)
         ut[(size_t)iy * n + ix] = std::sin(M_PI * (ix / (double)(n - 1))) * std::sin(M_PI * (iy / (double)(n - 1)));
     OUU_CUDA_TRY(cudaMemcpy(d->d_ut, ut.data(), (size_t)d->nn * 8, cudaMemcpyHostToDevice));
+    std::vector<float> ones(d->ru, 1.f);
+    OUU_CUDA_TRY(cudaMemcpy(d->d_oscale, ones.data(), (size_t)d->ru * 4, cudaMemcpyHostToDevice));
   }
   OUU_CUDA_TRY(cudaDeviceSynchronize());
   *out = d;
@@ -670,10 +675,12 @@ static ouu_status forward_tangent(ouu_dino* d, const float* xi, const float* z, 
   {  // output layer: values and tangents
     EpiParams ev = epi(EPI_LINEAR);
     ev.bias = d->d_params + d->offb[3];
+    ev.col_scale = d->d_oscale;
     ev.out_f32 = d->OUT;
     ev.ld_f32 = rup;
     DINO_TRY(gemm(d, d->HS[3], wdp, d->Wb[3], wdp, B, d->ru, wd, ev));
     EpiParams et = epi(EPI_LINEAR);
+    et.col_scale = d->d_oscale;
     et.out_f32 = jout;
     et.ld_f32 = ld_jout;
     DINO_TRY(gemm(d, d->HS[3] + (int64_t)B * wdp, wdp, d->Wb[3], wdp, R, d->ru, wd, et));
@@ -687,8 +694,8 @@ static ouu_status loss_and_grad(ouu_dino* d, const float* xi, const float* z, co
   const int wd = d->wd, wdp = d->wd, rup = pad8(d->ru), dz = d->dz, ru = d->ru;
   const int R = B * dz, BR = B + R;
   DINO_TRY(forward_tangent(d, xi, z, dz, idx, B, d->OUT + (int64_t)B * rup, rup, true));
-  k_loss_out<<<LOSS_BLOCKS, 256, 0, d->stream>>>(d->OUT, rup, y, jy, idx, B, dz, ru, (float)d->desc.jac_weight, d->GO,
-                                                 rup, d->d_gov, d->d_loss_part);
+  k_loss_out<<<LOSS_BLOCKS, 256, 0, d->stream>>>(d->OUT, rup, y, jy, idx, B, dz, ru, (float)d->desc.jac_weight,
+                                                 d->d_oscale, d->GO, rup, d->d_gov, d->d_loss_part);
   k_sum_parts<<<1, 256, 0, d->stream>>>(d->d_loss_part, LOSS_BLOCKS, d->d_loss);
   transpose_bf16(d->GO, rup, BR, ru, d->GOT, BR, d->stream);
   float* g = d->d_grad;
@@ -805,11 +812,12 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
   {
     EpiParams e = epi(EPI_LINEAR);
     e.bias = d->d_params + d->offb[3];
+    e.col_scale = d->d_oscale;
     e.out_f32 = d->OUTe;
     e.ld_f32 = rup;
     DINO_TRY(gemm(d, hin, wdp, d->Wb[3], wdp, N, d->ru, wd, e));
   }
-  k_qoi_seed<<<(N * 32 + 255) / 256, 256, 0, d->stream>>>(d->OUTe, rup, d->d_c, d->qconst, N, d->ru, d->Qe,
+  k_qoi_seed<<<(N * 32 + 255) / 256, 256, 0, d->stream>>>(d->OUTe, rup, d->d_c, d->qconst, N, d->ru, d->d_oscale, d->Qe,
                                                            want_grad ? d->Ge : nullptr, rup);
   if (want_grad) {
     const __nv_bfloat16* gin = d->Ge;
@@ -864,4 +872,19 @@ extern "C" ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_sam
 void dino_weighted_grads(ouu_dino* d, const double* w, int N, int n_w, double* out) {
   dim3 g(d->dz, n_w);
   k_weighted_grads<<<g, 256, 0, d->stream>>>(w, d->GQe, pad8(d->dz), N, d->dz, out);
+}
+
+extern "C" ouu_status ouu_dino_set_output_scale(ouu_dino_t d, const float* s_host) {
+  OUU_CHECK_ARG(d && s_host, "null argument");
+  for (int r = 0; r < d->ru; ++r) OUU_CHECK_ARG(s_host[r] > 0 && std::isfinite(s_host[r]), "scales must be positive");
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_oscale, s_host, (size_t)d->ru * 4, cudaMemcpyHostToDevice, d->stream));
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_get_output_scale(ouu_dino_t d, float* s_host) {
+  OUU_CHECK_ARG(d && s_host, "null argument");
+  OUU_CUDA_TRY(cudaMemcpyAsync(s_host, d->d_oscale, (size_t)d->ru * 4, cudaMemcpyDeviceToHost, d->stream));
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OUU_OK;
 }

@@ -27,6 +27,7 @@ struct ouu_dino {
   double* d_ubar = nullptr;        // [nn]
   double* d_ut = nullptr;          // [nn] target state
   double* d_c = nullptr;           // [ru]  c = h^2 Phi^T (ubar - ut)
+  float* d_oscale = nullptr;       // [ru]  fixed output scale: phi = s * (W3 h3 + b3)
   double qconst = 0.0;
   __nv_bfloat16* d_wkl = nullptr;  // [rm][nnp] KL projection rows
   int* d_kl_order = nullptr;       // [rm] flat mode index of each KL coordinate

@@ -298,5 +298,9 @@ extern "C" ouu_status ouu_dino_build_bases(ouu_dino_t d, const double* u_dev, in
   OUU_CUDA_TRY(cudaStreamSynchronize(st));
   cudaFree(d_is);
   cleanup();
+  // output scale of the network: RMS of each kept mode over the snapshots, sqrt(lambda_k / Ns)
+  std::vector<float> sc(d->ru);
+  for (int k = 0; k < d->ru; ++k) sc[k] = (float)std::sqrt(lam[order[k]] / Ns);
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_oscale, sc.data(), (size_t)d->ru * 4, cudaMemcpyHostToDevice, st));
   return dino_install_bases(d);
 }

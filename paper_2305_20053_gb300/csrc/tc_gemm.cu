@@ -127,6 +127,7 @@ static __device__ __forceinline__ void epilogue16(const EpiParams& ep, int r, in
     float y, ob;
     if (ep.mode == EPI_LINEAR) {
       y = ep.alpha * acc + (ep.bias ? ep.bias[c] : 0.f);
+      if (ep.col_scale) y *= ep.col_scale[c];
       ob = y;
     } else if (ep.mode == EPI_GELU) {
       y = acc + (ep.bias ? ep.bias[c] : 0.f);
@@ -338,6 +339,7 @@ extern "C" ouu_status ouu_kernel_gemm_bf16(const void* A, int lda, const void* B
   ep.mode = mode;
   ep.alpha = alpha;
   ep.bias = bias;
+  ep.col_scale = nullptr;
   ep.out_f32 = out_f32;
   ep.ld_f32 = ld_f32;
   ep.accumulate = accumulate;

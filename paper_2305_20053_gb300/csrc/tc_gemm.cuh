@@ -18,6 +18,7 @@ struct EpiParams {
   int mode;
   float alpha;
   const float* bias;              // [N] or null
+  const float* col_scale;         // EPI_LINEAR: y *= col_scale[c] after the bias (null: 1)
   float* out_f32;                 // [M][ld_f32] or null
   int ld_f32;
   int accumulate;                 // out_f32 += y instead of =

@@ -37,7 +37,8 @@ def _net(seed=11):
     bs = [0.1 * random_state_like(seed + 50 + l, b.shape) for l, b in enumerate(bs)]
     flat = capi.flatten_params(Ws, bs)
     Ws64, bs64 = capi.unflatten_params(flat, widths)      # the FP32-rounded weights both sides use
-    return flat, dino.MLP(Ws64, bs64, RM), widths
+    scale = np.linspace(1.0, 0.1, RU).astype(np.float32)  # a fixed output scale, as build_bases sets one
+    return flat, dino.MLP(Ws64, bs64, RM, out_scale=scale.astype(np.float64)), widths, scale
 
 
 @pytest.fixture(scope="module")
@@ -57,9 +58,10 @@ def setup():
     phi_full[:, 1:-1, 1:-1] = Phi.T.reshape(RU, n - 2, n - 2)
     ubar_full = np.zeros((n, n))
     ubar_full[1:-1, 1:-1] = ubar.reshape(n - 2, n - 2)
-    flat, net, widths = _net()
+    flat, net, widths, scale = _net()
     D = capi.Dino(n=n, lattice_L=L, r_m=RM, r_u=RU, width=W, max_batch=16, max_eval=64)
     D.ouu_dino_set_params(flat)
+    D.ouu_dino_set_output_scale(scale)
     D.ouu_dino_set_bases(torch.tensor(phi_full, device="cuda"), torch.tensor(ubar_full, device="cuda"))
     P = capi.Problem(n=n, lattice_L=L, max_samples=64)
     return dict(prob=prob, G=G, ut=ut, ms=ms, zs=zs, states=states, U=U, Phi=Phi, ubar=ubar, ev=ev, net=net,
@@ -144,9 +146,10 @@ def test_adam_step_moves_by_lr(setup):
     about lr against the sign of its gradient (checked where the oracle gradient is large)."""
     from paper_2305_20053_gb300 import capi
     n = N_GRID
-    flat, net, widths = _net(seed=21)
+    flat, net, widths, scale = _net(seed=21)
     D2 = capi.Dino(n=n, lattice_L=L, r_m=RM, r_u=RU, width=W, max_batch=16, max_eval=16)
     D2.ouu_dino_set_params(flat)
+    D2.ouu_dino_set_output_scale(scale)
     B = 16
     xi = random_state_like(201, (B, RM)).astype(np.float32)
     z = controls(202, B, DZ).astype(np.float32)
@@ -208,6 +211,7 @@ def test_pod_build_parity(setup):
     np.testing.assert_allclose(ev[:RU], setup["ev"][:RU], rtol=1e-9)
     P = phi[:, 1:-1, 1:-1].reshape(RU, -1).T
     np.testing.assert_allclose(h * h * P.T @ P, np.eye(RU), atol=1e-12)
+    np.testing.assert_allclose(D3.ouu_dino_get_output_scale(), np.sqrt(setup["ev"][:RU] / 24), rtol=1e-6)
     gaps = np.abs(np.diff(setup["ev"][:RU + 1])) / setup["ev"][0]
     for k in range(RU):
         if min(gaps[k], gaps[k - 1] if k else 1.0) > 1e-6:

@@ -57,15 +57,17 @@ def test_gelu_derivatives():
     np.testing.assert_allclose(dino.gelu(np.array([0.0, 1.0])), [0.0, 0.8413447460685429], rtol=1e-14)
 
 
-def _small_net(r_m=3, d_z=2, widths=(5, 6, 4), r_u=3, seed=1):
+def _small_net(r_m=3, d_z=2, widths=(5, 6, 4), r_u=3, seed=1, scaled=True):
     Ws, bs = glorot_uniform_mlp([r_m + d_z, *widths, r_u], seed=seed)
     rng = np.random.default_rng(seed)
     bs = [0.1 * rng.standard_normal(b.shape) for b in bs]
-    return dino.MLP(Ws, bs, r_m)
+    s = rng.uniform(0.2, 2.0, r_u) if scaled else None
+    return dino.MLP(Ws, bs, r_m, out_scale=s)
 
 
-def test_forward_jacobian_finite_difference():
-    net = _small_net()
+@pytest.mark.parametrize("scaled", [True, False])
+def test_forward_jacobian_finite_difference(scaled):
+    net = _small_net(scaled=scaled)
     rng = np.random.default_rng(3)
     xi, z = rng.standard_normal((4, 3)), rng.uniform(-1, 1, (4, 2))
     J = net.forward(xi, z)["J"]
@@ -77,9 +79,9 @@ def test_forward_jacobian_finite_difference():
         np.testing.assert_allclose(J[:, :, j], fd, rtol=1e-7, atol=1e-9)
 
 
-@pytest.mark.parametrize("w_j", [1.0, 0.0])
-def test_loss_gradient_finite_difference(w_j):
-    net = _small_net()
+@pytest.mark.parametrize("w_j,scaled", [(1.0, True), (0.0, True), (1.0, False)])
+def test_loss_gradient_finite_difference(w_j, scaled):
+    net = _small_net(scaled=scaled)
     rng = np.random.default_rng(5)
     B = 4
     xi, z = rng.standard_normal((B, 3)), rng.uniform(-1, 1, (B, 2))
@@ -175,3 +177,17 @@ def test_bf16_rounding():
     r = dino.round_bf16(x)
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -7
     assert abs(r[3] + 3.14159) < 2 ** -7 * 4
+
+
+def test_output_scale_is_a_reparametrisation():
+    """phi = s * (W h + b) equals the unscaled net whose last layer is diag(s) W, diag(s) b."""
+    net = _small_net(scaled=True)
+    plain = net.copy()
+    plain.s = None
+    plain.Ws[-1] = net.s[:, None] * net.Ws[-1]
+    plain.bs[-1] = net.s * net.bs[-1]
+    rng = np.random.default_rng(9)
+    xi, z = rng.standard_normal((4, 3)), rng.uniform(-1, 1, (4, 2))
+    a, b = net.forward(xi, z), plain.forward(xi, z)
+    np.testing.assert_allclose(a["phi"], b["phi"], rtol=1e-13)
+    np.testing.assert_allclose(a["J"], b["J"], rtol=1e-13)
