@@ -84,11 +84,14 @@ typedef struct {
   int cg_total;                 /* inner CG iterations summed over samples and solves */
   int adjoint_solves;           /* adjoint solves performed (samples with nonzero weight) */
   int n_not_converged;
-  float ms_state;               /* device time of the batched state solve (CUDA events on the stream) */
+  float ms_state;               /* PDE: batched state solve; DINO: projection + network (CUDA events) */
   float ms_weights;             /* risk weights / t* */
   float ms_adjoint;             /* batched adjoint solve */
   float ms_reduce;              /* weighted adjoint sum and G^T */
   float ms_total;               /* whole evaluation on the device */
+  float ms_cast;                /* DINO: FP64 -> BF16 cast of the fields (single-chunk evaluations) */
+  float ms_project;             /* DINO: KL projection GEMM (single-chunk evaluations) */
+  float ms_network;             /* DINO: network forward + reverse-mode gradient */
 } ouu_eval_stats;
 
 typedef struct ouu_problem* ouu_problem_t;
@@ -268,6 +271,12 @@ ouu_status ouu_dino_loss_grad(ouu_dino_t d, const float* xi_dev, const float* z_
  * FP64 (grad_z Q by reverse mode through the network).  Synchronises. */
 ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_samples, const double* z_host, float* phi_dev,
                          float* jphi_dev, double* q_dev, double* gradq_dev);
+
+/* DINO risk evaluations in ouu_risk_and_grad are replayed from a CUDA graph that is
+ * captured (on a private stream, after one eager evaluation) for each new combination
+ * of (problem, m_dev, n_samples, n_risks); enable = 0 turns this off (every call then
+ * enqueues its kernels eagerly and reports per-phase times in ouu_eval_stats). */
+ouu_status ouu_dino_set_graphs(ouu_dino_t d, int enable);
 
 /* Thread-local message of the last failed call ("" if none).  Copies at most
  * len-1 bytes plus a terminating zero into buf; returns the full length. */

@@ -52,7 +52,8 @@ class EvalStats(ctypes.Structure):
     _fields_ = [("newton_min", ctypes.c_int), ("newton_max", ctypes.c_int), ("newton_mean", ctypes.c_double),
                 ("cg_total", ctypes.c_int), ("adjoint_solves", ctypes.c_int), ("n_not_converged", ctypes.c_int),
                 ("ms_state", ctypes.c_float), ("ms_weights", ctypes.c_float), ("ms_adjoint", ctypes.c_float),
-                ("ms_reduce", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_reduce", ctypes.c_float), ("ms_total", ctypes.c_float), ("ms_cast", ctypes.c_float),
+                ("ms_project", ctypes.c_float), ("ms_network", ctypes.c_float)]
 
 
 _vp = ctypes.c_void_p
@@ -89,6 +90,7 @@ SIGNATURES = {
     "ouu_dino_train_step": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, ctypes.c_float, _dp]),
     "ouu_dino_loss_grad": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(ctypes.c_float), _dp]),
     "ouu_dino_eval": (_i, [_vp, _vp, _i, _dp, _vp, _vp, _vp, _vp]),
+    "ouu_dino_set_graphs": (_i, [_vp, _i]),
     "ouu_kernel_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _i, _i, _vp, _i, _i,
                                   _vp, _i, _vp, _i, _vp, _i, _vp, _vp]),
     "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
@@ -302,6 +304,9 @@ class Dino:
         s = np.zeros(self.desc.r_u, dtype=np.float32)
         check(load().ouu_dino_get_output_scale(self.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
         return s
+
+    def ouu_dino_set_graphs(self, enable):
+        check(load().ouu_dino_set_graphs(self.handle, int(enable)))
 
     def ouu_dino_get_bases(self, phi_dev, ubar_dev):
         import torch

@@ -130,6 +130,7 @@ static void free_problem(ouu_problem* p) {
   cudaFree(p->d_out);
   cudaFree(p->d_risks);
   cudaFree(p->d_z);
+  cudaFree(p->d_rscr);
   cudaFreeHost(p->h_out);
   cudaFreeHost(p->h_stat);
   for (auto& e : p->ev)
@@ -219,6 +220,7 @@ extern "C" ouu_status ouu_create_problem(const ouu_problem_desc* desc, void* cud
   OUU_ALLOC(p->d_out, (size_t)(OUU_MAX_RISKS * (3 + p->dz) + 8) * 8);
   OUU_ALLOC(p->d_risks, sizeof(RiskDev) * OUU_MAX_RISKS);
   OUU_ALLOC(p->d_z, (size_t)p->dz * 8);
+  OUU_ALLOC(p->d_rscr, (size_t)OUU_RISK_SCRATCH * 8);
   if (cudaMallocHost((void**)&p->h_out, (size_t)(OUU_MAX_RISKS * (3 + p->dz) + 8) * 8) != cudaSuccess ||
       cudaMallocHost((void**)&p->h_stat, (size_t)N * 4 * 4 + 64) != cudaSuccess) {
     cudaGetLastError();
@@ -400,21 +402,63 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
       return OUU_ERR_STATE;
     }
     cudaStream_t ds = dino->stream;
-    OUU_CUDA_TRY(cudaEventRecord(p->ev[0], ds));
-    if (ouu_status st = dino_eval_core(dino, m_dev, n_samples, z_host, true)) return st;
-    OUU_CUDA_TRY(cudaEventRecord(p->ev[1], ds));
-    launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, ds);
-    OUU_CUDA_TRY(cudaEventRecord(p->ev[2], ds));
-    dino_weighted_grads(dino, p->d_w, n_samples, n_risks, d_grad);
-    OUU_CUDA_TRY(cudaEventRecord(p->ev[3], ds));
-    OUU_CUDA_TRY(cudaGetLastError());
     const size_t ob = (size_t)(OUU_MAX_RISKS * (3 + dz) + 8) * 8;
-    OUU_CUDA_TRY(cudaMemcpyAsync(p->h_out, p->d_out, ob, cudaMemcpyDeviceToHost, ds));
-    int gemm_err = 0;
-    OUU_CUDA_TRY(cudaMemcpyAsync(p->h_stat, dino->d_err, 4, cudaMemcpyDeviceToHost, ds));
+    // The evaluation as one stream-ordered sequence: projection + network + reduced QoI +
+    // reverse-mode gradient, risk weights, weighted gradient sum, results to pinned host memory.
+    auto enqueue = [&]() -> ouu_status {
+      if (ouu_status st = dino_eval_core(dino, m_dev, n_samples, z_host, true)) return st;
+      if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[1], dino->stream));
+      launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream);
+      if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[2], dino->stream));
+      dino_weighted_grads(dino, p->d_w, n_samples, n_risks, d_grad);
+      OUU_CUDA_TRY(cudaGetLastError());
+      OUU_CUDA_TRY(cudaMemcpyAsync(p->h_out, p->d_out, ob, cudaMemcpyDeviceToHost, dino->stream));
+      OUU_CUDA_TRY(cudaMemcpyAsync(p->h_stat, dino->d_err, 4, cudaMemcpyDeviceToHost, dino->stream));
+      return OUU_OK;
+    };
+    const bool replay = dino->use_graphs && dino->gexec && dino->gkey_p == p && dino->gkey_m == m_dev &&
+                        dino->gkey_N == n_samples && dino->gkey_nr == n_risks;
+    OUU_CUDA_TRY(cudaEventRecord(p->ev[0], ds));
+    if (replay) {
+      float* zh = (float*)dino->h_pin;   // the graph's copy node reads z from here
+      for (int j = 0; j < dz; ++j) zh[j] = (float)z_host[j];
+      OUU_CUDA_TRY(cudaGraphLaunch(dino->gexec, ds));
+    } else {
+      if (ouu_status st = enqueue()) return st;
+      if (dino->use_graphs) {
+        // capture the same sequence for the next calls with this (problem, fields, N, risks)
+        if (dino->gexec) {
+          cudaGraphExecDestroy(dino->gexec);
+          dino->gexec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        dino->capturing = true;
+        dino->stream = dino->cap;
+        ouu_status cst = OUU_OK;
+        if (cudaStreamBeginCapture(dino->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          cst = enqueue();
+          if (cudaStreamEndCapture(dino->cap, &g) != cudaSuccess) g = nullptr;
+        }
+        dino->stream = ds;
+        dino->capturing = false;
+        cudaGetLastError();
+        if (cst == OUU_OK && g) {
+          cudaGraphExec_t ex = nullptr;
+          if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+            dino->gexec = ex;
+            dino->gkey_p = p;
+            dino->gkey_m = m_dev;
+            dino->gkey_N = n_samples;
+            dino->gkey_nr = n_risks;
+          }
+          cudaGetLastError();
+        }
+        if (g) cudaGraphDestroy(g);
+      }
+    }
+    OUU_CUDA_TRY(cudaEventRecord(p->ev[3], ds));
     OUU_CUDA_TRY(cudaStreamSynchronize(ds));
-    gemm_err = p->h_stat[0];
-    if (gemm_err) {
+    if (p->h_stat[0]) {
       cudaMemsetAsync(dino->d_err, 0, 4, ds);
       ouu_set_error("tensor-core GEMM pipeline wait timed out");
       return OUU_ERR_CUDA;
@@ -427,10 +471,15 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
     }
     if (stats) {
       std::memset(stats, 0, sizeof(*stats));
-      cudaEventElapsedTime(&stats->ms_state, p->ev[0], p->ev[1]);
-      cudaEventElapsedTime(&stats->ms_weights, p->ev[1], p->ev[2]);
-      cudaEventElapsedTime(&stats->ms_reduce, p->ev[2], p->ev[3]);
       cudaEventElapsedTime(&stats->ms_total, p->ev[0], p->ev[3]);
+      if (!replay) {   // phase marks exist only for an eagerly enqueued evaluation
+        cudaEventElapsedTime(&stats->ms_state, p->ev[0], p->ev[1]);
+        cudaEventElapsedTime(&stats->ms_weights, p->ev[1], p->ev[2]);
+        cudaEventElapsedTime(&stats->ms_reduce, p->ev[2], p->ev[3]);
+        cudaEventElapsedTime(&stats->ms_cast, dino->ev[0], dino->ev[1]);
+        cudaEventElapsedTime(&stats->ms_project, dino->ev[1], dino->ev[2]);
+        cudaEventElapsedTime(&stats->ms_network, dino->ev[2], dino->ev[3]);
+      }
     }
     return OUU_OK;
   }
@@ -446,7 +495,7 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
   OUU_CUDA_TRY(cudaEventRecord(p->ev[0], p->stream));
   launch_pde_state(a, solver_grid(p, n_samples), p->stream);
   OUU_CUDA_TRY(cudaEventRecord(p->ev[1], p->stream));
-  launch_risk_weights(p->d_q, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->stream);
+  launch_risk_weights(p->d_q, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, p->stream);
   OUU_CUDA_TRY(cudaEventRecord(p->ev[2], p->stream));
   a.w = p->d_w;
   a.n_w = n_risks;

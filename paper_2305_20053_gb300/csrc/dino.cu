@@ -33,12 +33,42 @@ static int grid_for(int64_t total, int threads = 256) {
 }
 
 // ------------------------------------------------------------------ element-wise kernels
-__global__ void k_cast_fields_bf16(const double* __restrict__ m, int nn, int nnp, double mean, int count,
-                                   __nv_bfloat16* __restrict__ out) {
-  GRID_STRIDE(e, (int64_t)count * nnp) {
-    const int64_t s = e / nnp;
-    const int k = (int)(e - s * nnp);
-    out[e] = __float2bfloat16(k < nn ? (float)(m[s * nn + k] - mean) : 0.f);
+// double -> float -> bfloat16, both roundings to nearest even, in integer arithmetic
+// only (GB300's FP64 pipe is narrow; this keeps the cast off it).  NaN stays NaN,
+// magnitudes beyond the float range become infinities, and magnitudes below the
+// normal float range (< 1.2e-38) flush to a signed zero.
+static __device__ __forceinline__ unsigned short d2bf16_bits(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned short sign = (unsigned short)((b >> 48) & 0x8000u);
+  if (e == 0x7FF) return (unsigned short)(sign | 0x7F80u | ((b & 0xFFFFFFFFFFFFFull) ? 0x40u : 0u));
+  if (e > 1023 + 127) return (unsigned short)(sign | 0x7F80u);
+  if (e < 1023 - 126) return sign;
+  // round the 52-bit mantissa to 23 bits
+  const uint64_t mant = b & 0xFFFFFFFFFFFFFull;
+  const uint64_t rest = mant & ((1ull << 29) - 1), half = 1ull << 28;
+  uint32_t f = (uint32_t)((b >> 63) << 31) | ((uint32_t)(e - 1023 + 127) << 23) | (uint32_t)(mant >> 29);
+  if (rest > half || (rest == half && (f & 1u))) f += 1u;
+  // float -> bfloat16
+  return (unsigned short)((f + 0x7FFFu + ((f >> 16) & 1u)) >> 16);
+}
+
+// out[s][k] = bf16(m[s][k]) for k < nn, 0 up to nnp (a multiple of 8); blockIdx.y =
+// sample.  Each thread converts 8 consecutive entries (8 independent loads in flight)
+// and writes them with one 16-byte store.
+__global__ void k_cast_fields_bf16(const double* __restrict__ m, int nn, int nnp, __nv_bfloat16* __restrict__ out) {
+  const double* row = m + (int64_t)blockIdx.y * nn;
+  uint4* o = (uint4*)(out + (int64_t)blockIdx.y * nnp);
+  for (int k8 = blockIdx.x * blockDim.x + threadIdx.x; k8 < nnp / 8; k8 += gridDim.x * blockDim.x) {
+    const int k = 8 * k8;
+    double x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = k + j < nn ? row[k + j] : 0.0;
+    unsigned w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      w[j] = (unsigned)d2bf16_bits(x[2 * j]) | ((unsigned)d2bf16_bits(x[2 * j + 1]) << 16);
+    o[k8] = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -345,7 +375,7 @@ static void free_dino(ouu_dino* d) {
   void* ptrs[] = {d->d_params, d->d_grad, d->d_adam_m, d->d_adam_v, d->d_phi, d->d_phi64, d->d_ubar, d->d_ut,
                   d->d_c, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
                   d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->Mbf, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
-                  d->Ge, d->GQe, d->Qe, d->d_zf, d->d_err, d->d_gov, d->d_oscale};
+                  d->Ge, d->GQe, d->Qe, d->d_zf, d->d_err, d->d_gov, d->d_oscale, d->d_klbias};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < 4; ++l) {
     cudaFree(d->A[l]);
@@ -357,6 +387,10 @@ static void free_dino(ouu_dino* d) {
     cudaFree(d->WTb[l]);
   }
   cudaFreeHost(d->h_pin);
+  for (auto& e : d->ev)
+    if (e) cudaEventDestroy(e);
+  if (d->gexec) cudaGraphExecDestroy(d->gexec);
+  if (d->cap) cudaStreamDestroy(d->cap);
   delete d;
 }
 
@@ -383,6 +417,11 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   ouu_dino* d = new ouu_dino();
   d->desc = *desc;
   d->stream = (cudaStream_t)cuda_stream;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) d->num_sms = 148;
+  }
   d->n = n;
   d->nn = n * n;
   d->nnp = pad64(n * n);
@@ -433,6 +472,7 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   al((void**)&d->d_oscale, (size_t)d->ru * 4);
   al((void**)&d->d_wkl, (size_t)d->rm * d->nnp * 2);
   al((void**)&d->d_kl_order, (size_t)d->rm * 4);
+  al((void**)&d->d_klbias, (size_t)d->rm * 4);
   al((void**)&d->X0, maxB * in0p * 2);
   al((void**)&d->X0T, (size_t)in0p * maxB * 2);
   for (int l = 1; l <= 3; ++l) {
@@ -499,6 +539,13 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
           rows[(size_t)j * d->nnp + iy * n + ix] = __float2bfloat16((float)(sc * V[(size_t)k2 * n + iy] * V[(size_t)k1 * n + ix]));
     }
     OUU_CUDA_TRY(cudaMemcpy(d->d_wkl, rows.data(), rows.size() * 2, cudaMemcpyHostToDevice));
+    std::vector<float> klb(d->rm, 0.f);
+    for (int j = 0; j < d->rm; ++j) {
+      double s = 0.0;
+      for (int p = 0; p < d->nn; ++p) s += (double)__bfloat162float(rows[(size_t)j * d->nnp + p]);
+      klb[j] = (float)(-desc->m_mean * s);
+    }
+    OUU_CUDA_TRY(cudaMemcpy(d->d_klbias, klb.data(), (size_t)d->rm * 4, cudaMemcpyHostToDevice));
     OUU_CUDA_TRY(cudaMemcpy(d->d_kl_order, q.data(), (size_t)d->rm * 4, cudaMemcpyHostToDevice));
     std::vector<double> ut(d->nn);
     for (int iy = 0; iy < n; ++iy)
@@ -508,6 +555,8 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
     std::vector<float> ones(d->ru, 1.f);
     OUU_CUDA_TRY(cudaMemcpy(d->d_oscale, ones.data(), (size_t)d->ru * 4, cudaMemcpyHostToDevice));
   }
+  for (auto& e : d->ev) OUU_CUDA_TRY(cudaEventCreate(&e));
+  OUU_CUDA_TRY(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
   OUU_CUDA_TRY(cudaDeviceSynchronize());
   *out = d;
   return OUU_OK;
@@ -588,15 +637,26 @@ static ouu_status check_err(ouu_dino* d) {
 }
 
 // KL coordinates of `count` fields (chunked BF16 cast + tensor-core projection).
-static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi) {
+// With mark, events ev[0] / ev[1] / ev[2] bracket the first chunk's cast and GEMM.
+static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi, bool mark = false) {
   for (int s0 = 0; s0 < count; s0 += d->chunkE) {
     const int cnt = std::min(d->chunkE, count - s0);
-    k_cast_fields_bf16<<<grid_for((int64_t)cnt * d->nnp), 256, 0, d->stream>>>(
-        m + (int64_t)s0 * d->nn, d->nn, d->nnp, d->desc.m_mean, cnt, d->Mbf);
+    if (mark && s0 == 0 && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
+    {
+      dim3 g((d->nnp / 8 + 255) / 256, cnt);
+      k_cast_fields_bf16<<<g, 256, 0, d->stream>>>(m + (int64_t)s0 * d->nn, d->nn, d->nnp, d->Mbf);
+    }
+    if (mark && s0 == 0 && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[1], d->stream));
     EpiParams ep = epi(EPI_LINEAR);
     ep.out_f32 = xi + (int64_t)s0 * d->rm;
     ep.ld_f32 = d->rm;
-    DINO_TRY(gemm(d, d->Mbf, d->nnp, d->d_wkl, d->nnp, cnt, d->rm, d->nn, ep));
+    ep.bias = d->d_klbias;   // -mbar * (row sums of the projection): the prior mean leaves the cast
+    // split-K so that the long-K projection fills every SM (FP32 atomics into a zeroed output)
+    const int mt = (cnt + 127) / 128;
+    const int splits = std::max(1, std::min(16, d->num_sms / mt));   // one wave (one CTA per SM)
+    OUU_CUDA_TRY(cudaMemsetAsync(ep.out_f32, 0, (size_t)cnt * d->rm * 4, d->stream));
+    DINO_TRY(ouu_gemm_bf16(d->Mbf, d->nnp, d->d_wkl, d->nnp, cnt, d->rm, d->nn, ep, d->d_err, d->stream, splits));
+    if (mark && s0 == 0 && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
   }
   return OUU_OK;
 }
@@ -791,7 +851,7 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
   float* zh = (float*)d->h_pin;
   for (int j = 0; j < dz; ++j) zh[j] = (float)z_host[j];
   OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)dz * 4, cudaMemcpyHostToDevice, d->stream));
-  DINO_TRY(project_fields(d, m_dev, N, d->XIe));
+  DINO_TRY(project_fields(d, m_dev, N, d->XIe, true));
   k_build_x0<<<grid_for((int64_t)N * in0p), 256, 0, d->stream>>>(d->XIe, nullptr, d->d_zf, 0, d->rm, dz, in0p, N,
                                                                   d->X0e, nullptr);
   __nv_bfloat16* hin = d->X0e;
@@ -839,6 +899,7 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
     e.ld_f32 = dzp;
     DINO_TRY(gemm(d, gin, wdp, d->WTb[0] + (int64_t)d->rm * d->outp_l[0], d->outp_l[0], N, dz, wd, e));
   }
+  if (!d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[3], d->stream));
   OUU_CUDA_TRY(cudaGetLastError());
   return OUU_OK;
 }
@@ -886,5 +947,15 @@ extern "C" ouu_status ouu_dino_get_output_scale(ouu_dino_t d, float* s_host) {
   OUU_CHECK_ARG(d && s_host, "null argument");
   OUU_CUDA_TRY(cudaMemcpyAsync(s_host, d->d_oscale, (size_t)d->ru * 4, cudaMemcpyDeviceToHost, d->stream));
   OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_set_graphs(ouu_dino_t d, int enable) {
+  OUU_CHECK_ARG(d != nullptr, "null argument");
+  d->use_graphs = enable ? 1 : 0;
+  if (!enable && d->gexec) {
+    cudaGraphExecDestroy(d->gexec);
+    d->gexec = nullptr;
+  }
   return OUU_OK;
 }

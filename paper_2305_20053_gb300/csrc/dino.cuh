@@ -10,7 +10,7 @@
 struct ouu_dino {
   ouu_dino_desc desc;
   cudaStream_t stream;
-  int n, nn, nnp, dz, rm, ru, wd, in0;
+  int n, nn, nnp, dz, rm, ru, wd, in0, num_sms;
   int maxB, maxE, R, BR;
   double h;
   // parameters: flat FP32 [W0, b0, W1, b1, W2, b2, W3, b3], W_l row-major [out][in]
@@ -31,6 +31,7 @@ struct ouu_dino {
   double qconst = 0.0;
   __nv_bfloat16* d_wkl = nullptr;  // [rm][nnp] KL projection rows
   int* d_kl_order = nullptr;       // [rm] flat mode index of each KL coordinate
+  float* d_klbias = nullptr;       // [rm] -mbar * sum_p W_KL[k][p] (bias of the projection GEMM)
   // training buffers (batch <= maxB)
   __nv_bfloat16 *X0 = nullptr, *X0T = nullptr;
   float* A[4] = {};                // pre-activations a_1..a_3 (index 1..3) [maxB][wd]
@@ -60,6 +61,15 @@ struct ouu_dino {
   float* d_zf = nullptr;           // [max(maxB, 1) * dz] FP32 controls of the current call
   double* h_pin = nullptr;         // pinned host scratch
   int* d_err = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // cast | projection | network phase marks
+  // CUDA graph of the risk evaluation (captured on a private stream, replayed on `stream`)
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey_p = nullptr;
+  const double* gkey_m = nullptr;
+  int gkey_N = 0, gkey_nr = 0;
+  int use_graphs = 1;
+  bool capturing = false;
 };
 
 // DINO forward/backward pieces used by the C ABI (dino.cu).

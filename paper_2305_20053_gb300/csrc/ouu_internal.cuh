@@ -129,10 +129,12 @@ struct RiskDev {
   int t_optimal;
 };
 
-// One CTA: per-risk weights w[r][i], value[r], dt[r], t[r] from q[N].
-// out layout: value[r], dt[r], t[r] at out[3r+0..2].
+// Per-risk weights w[r][i], value[r], dt[r], t[r] from q[N] (moments on many CTAs, t*
+// selection on one, weights on many).  out layout: value[r], dt[r], t[r] at out[3r+0..2].
+// scratch: OUU_RISK_SCRATCH doubles of device memory.
+#define OUU_RISK_SCRATCH 2048
 void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w,
-                         double* out, cudaStream_t s);
+                         double* out, double* scratch, cudaStream_t s);
 
 // ------------------------------------------------------------------ fields
 void launch_sample_fields(int n, uint64_t seed, int64_t first, int count, const double* invlam,
@@ -162,6 +164,7 @@ struct ouu_problem {
   double* d_out = nullptr;    // results: [OUU_MAX_RISKS][3] + grads [OUU_MAX_RISKS][dz] + misc
   RiskDev* d_risks = nullptr;
   double* d_z = nullptr;      // [dz] shared control of the current evaluation
+  double* d_rscr = nullptr;   // [OUU_RISK_SCRATCH] risk-weight scratch
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // evaluation phase timers
   double* h_out = nullptr;    // pinned mirror of d_out
   int32_t* h_stat = nullptr;  // pinned: per-sample status/iters copy (max_samples * 4)

@@ -15,7 +15,6 @@
 
 #define GEMM_BM 128
 #define GEMM_BK 64
-#define GEMM_STAGES 4
 #define GEMM_THREADS 192
 #define GEMM_WAIT_CYCLES (1ll << 32)
 
@@ -32,15 +31,17 @@ static __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t by
 }
 
 // Wait until the phase with the given parity has completed; false after the limit.
+// The suspend-time hint lets the waiting thread sleep until the phase completes instead
+// of spinning (spinning warps would take issue slots from the MMA-issuing thread).
 static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
   for (;;) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(1000000u)
         : "memory");
     if (ok) return true;
     if (clock64() - t0 > GEMM_WAIT_CYCLES) return false;
@@ -116,41 +117,17 @@ static __device__ __forceinline__ float gelu_d1f(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
 }
 
-static __device__ __forceinline__ void epilogue16(const EpiParams& ep, int r, int c0, const uint32_t (&v)[16], int M,
-                                                  int N) {
-  if (r >= M) return;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int c = c0 + j;
-    if (c >= N) break;
-    const float acc = __uint_as_float(v[j]);
-    float y, ob;
-    if (ep.mode == EPI_LINEAR) {
-      y = ep.alpha * acc + (ep.bias ? ep.bias[c] : 0.f);
-      if (ep.col_scale) y *= ep.col_scale[c];
-      ob = y;
-    } else if (ep.mode == EPI_GELU) {
-      y = acc + (ep.bias ? ep.bias[c] : 0.f);
-      ob = gelu_f(y);
-    } else {
-      const float a = ep.aux[(size_t)(r / ep.aux_rdiv) * ep.ld_aux + c];
-      y = acc * gelu_d1f(a);
-      ob = y;
-      if (ep.out2_bf16) ep.out2_bf16[(size_t)r * ep.ld2 + c] = __float2bfloat16(acc);
-    }
-    if (ep.out_f32) {
-      float* o = ep.out_f32 + (size_t)r * ep.ld_f32 + c;
-      *o = ep.accumulate ? *o + y : y;
-    }
-    if (ep.out_bf16) ep.out_bf16[(size_t)r * ep.ld_bf16 + c] = __float2bfloat16(ob);
-    if (ep.out_t_bf16) ep.out_t_bf16[(size_t)c * ep.ld_t + r] = __float2bfloat16(ob);
-  }
-}
+// Pipeline depth: four stages, five for the widest tiles (long-K projections, one CTA per SM).
+template <int BN>
+struct GemmStages {
+  static constexpr int value = BN > 128 ? 5 : 4;
+};
 
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N, int K,
                 EpiParams ep, int* err) {
+  constexpr int GEMM_STAGES = GemmStages<BN>::value;
   constexpr uint32_t A_BYTES = GEMM_BM * GEMM_BK * 2;
   constexpr uint32_t B_BYTES = BN * GEMM_BK * 2;
   constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
@@ -168,7 +145,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * GEMM_BM, n0 = blockIdx.x * BN;
-  const int KB = (K + GEMM_BK - 1) / GEMM_BK;
+  // split-K: CTA z owns K blocks [kb_lo, kb_lo + KB)
+  const int KB_all = (K + GEMM_BK - 1) / GEMM_BK;
+  const int per = (KB_all + gridDim.z - 1) / gridDim.z;
+  const int kb_lo = blockIdx.z * per;
+  const int KB = max(0, min(KB_all, kb_lo + per) - kb_lo);
+  const bool splitk = gridDim.z > 1;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -197,8 +179,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           break;
         }
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-        tma_load_2d(sa + s * A_BYTES, &ta, kb * GEMM_BK, m0, &full[s]);
-        tma_load_2d(sb + s * B_BYTES, &tb, kb * GEMM_BK, n0, &full[s]);
+        tma_load_2d(sa + s * A_BYTES, &ta, (kb_lo + kb) * GEMM_BK, m0, &full[s]);
+        tma_load_2d(sb + s * B_BYTES, &tb, (kb_lo + kb) * GEMM_BK, n0, &full[s]);
         issued = kb + 1;
       }
       // Drain: the last copy issued into every stage must have landed before exit.
@@ -226,22 +208,109 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       tc_commit(tfull);   // completes once every MMA issued above has finished
     }
   } else {
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0) ? 1 : 0) && KB > 0;
+    // Epilogue A (warps 2..5): TMEM -> shared staging tile, one accumulator row per thread
+    // (warp w may read TMEM lanes 32 (w % 4) .. +31).  The pipeline buffers are free once
+    // every MMA has completed.
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0) ? 1 : 0);
     tc_fence_after();
-    if (ok) {
-      const int q = warp & 3;   // TMEM lane quarter this warp may read
-      const int r = m0 + q * 32 + lane;
+    const int q = warp & 3;
+    float* stage = (float*)smem;
+    constexpr int SROW = BN + 1;
+    if (!ok && lane == 0) s_fail = 1;
+    if (ok && KB > 0) {
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (!s_fail) epilogue16(ep, r, n0 + c0, v, M, N);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) stage[(q * 32 + lane) * SROW + c0 + j] = __uint_as_float(v[j]);
       }
-    } else if (lane == 0) {
-      s_fail = 1;
+    } else if (ok) {   // empty K range (split-K remainder): contributes zero
+      for (int c = 0; c < BN; ++c) stage[(q * 32 + lane) * SROW + c] = 0.f;
     }
   }
   tc_fence_before();
+  __syncthreads();   // staging tile complete; producer and MMA roles are done
+  {
+    // Epilogue B (all 6 warps): lanes over columns, rows dealt to warps, four rows per step
+    // so that their loads are in flight together; row-major outputs are written coalesced.
+    constexpr int SROW = BN + 1;
+    constexpr int NC = (BN + 31) / 32;
+    constexpr int NW = GEMM_THREADS / 32;
+    float* stage = (float*)smem;
+    const bool run = !s_fail;
+    const float* __restrict__ bias = ep.bias;
+    const float* __restrict__ cscale = ep.col_scale;
+    const float* __restrict__ aux = ep.aux;
+    float* __restrict__ of = ep.out_f32;
+    __nv_bfloat16* __restrict__ ob16 = ep.out_bf16;
+    __nv_bfloat16* __restrict__ o2 = ep.out2_bf16;
+    const int mode = ep.mode;
+    float bcol[NC], scol[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const int cc = lane + 32 * k, c = n0 + cc;
+      const bool in = cc < BN && c < N;
+      bcol[k] = (in && bias && (!splitk || blockIdx.z == 0)) ? bias[c] : 0.f;
+      scol[k] = (in && cscale) ? cscale[c] : 1.f;
+    }
+    if (run) {
+      for (int t0 = warp; t0 < GEMM_BM; t0 += 4 * NW) {
+        float accv[4][NC], auxv[4][NC];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int tr = t0 + u * NW, r = m0 + tr;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            const int cc = lane + 32 * k, c = n0 + cc;
+            const bool in = tr < GEMM_BM && cc < BN && c < N && r < M;
+            accv[u][k] = in ? stage[tr * SROW + cc] : 0.f;
+            auxv[u][k] = (in && mode == EPI_DGELU_SCALE) ? aux[(size_t)(r / ep.aux_rdiv) * ep.ld_aux + c] : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int tr = t0 + u * NW, r = m0 + tr;
+          if (tr >= GEMM_BM || r >= M) break;
+          float* orow = of ? of + (size_t)r * ep.ld_f32 : nullptr;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            const int cc = lane + 32 * k, c = n0 + cc;
+            if (cc >= BN || c >= N) break;
+            const float acc = accv[u][k];
+            float y, obv;
+            if (splitk) {
+              atomicAdd(orow + c, ep.alpha * acc + bcol[k]);
+              continue;
+            }
+            if (mode == EPI_LINEAR) {
+              y = (ep.alpha * acc + bcol[k]) * scol[k];
+              obv = y;
+            } else if (mode == EPI_GELU) {
+              y = acc + bcol[k];
+              obv = gelu_f(y);
+            } else {
+              y = acc * gelu_d1f(auxv[u][k]);
+              obv = y;
+            }
+            if (orow) orow[c] = ep.accumulate ? orow[c] + y : y;
+            if (ob16) ob16[(size_t)r * ep.ld_bf16 + c] = __float2bfloat16(obv);
+            if (o2) o2[(size_t)r * ep.ld2 + c] = __float2bfloat16(acc);
+            if (ep.out_t_bf16) stage[tr * SROW + cc] = obv;
+          }
+        }
+      }
+    }
+    if (ep.out_t_bf16 && !splitk) {
+      // Epilogue C (all warps): transposed output, consecutive threads on consecutive rows.
+      __syncthreads();
+      if (run)
+        for (int e = threadIdx.x; e < GEMM_BM * BN; e += GEMM_THREADS) {
+          const int tr = e % GEMM_BM, cc = e / GEMM_BM, r = m0 + tr, c = n0 + cc;
+          if (r < M && c < N) ep.out_t_bf16[(size_t)c * ep.ld_t + r] = __float2bfloat16(stage[tr * SROW + cc]);
+        }
+    }
+  }
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
@@ -282,7 +351,10 @@ bool ouu_tmap_bf16(CUtensorMap* map, const void* base, uint64_t k, uint64_t rows
 
 template <int BN>
 static ouu_status launch_bn(const CUtensorMap& ta, const __nv_bfloat16* B, int ldb, int M, int N, int K,
-                            const EpiParams& ep, int* err, cudaStream_t s) {
+                            const EpiParams& ep, int* err, cudaStream_t s, int splits) {
+  constexpr int GEMM_STAGES = GemmStages<BN>::value;
+  static_assert((size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) >= (size_t)GEMM_BM * (BN + 1) * 4,
+                "the pipeline buffers must hold the epilogue staging tile");
   CUtensorMap tb;
   if (!ouu_tmap_bf16(&tb, B, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, BN)) {
     ouu_set_error("tensor map for GEMM operand B failed (alignment or driver entry point)");
@@ -290,19 +362,27 @@ static ouu_status launch_bn(const CUtensorMap& ta, const __nv_bfloat16* B, int l
   }
   const size_t smem = 1024 + (size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) +
                       (2 * GEMM_STAGES + 1) * 8 + 16;
-  cudaFuncSetAttribute((const void*)k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((N + BN - 1) / BN, (M + GEMM_BM - 1) / GEMM_BM);
+  static bool attr_set = false;   // one device per process is the supported set-up
+  if (!attr_set) {
+    cudaFuncSetAttribute((const void*)k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  dim3 grid((N + BN - 1) / BN, (M + GEMM_BM - 1) / GEMM_BM, splits);
   k_gemm_bf16<BN><<<grid, GEMM_THREADS, smem, s>>>(ta, tb, M, N, K, ep, err);
   OUU_CUDA_TRY(cudaGetLastError());
   return OUU_OK;
 }
 
 ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
-                         const EpiParams& ep, int* err, cudaStream_t s) {
+                         const EpiParams& ep, int* err, cudaStream_t s, int splits) {
   OUU_CHECK_ARG(M >= 1 && N >= 1 && K >= 1, "GEMM sizes must be positive");
   OUU_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0, "GEMM operands must be 16-byte aligned");
   OUU_CHECK_ARG(lda % 8 == 0 && ldb % 8 == 0 && lda >= K && ldb >= K, "GEMM leading dimensions: multiple of 8, >= K");
   OUU_CHECK_ARG(ep.mode != EPI_DGELU_SCALE || (ep.aux && ep.aux_rdiv >= 1), "EPI_DGELU_SCALE needs aux");
+  OUU_CHECK_ARG(splits >= 1 && splits <= 64, "split-K factor in [1, 64]");
+  OUU_CHECK_ARG(splits == 1 || (ep.mode == EPI_LINEAR && ep.out_f32 && !ep.out_bf16 && !ep.out_t_bf16 &&
+                                !ep.out2_bf16 && !ep.col_scale && !ep.accumulate),
+                "split-K supports one FP32 output of EPI_LINEAR, accumulated into a zeroed buffer");
   CUtensorMap ta;
   if (!ouu_tmap_bf16(&ta, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda, GEMM_BM)) {
     ouu_set_error("tensor map for GEMM operand A failed (alignment or driver entry point)");
@@ -320,12 +400,12 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
     }
   }
   switch (best) {
-    case 256: return launch_bn<256>(ta, B, ldb, M, N, K, ep, err, s);
-    case 208: return launch_bn<208>(ta, B, ldb, M, N, K, ep, err, s);
-    case 128: return launch_bn<128>(ta, B, ldb, M, N, K, ep, err, s);
-    case 112: return launch_bn<112>(ta, B, ldb, M, N, K, ep, err, s);
-    case 80: return launch_bn<80>(ta, B, ldb, M, N, K, ep, err, s);
-    default: return launch_bn<64>(ta, B, ldb, M, N, K, ep, err, s);
+    case 256: return launch_bn<256>(ta, B, ldb, M, N, K, ep, err, s, splits);
+    case 208: return launch_bn<208>(ta, B, ldb, M, N, K, ep, err, s, splits);
+    case 128: return launch_bn<128>(ta, B, ldb, M, N, K, ep, err, s, splits);
+    case 112: return launch_bn<112>(ta, B, ldb, M, N, K, ep, err, s, splits);
+    case 80: return launch_bn<80>(ta, B, ldb, M, N, K, ep, err, s, splits);
+    default: return launch_bn<64>(ta, B, ldb, M, N, K, ep, err, s, splits);
   }
 }
 
@@ -354,5 +434,5 @@ extern "C" ouu_status ouu_kernel_gemm_bf16(const void* A, int lda, const void* B
   ep.aux_rdiv = aux_rdiv;
   OUU_CHECK_ARG(err_dev != nullptr, "err_dev is required");
   return ouu_gemm_bf16((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)B, ldb, M, N, K, ep, err_dev,
-                       (cudaStream_t)stream);
+                       (cudaStream_t)stream, 1);
 }

@@ -38,7 +38,9 @@ struct EpiParams {
 // (base must be 16-byte aligned and ld a multiple of 8).
 bool ouu_tmap_bf16(CUtensorMap* map, const void* base, uint64_t k, uint64_t rows, uint64_t ld, uint32_t box_rows);
 
-// Launch D = A B^T with A = [M][K] (lda), B = [N][K] (ldb), both BF16 row-major.
-// bn: N tile (64, 128 or 256).  err: device int set non-zero when a wait times out.
+// Launch D = A B^T with A = [M][K] (lda), B = [N][K] (ldb), both BF16 row-major; the N
+// tile is chosen for the least padding.  err: device int set non-zero when a wait times
+// out.  splits > 1: split-K over gridDim.z; only for one FP32 EPI_LINEAR output, which the
+// CTAs accumulate atomically and which must be zeroed beforehand.
 ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
-                         const EpiParams& ep, int* err, cudaStream_t s);
+                         const EpiParams& ep, int* err, cudaStream_t s, int splits = 1);

@@ -239,3 +239,21 @@ def test_dino_risk_path(setup):
     v1, g1, _, _ = risk.cvar(Q, gQ, 0.9, 1e-4)
     assert abs(val[0] - v0) <= 1e-3 * abs(v0) and rel(grad[0], g0) <= 1e-2
     assert abs(val[1] - v1) <= 1e-3 * abs(v1) and rel(grad[1], g1) <= 2e-2
+
+
+def test_graph_replay_matches_eager(setup):
+    """The captured graph of the DINO risk evaluation gives the eager results, also after z changes."""
+    from paper_2305_20053_gb300 import capi
+    D, P, n, N = setup["D"], setup["P"], N_GRID, 40
+    m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
+    P.ouu_sample_fields(SEED_SAA, 0, N, m)
+    risks = [capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0),
+             capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.9, eps=1e-4, t_optimal=1)]
+    zs = controls(SEED_EVAL_Z + 7, 3, DZ)
+    D.ouu_dino_set_graphs(0)
+    eager = [P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)[:2] for z in zs]
+    D.ouu_dino_set_graphs(1)
+    graphed = [P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)[:2] for z in zs]   # capture, replay, replay
+    for (v0, g0), (v1, g1) in zip(eager, graphed):
+        np.testing.assert_array_equal(v0, v1)
+        np.testing.assert_array_equal(g0, g1)
