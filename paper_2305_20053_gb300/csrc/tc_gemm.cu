@@ -117,11 +117,94 @@ static __device__ __forceinline__ float gelu_d1f(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
 }
 
-// Pipeline depth: four stages, five for the widest tiles (long-K projections, one CTA per SM).
+// Pipeline depth: four stages; five for the wide tiles of long-K projections (one CTA per
+// SM) where five still fit in 227 KB of shared memory (BN = 208: 210 KB; BN = 256 would need 240).
 template <int BN>
 struct GemmStages {
-  static constexpr int value = BN > 128 ? 5 : 4;
+  static constexpr int value = (BN > 128 && 5 * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) <= 216 * 1024) ? 5 : 4;
 };
+
+// Epilogue B: one pass over the staged tile in quads of four consecutive columns,
+// consecutive threads on consecutive quads of a row (16-byte shared loads, 16-byte FP32
+// and 8-byte BF16 global stores when ep.vec).  One compact loop per mode keeps the code
+// that every CTA runs once small.  MODE 3 = split-K partial sums, added atomically.
+template <int BN, int MODE>
+static __device__ __forceinline__ void epi_quads(float* stage, const float* sbias, const float* sscale, int m0,
+                                                 int n0, int M, int N, const EpiParams& ep, bool keep) {
+  constexpr int SROW = BN + 4, QPR = BN / 4;
+  const bool vec = ep.vec != 0;
+  const float alpha = ep.alpha;
+#pragma unroll 2
+  for (int e = threadIdx.x; e < GEMM_BM * QPR; e += GEMM_THREADS) {
+    const int tr = e / QPR, cc = (e - tr * QPR) * 4, r = m0 + tr, c = n0 + cc;
+    if (r >= M || c >= N) continue;
+    const int nv = min(4, N - c);
+    const bool full = vec && nv == 4;
+    float* sp = stage + tr * SROW + cc;
+    const float4 a4 = *reinterpret_cast<const float4*>(sp);
+    const float acc[4] = {a4.x, a4.y, a4.z, a4.w};
+    float y[4], o[4];
+    if (MODE == EPI_DGELU_SCALE) {
+      const float* ap = ep.aux + (size_t)(r / ep.aux_rdiv) * ep.ld_aux + c;
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      if (full) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(ap));
+        x[0] = t.x, x[1] = t.y, x[2] = t.z, x[3] = t.w;
+      } else {
+        for (int j = 0; j < nv; ++j) x[j] = ap[j];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j] = y[j] = acc[j] * gelu_d1f(x[j]);
+    } else if (MODE == EPI_GELU) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        y[j] = acc[j] + sbias[cc + j];
+        o[j] = gelu_f(y[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j] = y[j] = (alpha * acc[j] + sbias[cc + j]) * sscale[cc + j];
+    }
+    float* of = ep.out_f32 ? ep.out_f32 + (size_t)r * ep.ld_f32 + c : nullptr;
+    if (MODE == 3) {
+      if (full) {
+        atomicAdd(reinterpret_cast<float4*>(of), make_float4(y[0], y[1], y[2], y[3]));
+      } else {
+        for (int j = 0; j < nv; ++j) atomicAdd(of + j, y[j]);
+      }
+      continue;
+    }
+    __nv_bfloat16* ob = ep.out_bf16 ? ep.out_bf16 + (size_t)r * ep.ld_bf16 + c : nullptr;
+    __nv_bfloat16* o2 = ep.out2_bf16 ? ep.out2_bf16 + (size_t)r * ep.ld2 + c : nullptr;
+    if (full) {
+      if (of) {
+        float4 v = make_float4(y[0], y[1], y[2], y[3]);
+        if (ep.accumulate) {
+          const float4 old = *reinterpret_cast<const float4*>(of);
+          v.x += old.x, v.y += old.y, v.z += old.z, v.w += old.w;
+        }
+        *reinterpret_cast<float4*>(of) = v;
+      }
+      if (ob) {
+        const __nv_bfloat162 p0 = __floats2bfloat162_rn(o[0], o[1]), p1 = __floats2bfloat162_rn(o[2], o[3]);
+        *reinterpret_cast<uint2*>(ob) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+      }
+      if (o2) {
+        const __nv_bfloat162 p0 = __floats2bfloat162_rn(acc[0], acc[1]), p1 = __floats2bfloat162_rn(acc[2], acc[3]);
+        *reinterpret_cast<uint2*>(o2) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+      }
+    } else {
+      for (int j = 0; j < nv; ++j) {
+        if (of) of[j] = ep.accumulate ? of[j] + y[j] : y[j];
+        if (ob) ob[j] = __float2bfloat16(o[j]);
+        if (o2) o2[j] = __float2bfloat16(acc[j]);
+      }
+    }
+    if (keep) *reinterpret_cast<float4*>(sp) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+}
 
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
@@ -142,6 +225,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint64_t* tfull = empty + GEMM_STAGES;
   uint32_t* tslot = (uint32_t*)(tfull + 1);
   __shared__ volatile int s_fail;
+  __shared__ __align__(16) float s_bias[BN], s_scale[BN];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * GEMM_BM, n0 = blockIdx.x * BN;
@@ -163,6 +247,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tslot, TMEM_COLS);
+  for (int i = threadIdx.x; i < BN; i += GEMM_THREADS) {   // per-column epilogue constants
+    const int c = n0 + i;
+    s_bias[i] = (c < N && ep.bias && blockIdx.z == 0) ? ep.bias[c] : 0.f;
+    s_scale[i] = (c < N && ep.col_scale) ? ep.col_scale[c] : 1.f;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -214,8 +303,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0) ? 1 : 0);
     tc_fence_after();
     const int q = warp & 3;
+    // Row stride BN + 4 floats (4 x an odd number): the 16-byte stores of eight
+    // consecutive rows fall in distinct bank groups.
     float* stage = (float*)smem;
-    constexpr int SROW = BN + 1;
+    constexpr int SROW = BN + 4;
+    float4* srow = reinterpret_cast<float4*>(stage + (q * 32 + lane) * SROW);
     if (!ok && lane == 0) s_fail = 1;
     if (ok && KB > 0) {
 #pragma unroll 1
@@ -223,83 +315,30 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         uint32_t v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) stage[(q * 32 + lane) * SROW + c0 + j] = __uint_as_float(v[j]);
+        for (int j = 0; j < 16; j += 4)
+          srow[(c0 + j) >> 2] = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                            __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
       }
     } else if (ok) {   // empty K range (split-K remainder): contributes zero
-      for (int c = 0; c < BN; ++c) stage[(q * 32 + lane) * SROW + c] = 0.f;
+      for (int c = 0; c < BN; c += 4) srow[c >> 2] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   tc_fence_before();
   __syncthreads();   // staging tile complete; producer and MMA roles are done
   {
-    // Epilogue B (all 6 warps): lanes over columns, rows dealt to warps, four rows per step
-    // so that their loads are in flight together; row-major outputs are written coalesced.
-    constexpr int SROW = BN + 1;
-    constexpr int NC = (BN + 31) / 32;
-    constexpr int NW = GEMM_THREADS / 32;
+    constexpr int SROW = BN + 4;
     float* stage = (float*)smem;
     const bool run = !s_fail;
-    const float* __restrict__ bias = ep.bias;
-    const float* __restrict__ cscale = ep.col_scale;
-    const float* __restrict__ aux = ep.aux;
-    float* __restrict__ of = ep.out_f32;
-    __nv_bfloat16* __restrict__ ob16 = ep.out_bf16;
-    __nv_bfloat16* __restrict__ o2 = ep.out2_bf16;
-    const int mode = ep.mode;
-    float bcol[NC], scol[NC];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const int cc = lane + 32 * k, c = n0 + cc;
-      const bool in = cc < BN && c < N;
-      bcol[k] = (in && bias && (!splitk || blockIdx.z == 0)) ? bias[c] : 0.f;
-      scol[k] = (in && cscale) ? cscale[c] : 1.f;
-    }
+    const bool keep = ep.out_t_bf16 != nullptr && !splitk;
     if (run) {
-      for (int t0 = warp; t0 < GEMM_BM; t0 += 4 * NW) {
-        float accv[4][NC], auxv[4][NC];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int tr = t0 + u * NW, r = m0 + tr;
-#pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            const int cc = lane + 32 * k, c = n0 + cc;
-            const bool in = tr < GEMM_BM && cc < BN && c < N && r < M;
-            accv[u][k] = in ? stage[tr * SROW + cc] : 0.f;
-            auxv[u][k] = (in && mode == EPI_DGELU_SCALE) ? aux[(size_t)(r / ep.aux_rdiv) * ep.ld_aux + c] : 0.f;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int tr = t0 + u * NW, r = m0 + tr;
-          if (tr >= GEMM_BM || r >= M) break;
-          float* orow = of ? of + (size_t)r * ep.ld_f32 : nullptr;
-#pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            const int cc = lane + 32 * k, c = n0 + cc;
-            if (cc >= BN || c >= N) break;
-            const float acc = accv[u][k];
-            float y, obv;
-            if (splitk) {
-              atomicAdd(orow + c, ep.alpha * acc + bcol[k]);
-              continue;
-            }
-            if (mode == EPI_LINEAR) {
-              y = (ep.alpha * acc + bcol[k]) * scol[k];
-              obv = y;
-            } else if (mode == EPI_GELU) {
-              y = acc + bcol[k];
-              obv = gelu_f(y);
-            } else {
-              y = acc * gelu_d1f(auxv[u][k]);
-              obv = y;
-            }
-            if (orow) orow[c] = ep.accumulate ? orow[c] + y : y;
-            if (ob16) ob16[(size_t)r * ep.ld_bf16 + c] = __float2bfloat16(obv);
-            if (o2) o2[(size_t)r * ep.ld2 + c] = __float2bfloat16(acc);
-            if (ep.out_t_bf16) stage[tr * SROW + cc] = obv;
-          }
-        }
-      }
+      if (splitk)
+        epi_quads<BN, 3>(stage, s_bias, s_scale, m0, n0, M, N, ep, false);
+      else if (ep.mode == EPI_LINEAR)
+        epi_quads<BN, EPI_LINEAR>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
+      else if (ep.mode == EPI_GELU)
+        epi_quads<BN, EPI_GELU>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
+      else
+        epi_quads<BN, EPI_DGELU_SCALE>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
     }
     if (ep.out_t_bf16 && !splitk) {
       // Epilogue C (all warps): transposed output, consecutive threads on consecutive rows.
@@ -353,7 +392,7 @@ template <int BN>
 static ouu_status launch_bn(const CUtensorMap& ta, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                             const EpiParams& ep, int* err, cudaStream_t s, int splits) {
   constexpr int GEMM_STAGES = GemmStages<BN>::value;
-  static_assert((size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) >= (size_t)GEMM_BM * (BN + 1) * 4,
+  static_assert((size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) >= (size_t)GEMM_BM * (BN + 4) * 4,
                 "the pipeline buffers must hold the epilogue staging tile");
   CUtensorMap tb;
   if (!ouu_tmap_bf16(&tb, B, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, BN)) {
@@ -383,6 +422,12 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   OUU_CHECK_ARG(splits == 1 || (ep.mode == EPI_LINEAR && ep.out_f32 && !ep.out_bf16 && !ep.out_t_bf16 &&
                                 !ep.out2_bf16 && !ep.col_scale && !ep.accumulate),
                 "split-K supports one FP32 output of EPI_LINEAR, accumulated into a zeroed buffer");
+  // 16-byte FP32 / 8-byte BF16 epilogue accesses need aligned bases and leading dimensions
+  // that are multiples of four elements; otherwise every element is stored on its own.
+  auto al = [](const void* q, uintptr_t a, int ld) { return q == nullptr || (((uintptr_t)q % a) == 0 && ld % 4 == 0); };
+  EpiParams e2 = ep;
+  e2.vec = al(ep.out_f32, 16, ep.ld_f32) && al(ep.out_bf16, 8, ep.ld_bf16) && al(ep.out2_bf16, 8, ep.ld2) &&
+           (ep.mode != EPI_DGELU_SCALE || al(ep.aux, 16, ep.ld_aux));
   CUtensorMap ta;
   if (!ouu_tmap_bf16(&ta, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda, GEMM_BM)) {
     ouu_set_error("tensor map for GEMM operand A failed (alignment or driver entry point)");
@@ -400,12 +445,12 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
     }
   }
   switch (best) {
-    case 256: return launch_bn<256>(ta, B, ldb, M, N, K, ep, err, s, splits);
-    case 208: return launch_bn<208>(ta, B, ldb, M, N, K, ep, err, s, splits);
-    case 128: return launch_bn<128>(ta, B, ldb, M, N, K, ep, err, s, splits);
-    case 112: return launch_bn<112>(ta, B, ldb, M, N, K, ep, err, s, splits);
-    case 80: return launch_bn<80>(ta, B, ldb, M, N, K, ep, err, s, splits);
-    default: return launch_bn<64>(ta, B, ldb, M, N, K, ep, err, s, splits);
+    case 256: return launch_bn<256>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    case 208: return launch_bn<208>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    case 128: return launch_bn<128>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    case 112: return launch_bn<112>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    case 80: return launch_bn<80>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    default: return launch_bn<64>(ta, B, ldb, M, N, K, e2, err, s, splits);
   }
 }
 

@@ -31,6 +31,7 @@ struct EpiParams {
   const float* aux;               // pre-activations for gelu' (EPI_DGELU_SCALE)
   int ld_aux;
   int aux_rdiv;
+  int vec;                        // set by ouu_gemm_bf16: vector epilogue accesses are aligned
 };
 
 // Tensor map of a row-major BF16 matrix [rows][ld] (K = inner, contiguous), box 64 x box_rows.
