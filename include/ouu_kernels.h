@@ -14,7 +14,14 @@
  * (overwritten, or incremented when accumulate != 0), out_bf16 [M][ld_bf16],
  * out_t_bf16 transposed [N][ld_t], out2_bf16 [M][ld2].  err_dev: device int set
  * to 1 if a pipeline wait timed out (the kernel then returns without hanging).
- * Launches on `stream`; returns INVALID_ARG for bad sizes/alignment. */
+ * Launches on `stream`; returns INVALID_ARG for bad sizes/alignment.
+ *
+ * ouu_kernel_kl_project: the fused KL projection of Sec. 3.3's input reduction,
+ *   xi[s][c] = bias[c] + sum_k bf16(m[s][k]) W[c][k],   s < N, c < rm, k < nn,
+ * reading the FP64 fields m [N][nn] (device, 16-byte aligned, row-major) once; the
+ * rounding to BF16 goes through FP32 (both to nearest even).  W: device BF16
+ * [rm][ldw] (ldw a multiple of 8, >= nn).  bias: device FP32 [rm].  xi: device FP32
+ * [N][rm], overwritten.  rm <= 240.  err_dev as above. */
 #ifndef OUU_KERNELS_H
 #define OUU_KERNELS_H
 
@@ -28,6 +35,9 @@ ouu_status ouu_kernel_gemm_bf16(const void* A, int lda, const void* B, int ldb, 
                                 float alpha, const float* bias, const float* aux, int ld_aux, int aux_rdiv,
                                 float* out_f32, int ld_f32, int accumulate, void* out_bf16, int ld_bf16,
                                 void* out_t_bf16, int ld_t, void* out2_bf16, int ld2, int* err_dev, void* stream);
+
+ouu_status ouu_kernel_kl_project(const double* m, int N, int nn, const void* W, int ldw, int rm, const float* bias,
+                                 float* xi, int* err_dev, void* stream);
 
 #ifdef __cplusplus
 }

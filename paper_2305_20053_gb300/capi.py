@@ -93,6 +93,7 @@ SIGNATURES = {
     "ouu_dino_set_graphs": (_i, [_vp, _i]),
     "ouu_kernel_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _i, _i, _vp, _i, _i,
                                   _vp, _i, _vp, _i, _vp, _i, _vp, _vp]),
+    "ouu_kernel_kl_project": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _vp]),
     "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "ouu_problem_slots": (_i, [_vp]),
 }
@@ -242,6 +243,15 @@ def ouu_kernel_gemm_bf16(A, B, M, N, K, mode=0, alpha=1.0, bias=None, aux=None, 
                                       dev_ptr(out_t_bf16, torch.bfloat16), ld(out_t_bf16),
                                       dev_ptr(out2_bf16, torch.bfloat16), ld(out2_bf16), dev_ptr(err, torch.int32),
                                       _stream_handle(stream)))
+
+
+def ouu_kernel_kl_project(m, N, nn, W, rm, bias, xi, err=None, stream=None):
+    """Fused FP64-field KL projection xi = bf16(m) W^T + bias (kernel-level test entry)."""
+    import torch
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    check(load().ouu_kernel_kl_project(dev_ptr(m, torch.float64), N, nn, dev_ptr(W, torch.bfloat16), W.stride(0), rm,
+                                       dev_ptr(bias, torch.float32), dev_ptr(xi, torch.float32),
+                                       dev_ptr(err, torch.int32), _stream_handle(stream)))
 
 
 def dino_desc(**kw) -> DinoDesc:

@@ -33,45 +33,6 @@ static int grid_for(int64_t total, int threads = 256) {
 }
 
 // ------------------------------------------------------------------ element-wise kernels
-// double -> float -> bfloat16, both roundings to nearest even, in integer arithmetic
-// only (GB300's FP64 pipe is narrow; this keeps the cast off it).  NaN stays NaN,
-// magnitudes beyond the float range become infinities, and magnitudes below the
-// normal float range (< 1.2e-38) flush to a signed zero.
-static __device__ __forceinline__ unsigned short d2bf16_bits(double x) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FF);
-  const unsigned short sign = (unsigned short)((b >> 48) & 0x8000u);
-  if (e == 0x7FF) return (unsigned short)(sign | 0x7F80u | ((b & 0xFFFFFFFFFFFFFull) ? 0x40u : 0u));
-  if (e > 1023 + 127) return (unsigned short)(sign | 0x7F80u);
-  if (e < 1023 - 126) return sign;
-  // round the 52-bit mantissa to 23 bits
-  const uint64_t mant = b & 0xFFFFFFFFFFFFFull;
-  const uint64_t rest = mant & ((1ull << 29) - 1), half = 1ull << 28;
-  uint32_t f = (uint32_t)((b >> 63) << 31) | ((uint32_t)(e - 1023 + 127) << 23) | (uint32_t)(mant >> 29);
-  if (rest > half || (rest == half && (f & 1u))) f += 1u;
-  // float -> bfloat16
-  return (unsigned short)((f + 0x7FFFu + ((f >> 16) & 1u)) >> 16);
-}
-
-// out[s][k] = bf16(m[s][k]) for k < nn, 0 up to nnp (a multiple of 8); blockIdx.y =
-// sample.  Each thread converts 8 consecutive entries (8 independent loads in flight)
-// and writes them with one 16-byte store.
-__global__ void k_cast_fields_bf16(const double* __restrict__ m, int nn, int nnp, __nv_bfloat16* __restrict__ out) {
-  const double* row = m + (int64_t)blockIdx.y * nn;
-  uint4* o = (uint4*)(out + (int64_t)blockIdx.y * nnp);
-  for (int k8 = blockIdx.x * blockDim.x + threadIdx.x; k8 < nnp / 8; k8 += gridDim.x * blockDim.x) {
-    const int k = 8 * k8;
-    double x[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = k + j < nn ? row[k + j] : 0.0;
-    unsigned w[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      w[j] = (unsigned)d2bf16_bits(x[2 * j]) | ((unsigned)d2bf16_bits(x[2 * j + 1]) << 16);
-    o[k8] = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
 // x0[b] = [xi[src]; z[src]; 0-pad], src = idx ? idx[b] : b (z_stride 0: one shared z).
 __global__ void k_build_x0(const float* __restrict__ xi, const int* __restrict__ idx, const float* __restrict__ z,
                            int64_t z_stride, int rm, int dz, int in0p, int B, __nv_bfloat16* __restrict__ x0,
@@ -374,7 +335,7 @@ static void free_dino(ouu_dino* d) {
   if (!d) return;
   void* ptrs[] = {d->d_params, d->d_grad, d->d_adam_m, d->d_adam_v, d->d_phi, d->d_phi64, d->d_ubar, d->d_ut,
                   d->d_c, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
-                  d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->Mbf, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
+                  d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
                   d->Ge, d->GQe, d->Qe, d->d_zf, d->d_err, d->d_gov, d->d_oscale, d->d_klbias};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < 4; ++l) {
@@ -450,7 +411,6 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   d->n_params = off;
   const int wdp = d->wd, rup = pad8(d->ru), in0p = d->inp_l[0], dzp = pad8(d->dz);
   const size_t BR = d->BR, maxB = d->maxB, E = d->maxE;
-  d->chunkE = (int)std::max<int64_t>(8, std::min<int64_t>(E, (256ll << 20) / ((int64_t)d->nnp * 2)));
   bool ok = true;
   auto al = [&](void** p, size_t bytes) {
     if (ok && cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) ok = false;
@@ -492,7 +452,6 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   al((void**)&d->GA1T, (size_t)d->wd * maxB * 2);
   al((void**)&d->d_loss_part, LOSS_BLOCKS * 8);
   al((void**)&d->d_loss, 16);
-  al((void**)&d->Mbf, (size_t)d->chunkE * d->nnp * 2);
   al((void**)&d->XIe, E * d->rm * 4);
   al((void**)&d->X0e, E * in0p * 2);
   for (int l = 1; l <= 3; ++l) al((void**)&d->Ae[l], E * d->wd * 4);
@@ -639,25 +598,13 @@ static ouu_status check_err(ouu_dino* d) {
 // KL coordinates of `count` fields (chunked BF16 cast + tensor-core projection).
 // With mark, events ev[0] / ev[1] / ev[2] bracket the first chunk's cast and GEMM.
 static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi, bool mark = false) {
-  for (int s0 = 0; s0 < count; s0 += d->chunkE) {
-    const int cnt = std::min(d->chunkE, count - s0);
-    if (mark && s0 == 0 && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
-    {
-      dim3 g((d->nnp / 8 + 255) / 256, cnt);
-      k_cast_fields_bf16<<<g, 256, 0, d->stream>>>(m + (int64_t)s0 * d->nn, d->nn, d->nnp, d->Mbf);
-    }
-    if (mark && s0 == 0 && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[1], d->stream));
-    EpiParams ep = epi(EPI_LINEAR);
-    ep.out_f32 = xi + (int64_t)s0 * d->rm;
-    ep.ld_f32 = d->rm;
-    ep.bias = d->d_klbias;   // -mbar * (row sums of the projection): the prior mean leaves the cast
-    // split-K so that the long-K projection fills every SM (FP32 atomics into a zeroed output)
-    const int mt = (cnt + 127) / 128;
-    const int splits = std::max(1, std::min(16, d->num_sms / mt));   // one wave (one CTA per SM)
-    OUU_CUDA_TRY(cudaMemsetAsync(ep.out_f32, 0, (size_t)cnt * d->rm * 4, d->stream));
-    DINO_TRY(ouu_gemm_bf16(d->Mbf, d->nnp, d->d_wkl, d->nnp, cnt, d->rm, d->nn, ep, d->d_err, d->stream, splits));
-    if (mark && s0 == 0 && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
+  // one fused pass over the FP64 fields (kl_project.cu); the bias -W mbar carries the prior mean
+  if (mark && !d->capturing) {
+    OUU_CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
+    OUU_CUDA_TRY(cudaEventRecord(d->ev[1], d->stream));
   }
+  DINO_TRY(ouu_kl_project(m, count, d->nn, d->d_wkl, d->nnp, d->rm, d->d_klbias, xi, d->d_err, d->num_sms, d->stream));
+  if (mark && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
   return OUU_OK;
 }
 

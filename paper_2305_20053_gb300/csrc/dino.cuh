@@ -48,8 +48,6 @@ struct ouu_dino {
   double* d_loss_part = nullptr;   // [256]
   double* d_loss = nullptr;        // [2]
   // evaluation buffers (n_samples <= maxE)
-  int chunkE = 0;
-  __nv_bfloat16* Mbf = nullptr;    // [chunkE][nnp]
   float* XIe = nullptr;            // [maxE][rm]
   __nv_bfloat16* X0e = nullptr;    // [maxE][in0p]
   float* Ae[4] = {};               // [maxE][wd] (index 1..3)
@@ -79,4 +77,9 @@ ouu_status dino_install_bases(ouu_dino* d);
 // Sum_i w[r][i] grad_z Q_i of the last evaluation into out [n_w][d_Z] (device).
 void dino_weighted_grads(ouu_dino* d, const double* w, int N, int n_w, double* out);
 // Jacobian-data solves (pde.cu): jy[i][j][r] = h^2 Phi_r . J(u_i)^-1 g_j.
+// Fused KL projection of FP64 fields (kl_project.cu): xi[N][rm] = bf16(m) W^T + bias with
+// W = [rm][ldw] BF16 (K = nn contiguous); xi is zeroed here.  m 16-byte aligned, rm <= 240.
+ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W, int ldw, int rm, const float* bias,
+                          float* xi, int* err, int num_sms, cudaStream_t s);
+
 void launch_pde_jacobian_data(const PdeArgs& a, int nslots, const float* phi, int ru, float* jy, cudaStream_t s);

@@ -1,0 +1,379 @@
+// Fused KL projection (Sec. 3.3, the input reduction of the reduced-basis network):
+//   xi[s][c] = bias[c] + sum_k bf16(m[s][k]) * W[c][k],   s < N, c < r_m,
+// reading the FP64 fields once.  One persistent CTA per SM; the (128-sample tile, 64-wide
+// K block) units are dealt to the CTAs in equal contiguous ranges ("stream-K"), so every
+// SM streams the same number of bytes whatever N and n^2 are.  Per CTA:
+//   warp 16      : producer.  Per K block, TMA loads of the FP64 slice m[tile rows][k0, k0+64)
+//                  and of the BF16 basis block W[0, BN) x [k0, k0 + 64) (128-byte swizzle).
+//                  With n^2 odd the row stride n^2 * 8 bytes is not a multiple of 16, which
+//                  a tensor map needs; the fields are then read as rows of sample PAIRS
+//                  (stride 2 n^2 * 8 bytes), even samples from x = k0 and odd samples from
+//                  x = n^2 + k0 - 1 (one element early, so that x stays 16-byte aligned),
+//                  66 elements each: two copies per K block.  A last unpaired sample (N odd)
+//                  is read with plain loads.
+//   warps 0..15  : converters.  FP64 -> BF16 (round to FP32, then to BF16, both to nearest
+//                  even; the first step in integer arithmetic, as the FP64 pipe is narrow)
+//                  written straight into the swizzled K-major A tile that tcgen05.mma reads.
+//   warp 17      : tcgen05.mma issuer (M = 128, N = BN, K = 16 per instruction) into one of
+//                  two TMEM accumulators; allocates and frees the tensor memory.
+//   warps 18..21 : epilogue.  TMEM -> registers, + bias on the unit range that holds K block
+//                  0 of its tile, 16-byte atomic adds into xi (zeroed beforehand).
+// Every mbarrier wait is bounded; on a timeout the CTA stops, drains its own copies and
+// raises *err.
+#include <cuda_bf16.h>
+
+#include "dino.cuh"
+#include "ouu_kernels.h"
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+#define KLP_CONV_WARPS 16
+#define KLP_PROD_WARP 16
+#define KLP_MMA_WARP 17
+#define KLP_EPI_WARP0 18
+#define KLP_THREADS (22 * 32)
+#define KLP_ROWS_PER_WARP (128 / KLP_CONV_WARPS)
+#define KLP_ROW_BYTES 528                    // pair mode: 66 doubles per sample row
+#define KLP_F64_STAGE (128 * KLP_ROW_BYTES)
+#define KLP_HALF (64 * KLP_ROW_BYTES)           // pair mode: even samples, then odd samples
+#define KLP_A_STAGE (128 * 64 * 2)
+
+struct KlpArgs {
+  const double* m;
+  int N, nn, KBt, BN, rm;
+  int pair;        // 1: fields read as sample pairs (n^2 odd); 0: as rows (n^2 even)
+  int n_tma;       // samples [0, n_tma) come by TMA, the rest (at most one) by plain loads
+  long long U;
+  const float* bias;
+  float* xi;
+  int* err;
+};
+
+// FP64 -> FP32, rounding to nearest even, in integer arithmetic on the two halves of the
+// double (GB300's FP64 pipe is narrow).  Normal FP32 range on the fast path; otherwise
+// a signed zero below it, an infinity above it, NaN kept.  The FP32 -> BF16 step (also to
+// nearest even) is one packed hardware conversion of two values.
+static __device__ __forceinline__ float f64_to_f32_slow(uint32_t hi, uint32_t lo) {
+  const uint32_t e = (hi >> 20) & 0x7FFu, sign = hi & 0x80000000u;
+  if (e == 0x7FFu) return __uint_as_float(sign | (((hi & 0xFFFFFu) | lo) ? 0x7FC00000u : 0x7F800000u));
+  if (e > 1023u + 127u) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign);   // below the normal FP32 range
+}
+
+// True when x rounds into FP32's normal range by the fast path below (exponent in [897, 1150]).
+static __device__ __forceinline__ bool f32_normal(double x) {
+  return ((((uint32_t)__double2hiint(x) >> 20) & 0x7FFu) - 897u) <= 253u;
+}
+
+// The fast path on its own: rounding the 64-bit pattern to nearest even at bit 29 carries
+// through the mantissa into the exponent as it should; bits 23..31 of (bits >> 29) hold
+// the low 9 exponent bits, and subtracting 896 mod 512 leaves the FP32 exponent.
+static __device__ __forceinline__ float f64_to_f32_fast(double x) {
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  b += 0x0FFFFFFFull + ((b >> 29) & 1ull);
+  return __uint_as_float(((uint32_t)(b >> 29) - 0xC0000000u) | sign);
+}
+
+static __device__ __forceinline__ float f64_to_f32_rne(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  if (e - 897u > 253u) return f64_to_f32_slow(hi, lo);   // e outside [897, 1150]
+  // sign | (e - 896) << 23 | the top 23 mantissa bits
+  uint32_t f = (hi & 0x80000000u) | ((((hi & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lo >> 29));
+  // the remaining 29 bits: +1 exactly when they exceed half, or equal it with f odd
+  f += ((lo & 0x1FFFFFFFu) + 0x0FFFFFFFu + (f & 1u)) >> 29;
+  return __uint_as_float(f);
+}
+
+__global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_constant__ CUtensorMap tw,
+                                                                const __grid_constant__ CUtensorMap tm, KlpArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t B_BYTES = (uint32_t)a.BN * 128u;
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + 2 * KLP_A_STAGE;
+  uint8_t* sF = sB + 2 * B_BYTES;
+  uint64_t* bars = (uint64_t*)(sF + 2 * KLP_F64_STAGE);
+  uint64_t* f64_full = bars + 0;    // producer: field copies landed
+  uint64_t* f64_empty = bars + 2;   // converters: FP64 stage consumed
+  uint64_t* b_full = bars + 4;      // producer: basis block landed
+  uint64_t* a_full = bars + 6;      // converters: BF16 A tile written
+  uint64_t* ab_empty = bars + 8;    // MMA: A and B stages consumed
+  uint64_t* acc_full = bars + 10;   // MMA: accumulator complete
+  uint64_t* acc_empty = bars + 12;  // epilogue: accumulator drained
+  uint64_t* mma_done = bars + 14;
+  uint32_t* tslot = (uint32_t*)(bars + 16);
+  __shared__ volatile int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long u0 = (long long)blockIdx.x * a.U / gridDim.x;
+  const long long u1 = (long long)(blockIdx.x + 1) * a.U / gridDim.x;
+  const int nj = (int)(u1 - u0);
+  const int nn = a.nn, KBt = a.KBt, N = a.N;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&f64_full[i], 1);
+      mbar_init(&f64_empty[i], KLP_CONV_WARPS);
+      mbar_init(&b_full[i], 1);
+      mbar_init(&a_full[i], KLP_CONV_WARPS);
+      mbar_init(&ab_empty[i], 1);
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 4);
+    }
+    mbar_init(mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+  }
+  if (warp == KLP_MMA_WARP) tmem_alloc(tslot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == KLP_PROD_WARP) {
+    // ---------------------------------------------------------------- producer
+    int issued = 0;
+    bool ok = true;
+    if (lane == 0) {
+      const uint32_t fbytes = a.pair ? 2u * KLP_HALF : 128u * 512u;
+      for (int j = 0; j < nj; ++j) {
+        const long long u = u0 + j;
+        const int t = (int)(u / KBt), k0 = (int)(u % KBt) * 64, s = j & 1;
+        const uint32_t ph = (uint32_t)(j >> 1) & 1u;
+        if (j >= 2 && !(mbar_wait(&f64_empty[s], ph ^ 1u) && mbar_wait(&ab_empty[s], ph ^ 1u))) {
+          ok = false;
+          break;
+        }
+        uint8_t* dst = sF + s * KLP_F64_STAGE;
+        if (a.n_tma == 0) {
+          mbar_arrive(&f64_full[s]);   // a single sample with n^2 odd: plain loads only
+        } else if (a.pair) {
+          mbar_expect_tx(&f64_full[s], fbytes);
+          tma_load_2d(dst, &tm, k0, t * 64, &f64_full[s]);
+          tma_load_2d(dst + KLP_HALF, &tm, nn + k0 - 1, t * 64, &f64_full[s]);
+        } else {
+          mbar_expect_tx(&f64_full[s], fbytes);
+          tma_load_2d(dst, &tm, k0, t * 128, &f64_full[s]);
+        }
+        mbar_expect_tx(&b_full[s], B_BYTES);
+        tma_load_2d(sB + s * B_BYTES, &tw, k0, 0, &b_full[s]);
+        issued = j + 1;
+      }
+      if (!ok) s_fail = 1;
+      // drain: the copies into both stages must have landed before the CTA exits
+      for (int j = max(0, issued - 2); j < issued; ++j) {
+        const uint32_t ph = (uint32_t)(j >> 1) & 1u;
+        if (!mbar_wait(&f64_full[j & 1], ph) || !mbar_wait(&b_full[j & 1], ph)) s_fail = 1;
+      }
+    }
+  } else if (warp < KLP_CONV_WARPS) {
+    // ---------------------------------------------------------------- converters
+    const int r0 = warp * KLP_ROWS_PER_WARP;
+    for (int j = 0; j < nj; ++j) {
+      const long long u = u0 + j;
+      const int t = (int)(u / KBt), kb = (int)(u % KBt), k0 = kb * 64, s = j & 1;
+      const uint32_t ph = (uint32_t)(j >> 1) & 1u;
+      bool ok = mbar_wait(&f64_full[s], ph);
+      if (ok && j >= 2) ok = mbar_wait(&ab_empty[s], ph ^ 1u);
+      if (!__all_sync(0xffffffffu, ok ? 1 : 0)) {
+        if (lane == 0) s_fail = 1;
+        break;
+      }
+      const uint8_t* fst = sF + s * KLP_F64_STAGE;
+      uint8_t* ast = sA + s * KLP_A_STAGE;
+      const bool c0ok = k0 + lane < nn, c1ok = k0 + 32 + lane < nn;
+#pragma unroll
+      for (int i = 0; i < KLP_ROWS_PER_WARP; ++i) {
+        const int rr = r0 + i, r = t * 128 + rr;   // r0 is a multiple of 8: rr & 7 == i
+        float fa = 0.f, fb = 0.f;
+        if (r < N) {
+          double x0 = 0.0, x1 = 0.0;
+          if (r < a.n_tma) {
+            const double* sp = a.pair ? (const double*)(fst + (i & 1) * KLP_HALF + (rr >> 1) * KLP_ROW_BYTES) + (i & 1)
+                                      : (const double*)(fst + rr * 512);
+            x0 = sp[lane];
+            x1 = sp[lane + 32];
+          } else {
+            const double* row = a.m + (size_t)r * nn + k0;
+            if (c0ok) x0 = row[lane];
+            if (c1ok) x1 = row[lane + 32];
+          }
+          if (__all_sync(0xffffffffu, f32_normal(x0) && f32_normal(x1))) {
+            fa = f64_to_f32_fast(x0);
+            fb = f64_to_f32_fast(x1);
+          } else {   // zeros past the last column, or values outside FP32's normal range
+            fa = c0ok ? f64_to_f32_rne(x0) : 0.f;
+            fb = c1ok ? f64_to_f32_rne(x1) : 0.f;
+          }
+        }
+        // w = bf16(column l) | bf16(column 32 + l) << 16; lane l then writes the word of
+        // columns (2l, 2l + 1), taken from lanes 2 (l mod 16) and 2 (l mod 16) + 1
+        const __nv_bfloat162 pk = __floats2bfloat162_rn(fa, fb);
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(&pk);
+        const int sl = 2 * (lane & 15);
+        const uint32_t xa = __shfl_sync(0xffffffffu, w, sl), xb = __shfl_sync(0xffffffffu, w, sl + 1);
+        const uint32_t word = __byte_perm(xa, xb, lane < 16 ? 0x5410u : 0x7632u);
+        // 128-byte swizzle: 16-byte chunk index XOR (row mod 8) within the 8-row atom
+        *(uint32_t*)(ast + rr * 128 + ((((uint32_t)lane >> 2) ^ (uint32_t)i) << 4) + ((lane & 3) << 2)) = word;
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&a_full[s]);
+        mbar_arrive(&f64_empty[s]);
+      }
+    }
+  } else if (warp == KLP_MMA_WARP) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.BN >> 3) << 17) | ((128u >> 4) << 24);
+      int seg = 0, issued_any = 0;
+      for (int j = 0; j < nj; ++j) {
+        const long long u = u0 + j;
+        const int kb = (int)(u % KBt), s = j & 1;
+        const uint32_t ph = (uint32_t)(j >> 1) & 1u;
+        const bool first = j == 0 || kb == 0, last = j == nj - 1 || kb == KBt - 1;
+        const int acc = seg & 1;
+        bool ok = true;
+        if (first && seg >= 2) ok = mbar_wait(&acc_empty[acc], (uint32_t)((seg >> 1) - 1) & 1u);
+        ok = ok && mbar_wait(&a_full[s], ph) && mbar_wait(&b_full[s], ph);
+        if (!ok) {
+          s_fail = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA + s * KLP_A_STAGE), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          tc_mma(tmem + (uint32_t)acc * 256u, smem_desc_sw128(a0 + k * 32), smem_desc_sw128(b0 + k * 32), idesc,
+                 (!first || k > 0) ? 1u : 0u);
+        tc_commit(&ab_empty[s]);
+        issued_any = 1;
+        if (last) {
+          tc_commit(&acc_full[acc]);
+          ++seg;
+        }
+      }
+      // every MMA issued above has completed before the tensor memory is freed
+      if (issued_any) {
+        tc_commit(mma_done);
+        if (!mbar_wait(mma_done, 0)) s_fail = 1;
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3;
+    int seg = 0, first_kb = 0;
+    for (int j = 0; j < nj; ++j) {
+      const long long u = u0 + j;
+      const int t = (int)(u / KBt), kb = (int)(u % KBt);
+      if (j == 0 || kb == 0) first_kb = kb;
+      if (!(j == nj - 1 || kb == KBt - 1)) continue;
+      const int acc = seg & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[acc], (uint32_t)(seg >> 1) & 1u) ? 1 : 0)) {
+        if (lane == 0) s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      const int r = t * 128 + q * 32 + lane;
+      float* orow = a.xi + (size_t)r * a.rm;
+      const bool vec4 = (a.rm & 3) == 0;
+      for (int c0 = 0; c0 < a.BN; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * 256u + (uint32_t)c0, v);
+        if (r < N) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) {
+            const int c = c0 + i;
+            if (c >= a.rm) break;
+            float y[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+              y[jj] = __uint_as_float(v[i + jj]) + ((first_kb == 0 && c + jj < a.rm) ? a.bias[c + jj] : 0.f);
+            if (vec4) {
+              atomicAdd(reinterpret_cast<float4*>(orow + c), make_float4(y[0], y[1], y[2], y[3]));
+            } else {
+              for (int jj = 0; jj < 4 && c + jj < a.rm; ++jj) atomicAdd(orow + c + jj, y[jj]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+      ++seg;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == KLP_MMA_WARP) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+  if (threadIdx.x == 0 && s_fail) atomicExch(a.err, 1);
+}
+
+ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W, int ldw, int rm, const float* bias,
+                          float* xi, int* err, int num_sms, cudaStream_t s) {
+  OUU_CHECK_ARG(m && W && bias && xi && err, "null argument");
+  OUU_CHECK_ARG(N >= 1 && nn >= 1 && rm >= 1 && rm <= 240, "KL projection sizes: N, n^2 >= 1, 1 <= r_m <= 240");
+  OUU_CHECK_ARG(((uintptr_t)m & 15) == 0, "fields must be 16-byte aligned");
+  const int BN = (rm + 15) / 16 * 16;
+  CUtensorMap tw;
+  if (!ouu_tmap_bf16(&tw, W, (uint64_t)nn, (uint64_t)rm, (uint64_t)ldw, (uint32_t)BN)) {
+    ouu_set_error("tensor map for the KL basis failed (alignment or driver entry point)");
+    return OUU_ERR_INVALID_ARG;
+  }
+  // fields tensor map: sample rows (n^2 even) or sample pairs (n^2 odd)
+  const int pair = nn & 1;
+  const int n_tma = pair ? N / 2 * 2 : N;
+  CUtensorMap tm;
+  if (n_tma > 0) {
+    const bool okm = pair ? ouu_tmap_2d(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, m, 2 * (uint64_t)nn, (uint64_t)(N / 2),
+                                        16 * (uint64_t)nn, 66, 64, CU_TENSOR_MAP_SWIZZLE_NONE)
+                          : ouu_tmap_2d(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, m, (uint64_t)nn, (uint64_t)N,
+                                        8 * (uint64_t)nn, 64, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (!okm) {
+      ouu_set_error("tensor map for the fields failed (alignment or driver entry point)");
+      return OUU_ERR_INVALID_ARG;
+    }
+  } else {
+    tm = tw;   // never read: N = 1 with n^2 odd goes by plain loads
+  }
+  KlpArgs a;
+  a.pair = pair;
+  a.n_tma = n_tma;
+  a.m = m;
+  a.N = N;
+  a.nn = nn;
+  a.KBt = (nn + 63) / 64;
+  a.BN = BN;
+  a.rm = rm;
+  a.U = (long long)((N + 127) / 128) * a.KBt;
+  a.bias = bias;
+  a.xi = xi;
+  a.err = err;
+  const size_t smem = 1024 + 2 * KLP_A_STAGE + 2 * (size_t)BN * 128 + 2 * KLP_F64_STAGE + 16 * 8 + 16;
+  static size_t attr = 0;   // one device per process is the supported set-up
+  if (attr < smem) {
+    OUU_CUDA_TRY(cudaFuncSetAttribute((const void*)k_kl_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  const int grid = (int)std::min<long long>(a.U, (long long)std::max(1, num_sms));
+  OUU_CUDA_TRY(cudaMemsetAsync(xi, 0, (size_t)N * rm * 4, s));
+  k_kl_project<<<grid, KLP_THREADS, smem, s>>>(tw, tm, a);
+  OUU_CUDA_TRY(cudaGetLastError());
+  return OUU_OK;
+}
+
+// Kernel-level entry used by the projection numerics test (declared in include/ouu_kernels.h).
+extern "C" ouu_status ouu_kernel_kl_project(const double* m, int N, int nn, const void* W, int ldw, int rm,
+                                            const float* bias, float* xi, int* err_dev, void* stream) {
+  int dev = 0, sms = 0;
+  OUU_CUDA_TRY(cudaGetDevice(&dev));
+  OUU_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  return ouu_kl_project(m, N, nn, (const __nv_bfloat16*)W, ldw, rm, bias, xi, err_dev, sms, (cudaStream_t)stream);
+}

@@ -64,20 +64,35 @@ static __device__ __forceinline__ double dval(uint64_t k) {
   return __longlong_as_double((long long)b);
 }
 
-// k-th largest (1-based) of q[0, N) by block-wide 8-bit radix select on the keys.
+// k-th largest (1-based) of q[0, N) by block-wide 8-bit radix select on the keys.  With
+// N <= KPT * blockDim.x the keys stay in registers across the eight passes.
+template <int KPT>
 static __device__ double kth_largest(const double* q, int N, int k, unsigned* hist, unsigned* sel) {
   uint64_t prefix = 0, mask = 0;
   unsigned kk = (unsigned)k;
   const int lane = threadIdx.x & 31;
+  const bool regs = N <= KPT * (int)blockDim.x;
+  uint64_t kr[KPT];
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) {
+    const int i = j * blockDim.x + threadIdx.x;
+    kr[j] = (regs && i < N) ? dkey(q[i]) : 0ull;
+  }
   for (int shift = 56; shift >= 0; shift -= 8) {
     for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0u;
     __syncthreads();
-    for (int i0 = 0; i0 < N; i0 += blockDim.x) {   // warp-uniform trip count for __match_any_sync
+    for (int i0 = 0, j = 0; i0 < N; i0 += blockDim.x, ++j) {   // warp-uniform trip count for __match_any_sync
       const int i = i0 + threadIdx.x;
       uint64_t key = 0;
       bool in = false;
       if (i < N) {
-        key = dkey(q[i]);
+        if (regs) {
+#pragma unroll
+          for (int jj = 0; jj < KPT; ++jj)
+            if (jj == j) key = kr[jj];
+        } else {
+          key = dkey(q[i]);
+        }
         in = (key & mask) == prefix;
       }
       const unsigned bin = in ? (unsigned)((key >> shift) & 255u) : 256u;
@@ -181,7 +196,7 @@ __global__ void k_risk_select(const double* __restrict__ q, int N, const double*
       int kq = (int)floor(K) + 1;
       if (kq > N) kq = N;
       if (kq < 1) kq = 1;
-      const double v = kth_largest(q, N, kq, hist, sel);
+      const double v = kth_largest<8>(q, N, kq, hist, sel);
       const uint64_t khi = dkey(v + eps), klo = dkey(v - eps);
       if (threadIdx.x == 0) nwin = 0;
       __syncthreads();
@@ -215,32 +230,35 @@ __global__ void k_risk_select(const double* __restrict__ q, int N, const double*
             if (sp < Tf) th_lo = mid;
             else th_hi = mid;
           }
-          // FP64: g(t) = 1 - S(t)/K over the window (lanes) -- bracket check, then Illinois
-          // regula falsi to the bisection end state (lo: g < 0, hi: g >= 0).
-          auto g = [&](double tt) {
+          // FP64 on G(t) = (K - C) - S_window(t), which has the sign of d rho/dt = 1 - S(t)/K
+          // without a division: bracket check, then Illinois regula falsi (secant ratio in
+          // FP32) until the bracket (lo: G < 0, hi: G >= 0) is a few ulps wide.
+          const double KC = K - C;
+          auto G = [&](double tt) {
             double S = 0.0;
             for (int i = lane; i < W; i += 32) S += splus_d1(win[i] - tt, eps, ie);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
-            return 1.0 - (C + S) / K;
+            return KC - S;
           };
           double lo = v - eps * (double)th_hi, hi = v - eps * (double)th_lo;
-          double glo = g(lo), ghi = g(hi);
+          double glo = G(lo), ghi = G(hi);
           if (!(glo < 0.0)) {
             lo = v - eps;
-            glo = g(lo);
+            glo = G(lo);
           }
           if (!(ghi >= 0.0)) {
             hi = v;
-            ghi = g(hi);
+            ghi = G(hi);
           }
           int side = 0;
-          for (int it = 0; it < 60; ++it) {
+          for (int it = 0; it < 60 && glo < 0.0; ++it) {
             const double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi) break;
-            double c = hi - ghi * (hi - lo) / (ghi - glo);
+            if (mid <= lo || mid >= hi || hi - lo <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) break;
+            const float ratio = (float)ghi / ((float)ghi - (float)glo);
+            double c = hi - (double)ratio * (hi - lo);
             if (!(c > lo && c < hi)) c = mid;
-            const double gc = g(c);
+            const double gc = G(c);
             if (gc < 0.0) {
               lo = c;
               glo = gc;
@@ -253,7 +271,7 @@ __global__ void k_risk_select(const double* __restrict__ q, int N, const double*
               side = 1;
             }
           }
-          const double tt = g(lo) >= 0.0 ? lo : hi;
+          const double tt = glo >= 0.0 ? lo : hi;
           if (threadIdx.x == 0) s_t = tt;
         }
         __syncthreads();

@@ -39,6 +39,11 @@ struct EpiParams {
 // (base must be 16-byte aligned and ld a multiple of 8).
 bool ouu_tmap_bf16(CUtensorMap* map, const void* base, uint64_t k, uint64_t rows, uint64_t ld, uint32_t box_rows);
 
+// General 2-D tensor map (dims d0 inner, d1 outer; outer stride in bytes, a multiple of 16;
+// box0 * esize a multiple of 16; out-of-range elements read as zero).
+bool ouu_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, uint32_t esize, const void* base, uint64_t d0, uint64_t d1,
+                 uint64_t stride1_bytes, uint32_t box0, uint32_t box1, CUtensorMapSwizzle sw);
+
 // Launch D = A B^T with A = [M][K] (lda), B = [N][K] (ldb), both BF16 row-major; the N
 // tile is chosen for the least padding.  err: device int set non-zero when a wait times
 // out.  splits > 1: split-K over gridDim.z; only for one FP32 EPI_LINEAR output, which the

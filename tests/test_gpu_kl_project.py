@@ -1,0 +1,66 @@
+"""Numerics of the fused FP64-field KL projection (Sec. 3.3 input reduction) against
+float64 products of the same BF16-rounded operands (the oracle's BF16 rounding:
+FP64 -> FP32 -> BF16, both to nearest even).  Products of BF16 values are exact in
+FP32, so only the FP32 summation order differs: tolerance, relative to the largest
+entry of each row, 1e-5 + 5e-7 sqrt(n^2).
+
+Cases: n^2 odd (sample-pair tensor map) and even (row tensor map); N even, odd (a
+last unpaired sample read with plain loads), one sample (plain loads only), a ragged
+last 128-sample tile, a ragged last 64-wide K block, r_m not a multiple of 16, and
+the 129 x 129 width.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.dino import round_bf16
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2305_20053_gb300 import build, capi
+    build.build()
+    capi.load()
+
+
+@pytest.mark.parametrize("N,nn,rm", [(40, 289, 16), (131, 289, 200), (1, 289, 16), (3, 300, 24), (129, 1024, 52),
+                                     (257, 16641, 200)])
+def test_kl_project_parity(N, nn, rm):
+    from paper_2305_20053_gb300 import capi
+    rng = np.random.default_rng(1000 + N + nn + rm)
+    m = rng.standard_normal((N, nn)) * 1.3 + 0.2
+    ldw = (nn + 63) // 64 * 64
+    W = np.zeros((rm, ldw))
+    W[:, :nn] = round_bf16(rng.standard_normal((rm, nn)) / math.sqrt(nn))
+    bias = rng.standard_normal(rm).astype(np.float32)
+    m_d = torch.tensor(m, device="cuda")
+    W_d = torch.tensor(W, device="cuda").to(torch.bfloat16)
+    b_d = torch.tensor(bias, device="cuda")
+    xi = torch.full((N, rm), float("nan"), device="cuda", dtype=torch.float32)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    capi.ouu_kernel_kl_project(m_d, N, nn, W_d, rm, b_d, xi, err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = round_bf16(m) @ W[:, :nn].T + bias.astype(np.float64)
+    got = xi.cpu().numpy().astype(np.float64)
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(got - ref) <= (1e-5 + 5e-7 * math.sqrt(nn)) * scale)
+
+
+def test_kl_project_rejects_unaligned_fields():
+    from paper_2305_20053_gb300 import capi
+    N, nn, rm = 4, 289, 16
+    buf = torch.zeros(N * nn + 1, device="cuda", dtype=torch.float64)
+    W = torch.zeros(rm, 320, device="cuda", dtype=torch.bfloat16)
+    b = torch.zeros(rm, device="cuda")
+    xi = torch.zeros(N, rm, device="cuda")
+    lib = capi.load()
+    import ctypes
+    rc = lib.ouu_kernel_kl_project(ctypes.c_void_p(buf.data_ptr() + 8), N, nn, ctypes.c_void_p(W.data_ptr()), 320,
+                                   rm, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(xi.data_ptr()),
+                                   ctypes.c_void_p(b.data_ptr()), None)
+    assert rc == 1   # OUU_ERR_INVALID_ARG
