@@ -7,6 +7,8 @@
  *   0 LINEAR     : y = alpha * acc + bias[c]
  *   1 GELU       : a = acc + bias[c]; out_f32 = a; BF16 outputs = gelu(a)   (exact erf GELU)
  *   2 DGELU_SCALE: y = acc * gelu'(aux[(r / aux_rdiv) * ld_aux + c]); out2 = bf16(acc)
+ *   3 GELU_D     : a = acc + bias[c]; out_f32 = gelu'(a); BF16 outputs = gelu(a)
+ *   4 SCALE      : y = acc * aux[(r / aux_rdiv) * ld_aux + c]
  * These are the dense layers of the reduced-basis network of Sec. 3.3 (forward
  * values, forward-mode control-Jacobian tangents, and their adjoints).
  * A, B: device BF16 row-major with leading dimensions lda, ldb (multiples of 8,
@@ -21,7 +23,14 @@
  * reading the FP64 fields m [N][nn] (device, 16-byte aligned, row-major) once; the
  * rounding to BF16 goes through FP32 (both to nearest even).  W: device BF16
  * [rm][ldw] (ldw a multiple of 8, >= nn).  bias: device FP32 [rm].  xi: device FP32
- * [N][rm], overwritten.  rm <= 240.  err_dev as above. */
+ * [N][rm], overwritten.  rm <= 240.  err_dev as above.
+ *
+ * ouu_kernel_risk_weights: the per-sample risk weights of the SAA gradient (Sec. 2.1-2.2)
+ * from the QoIs q_dev [N] (device FP64): for each of the n_risks (1..4) host descriptors,
+ * w_dev[r][i] (device FP64, [n_risks][N]) with grad rho = sum_i w[r][i] grad Q_i, and on the
+ * host out_host[3r + 0..2] = rho, d rho / dt, t (t = t* when t_optimal).  Mean + variance:
+ * w = (1 + 2 kappa (Q_i - Qbar)) / N; smoothed CVaR: w = s'_eps(Q_i - t) / (N (1 - beta)).
+ * Synchronises `stream`; allocates its own scratch (test entry only). */
 #ifndef OUU_KERNELS_H
 #define OUU_KERNELS_H
 
@@ -35,6 +44,9 @@ ouu_status ouu_kernel_gemm_bf16(const void* A, int lda, const void* B, int ldb, 
                                 float alpha, const float* bias, const float* aux, int ld_aux, int aux_rdiv,
                                 float* out_f32, int ld_f32, int accumulate, void* out_bf16, int ld_bf16,
                                 void* out_t_bf16, int ld_t, void* out2_bf16, int ld2, int* err_dev, void* stream);
+
+ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const ouu_risk_desc* risks, int n_risks, double* w_dev,
+                                   double* out_host, void* stream);
 
 ouu_status ouu_kernel_kl_project(const double* m, int N, int nn, const void* W, int ldw, int rm, const float* bias,
                                  float* xi, int* err_dev, void* stream);

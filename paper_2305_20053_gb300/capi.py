@@ -94,6 +94,7 @@ SIGNATURES = {
     "ouu_kernel_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _i, _i, _vp, _i, _i,
                                   _vp, _i, _vp, _i, _vp, _i, _vp, _vp]),
     "ouu_kernel_kl_project": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _vp]),
+    "ouu_kernel_risk_weights": (_i, [_vp, _i, ctypes.POINTER(RiskDesc), _i, _vp, _dp, _vp]),
     "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "ouu_problem_slots": (_i, [_vp]),
 }
@@ -243,6 +244,19 @@ def ouu_kernel_gemm_bf16(A, B, M, N, K, mode=0, alpha=1.0, bias=None, aux=None, 
                                       dev_ptr(out_t_bf16, torch.bfloat16), ld(out_t_bf16),
                                       dev_ptr(out2_bf16, torch.bfloat16), ld(out2_bf16), dev_ptr(err, torch.int32),
                                       _stream_handle(stream)))
+
+
+def ouu_kernel_risk_weights(q, risks, w, stream=None):
+    """Per-sample risk weights and (rho, d rho/dt, t) per risk (kernel-level test entry)."""
+    import numpy as np
+    import torch
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    n = len(risks)
+    arr = (RiskDesc * n)(*risks)
+    out = np.zeros(3 * n)
+    check(load().ouu_kernel_risk_weights(dev_ptr(q, torch.float64), q.numel(), arr, n, dev_ptr(w, torch.float64),
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream)))
+    return out.reshape(n, 3)
 
 
 def ouu_kernel_kl_project(m, N, nn, W, rm, bias, xi, err=None, stream=None):

@@ -221,6 +221,7 @@ extern "C" ouu_status ouu_create_problem(const ouu_problem_desc* desc, void* cud
   OUU_ALLOC(p->d_risks, sizeof(RiskDev) * OUU_MAX_RISKS);
   OUU_ALLOC(p->d_z, (size_t)p->dz * 8);
   OUU_ALLOC(p->d_rscr, (size_t)OUU_RISK_SCRATCH * 8);
+  OUU_CUDA_TRY(cudaMemset(p->d_rscr, 0, (size_t)OUU_RISK_SCRATCH * 8));   // the block-arrival counter starts at 0
   if (cudaMallocHost((void**)&p->h_out, (size_t)(OUU_MAX_RISKS * (3 + p->dz) + 8) * 8) != cudaSuccess ||
       cudaMallocHost((void**)&p->h_stat, (size_t)N * 4 * 4 + 64) != cudaSuccess) {
     cudaGetLastError();

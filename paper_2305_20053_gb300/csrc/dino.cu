@@ -804,8 +804,8 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
   __nv_bfloat16* hin = d->X0e;
   int ldin = in0p, kin = d->in0;
   __nv_bfloat16* hbuf[2] = {d->He0, d->He1};
-  for (int l = 0; l < 3; ++l) {
-    EpiParams e = epi(EPI_GELU);
+  for (int l = 0; l < 3; ++l) {   // Ae[l + 1] = gelu'(a_{l+1}) for the reverse pass
+    EpiParams e = epi(EPI_GELU_D);
     e.bias = d->d_params + d->offb[l];
     e.out_f32 = d->Ae[l + 1];
     e.ld_f32 = wd;
@@ -830,7 +830,7 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
     const __nv_bfloat16* gin = d->Ge;
     int ldg = rup, kg = d->ru;
     for (int l = 3; l >= 1; --l) {   // ga_l = s'(a_l) * (g W_l)
-      EpiParams e = epi(EPI_DGELU_SCALE);
+      EpiParams e = epi(EPI_SCALE);
       e.aux = d->Ae[l];
       e.ld_aux = wd;
       e.aux_rdiv = 1;

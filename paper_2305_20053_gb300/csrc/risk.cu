@@ -4,6 +4,7 @@
 //   mean + kappa var:  w_i = (1 + 2 kappa (Q_i - Qbar)) / N
 //   smoothed CVaR:     w_i = s'_eps(Q_i - t) / (N (1 - beta))
 #include "ouu_internal.cuh"
+#include "ouu_kernels.h"
 
 struct BlockRed {
   double* red;
@@ -157,6 +158,113 @@ __global__ void k_risk_moments(const double* __restrict__ q, int N, double* __re
   }
 }
 
+// Warp sum of v over lanes [0, 2^k) where 2^k >= active (active <= 32): the butterfly runs only
+// as deep as the data, then lane 0's total is broadcast.  (FP64 adds are expensive on
+// GB300's narrow FP64 pipe; a window of one sample needs none.)
+static __device__ __forceinline__ double warp_sum_active(double v, int active) {
+  for (int o = 1; o < active && o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+static __device__ __forceinline__ float warp_sum_active_f(float v, int active) {
+  for (int o = 1; o < active && o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// k-th largest (1-based) of q[0, N) for N <= 16 * blockDim.x: an 11/11/10-bit radix select
+// on the top 32 bits of the order-preserving keys (held in registers), then an exact choice
+// among the samples that share those 32 bits (at most 32 of them; otherwise *ok = false).
+static __device__ double kth_largest_prefix(const double* q, int N, int k, unsigned* hist, unsigned* sel,
+                                            double* cand, int* ncand, bool* ok) {
+  constexpr int KPT = 16;
+  uint32_t kr[KPT];
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) {
+    const int i = j * blockDim.x + threadIdx.x;
+    kr[j] = i < N ? (uint32_t)(dkey(q[i]) >> 32) : 0u;
+  }
+  uint32_t prefix = 0, mask = 0;
+  unsigned kk = (unsigned)k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int pass = 0; pass < 3; ++pass) {
+    const int shift = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
+    const uint32_t dmask = pass == 2 ? 1023u : 2047u;
+    for (int b = threadIdx.x; b < 2048; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const int i = j * blockDim.x + threadIdx.x;
+      if (i < N && (kr[j] & mask) == prefix) atomicAdd(&hist[(kr[j] >> shift) & dmask], 1u);
+    }
+    __syncthreads();
+    // descending bins: thread t owns bins 2047 - 2t and 2046 - 2t; block-wide exclusive scan
+    unsigned h0 = 0, h1 = 0;
+    if (2 * threadIdx.x < 2048) {
+      h0 = hist[2047 - 2 * threadIdx.x];
+      h1 = hist[2046 - 2 * threadIdx.x];
+    }
+    const unsigned c = h0 + h1;
+    unsigned incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) sel[2 + warp] = incl;   // warp totals
+    __syncthreads();
+    if (warp == 0) {
+      unsigned wt = lane < nw ? sel[2 + lane] : 0u, wi = wt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      if (lane < nw) sel[2 + 32 + lane] = wi - wt;   // exclusive warp offsets
+    }
+    __syncthreads();
+    const unsigned excl = sel[2 + 32 + warp] + incl - c;
+    if (2 * threadIdx.x < 2048 && excl < kk && kk <= excl + c) {
+      if (excl + h0 >= kk) {
+        sel[0] = 2047u - 2u * threadIdx.x;
+        sel[1] = kk - excl;
+      } else {
+        sel[0] = 2046u - 2u * threadIdx.x;
+        sel[1] = kk - excl - h0;
+      }
+    }
+    __syncthreads();
+    prefix |= sel[0] << shift;
+    mask |= dmask << shift;
+    kk = sel[1];
+    __syncthreads();
+  }
+  // samples whose top 32 key bits equal the selected prefix; the answer is the kk-th largest of them
+  if (threadIdx.x == 0) *ncand = 0;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) {
+    const int i = j * blockDim.x + threadIdx.x;
+    if (i < N && kr[j] == prefix) {
+      const int slot = atomicAdd(ncand, 1);
+      if (slot < 32) cand[slot] = q[i];
+    }
+  }
+  __syncthreads();
+  const int nc = *ncand;
+  *ok = nc <= 32;
+  if (!*ok) return 0.0;
+  if (warp == 0) {
+    const uint64_t mine = lane < nc ? dkey(cand[lane]) : 0ull;
+    unsigned rank = 0;
+    for (int i = 0; i < nc; ++i) {
+      const uint64_t o = dkey(cand[i]);
+      rank += (o > mine || (o == mine && i < lane)) ? 1u : 0u;
+    }
+    if (lane < nc && rank == kk - 1) sel[0] = (unsigned)lane;
+  }
+  __syncthreads();
+  return cand[sel[0]];
+}
+
 // Pass 2 (one CTA): moments and, per CVaR risk, t* = argmin_t rho(z, t).
 // With K = N (1 - beta), k0 = floor(K) and v the (k0 + 1)-th largest QoI (the N-th
 // when k0 = N), the root of d rho/dt = 1 - S(t)/K, S(t) = sum_i s'_eps(Q_i - t), lies
@@ -164,82 +272,132 @@ __global__ void k_risk_moments(const double* __restrict__ q, int N, double* __re
 // Q_i <= v - eps exactly 0, so S(t) = C + sum over the window v - eps < Q_i < v + eps
 // (v itself is in it).  The window test runs on order-preserving integer keys.  In the
 // window coordinates y_i = (Q_i - v)/eps and t = v - eps theta, S = C + sum s'(y_i + theta)
-// with s'(y) = y^2 (3 - 2y) on (0, 1): an FP32 bisection on theta in [0, 1] brackets the
-// root, and an FP64 Illinois regula falsi (bracketing, so safe where S is flat) takes the
-// bracket down to adjacent doubles; the end rule is that of a plain bisection over
-// [min Q - eps, max Q]: lo if d rho/dt(lo) >= 0, else hi.  (Every FP64 instruction
-// occupies GB300's narrow FP64 pipe for a whole warp, so most of the search runs in FP32
-// and the window is spread over the lanes of one warp.)  params[r] = {t, mean, var}.
-__global__ void k_risk_select(const double* __restrict__ q, int N, const double* __restrict__ part, int nparts,
+// with s'(y) = y^2 (3 - 2y) on (0, 1), non-decreasing in theta: an FP32 Illinois regula
+// falsi on theta in [0, 1] narrows the bracket, and an FP64 one (bracketing, so safe where
+// S is flat) takes it to a few ulps; the end rule is that of a plain bisection over
+// [min Q - eps, max Q]: lo if d rho/dt(lo) >= 0, else hi.  Every FP64 instruction occupies
+// GB300's narrow FP64 pipe for a whole warp, so the FP64 work stays on one warp and the
+// block-wide parts are integer.  params[r] = {t, mean, var}.
+__global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restrict__ q, int N, const double* __restrict__ part, int nparts,
                               const RiskDev* __restrict__ risks, int n_risks, double* __restrict__ params) {
-  __shared__ double red[40];
-  __shared__ unsigned hist[256];
-  __shared__ unsigned sel[2];
+  __shared__ unsigned hist[2048];
+  __shared__ unsigned sel[2 + 64];
+  __shared__ double cand[32];
+  __shared__ int ncand;
   __shared__ double win[RISK_WINDOW_MAX];
+  __shared__ float winf[RISK_WINDOW_MAX];
   __shared__ int nwin;
-  __shared__ double s_t;
-  BlockRed br{red};
-  double s = 0.0, s2 = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-    s += part[2 * i];
-    s2 += part[2 * i + 1];
+  __shared__ double s_par[6];   // qbar, var, K, v, t
+  __shared__ int s_kq;
+  __shared__ bool s_ok;
+  __shared__ double red[40];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {   // moments from the per-block partial sums
+    double s = 0.0, s2 = 0.0;
+    for (int i = lane; i < nparts; i += 32) {
+      s += part[2 * i];
+      s2 += part[2 * i + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      const double invN = 1.0 / N;
+      s_par[0] = s * invN;
+      s_par[1] = fmax(s2 * invN - s_par[0] * s_par[0], 0.0);
+    }
   }
-  const double qbar = br.sum(s) / N;
-  const double var = fmax(br.sum(s2) / N - qbar * qbar, 0.0);
-  const int lane = threadIdx.x & 31;
+  __syncthreads();
+  const double qbar = s_par[0], var = s_par[1];
   for (int r = 0; r < n_risks; ++r) {
     const RiskDev R = risks[r];
     double t = R.t;
     if (R.kind == OUU_RISK_CVAR_SMOOTH && R.t_optimal) {
       const double eps = R.eps, ie = 1.0 / eps;
-      const double K = (double)N * (1.0 - R.beta);
-      int kq = (int)floor(K) + 1;
-      if (kq > N) kq = N;
-      if (kq < 1) kq = 1;
-      const double v = kth_largest<8>(q, N, kq, hist, sel);
-      const uint64_t khi = dkey(v + eps), klo = dkey(v - eps);
-      if (threadIdx.x == 0) nwin = 0;
-      __syncthreads();
-      unsigned cnt = 0;
-      for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const uint64_t k = dkey(q[i]);
-        if (k >= khi) cnt += 1u;
-        else if (k > klo) {
-          const int slot = atomicAdd(&nwin, 1);
-          if (slot < RISK_WINDOW_MAX) win[slot] = q[i];
-        }
+      if (threadIdx.x == 0) {
+        const double K = (double)N * (1.0 - R.beta);
+        int kq = (int)floor(K) + 1;
+        s_kq = kq > N ? N : (kq < 1 ? 1 : kq);
+        s_par[2] = K;
       }
-      const double C = br.sum((double)cnt);
+      __syncthreads();
+      const int kq = s_kq;
+      double v = 0.0;
+      bool okp = false;
+      if (N <= 16 * (int)blockDim.x) {
+        v = kth_largest_prefix(q, N, kq, hist, sel, cand, &ncand, &s_ok);
+        okp = s_ok;
+      }
+      if (!okp) v = kth_largest<8>(q, N, kq, hist, sel);
+      if (threadIdx.x == 0) {
+        s_par[3] = v + eps;
+        s_par[4] = v - eps;
+        nwin = 0;
+      }
+      __syncthreads();
+      const uint64_t khi = dkey(s_par[3]), klo = dkey(s_par[4]);
+      int C = 0;   // samples at or above v + eps (each contributes exactly 1)
+      for (int i0 = 0; i0 < N; i0 += blockDim.x) {   // uniform trip count for __syncthreads_count
+        const int i = i0 + threadIdx.x;
+        bool above = false;
+        if (i < N) {
+          const double qi = q[i];
+          const uint64_t k = dkey(qi);
+          above = k >= khi;
+          if (!above && k > klo) {
+            const int slot = atomicAdd(&nwin, 1);
+            if (slot < RISK_WINDOW_MAX) win[slot] = qi;
+          }
+        }
+        C += __syncthreads_count(above);
+      }
       const int W = nwin;
+      const double K = s_par[2];
       if (W <= RISK_WINDOW_MAX) {
-        if (threadIdx.x < 32) {
-          // FP32 bisection on theta (S(theta) = C + sum s'(y_i + theta) is non-decreasing):
-          // compares the window sum against K - C so that tiny targets keep their precision.
-          const float Tf = (float)(K - C);
-          float th_lo = 0.f, th_hi = 1.f;
-          for (int it = 0; it < 40; ++it) {
-            const float mid = 0.5f * (th_lo + th_hi);
-            if (mid <= th_lo || mid >= th_hi) break;
+        if (warp == 0) {
+          for (int i = lane; i < W; i += 32) winf[i] = (float)((win[i] - v) * ie);
+          __syncwarp();
+          // FP32 Illinois on F(theta) = sum_window s'(y_i + theta) - (K - C), non-decreasing on [0, 1]
+          const int act = W < 32 ? W : 32;
+          const float Tf = (float)(K - (double)C);
+          auto F = [&](float th) {
             float sp = 0.f;
             for (int i = lane; i < W; i += 32) {
-              const float y = (float)((win[i] - v) * ie) + mid;
+              const float y = winf[i] + th;
               sp += y <= 0.f ? 0.f : (y >= 1.f ? 1.f : y * y * (3.f - 2.f * y));
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
-            if (sp < Tf) th_lo = mid;
-            else th_hi = mid;
+            return warp_sum_active_f(sp, act) - Tf;
+          };
+          float th_lo = 0.f, th_hi = 1.f, flo = F(0.f), fhi = F(1.f);
+          if (flo < 0.f && fhi >= 0.f) {
+            int side = 0;
+            for (int it = 0; it < 24 && th_hi - th_lo > 1e-6f; ++it) {
+              float c = th_hi - fhi * (th_hi - th_lo) / (fhi - flo);
+              if (!(c > th_lo && c < th_hi)) c = 0.5f * (th_lo + th_hi);
+              const float fc = F(c);
+              if (fc < 0.f) {
+                th_lo = c;
+                flo = fc;
+                if (side == -1) fhi *= 0.5f;
+                side = -1;
+              } else {
+                th_hi = c;
+                fhi = fc;
+                if (side == 1) flo *= 0.5f;
+                side = 1;
+              }
+            }
           }
           // FP64 on G(t) = (K - C) - S_window(t), which has the sign of d rho/dt = 1 - S(t)/K
           // without a division: bracket check, then Illinois regula falsi (secant ratio in
           // FP32) until the bracket (lo: G < 0, hi: G >= 0) is a few ulps wide.
-          const double KC = K - C;
+          const double KC = K - (double)C;
           auto G = [&](double tt) {
             double S = 0.0;
             for (int i = lane; i < W; i += 32) S += splus_d1(win[i] - tt, eps, ie);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
-            return KC - S;
+            return KC - warp_sum_active(S, act);
           };
           double lo = v - eps * (double)th_hi, hi = v - eps * (double)th_lo;
           double glo = G(lo), ghi = G(hi);
@@ -271,12 +429,12 @@ __global__ void k_risk_select(const double* __restrict__ q, int N, const double*
               side = 1;
             }
           }
-          const double tt = glo >= 0.0 ? lo : hi;
-          if (threadIdx.x == 0) s_t = tt;
+          if (lane == 0) s_par[5] = glo >= 0.0 ? lo : hi;
         }
         __syncthreads();
-        t = s_t;
+        t = s_par[5];
       } else {
+        BlockRed br{red};
         double lo = v - eps, hi = v;
         for (int it = 0; it < 200; ++it) {
           const double mid = 0.5 * (lo + hi);
@@ -296,10 +454,14 @@ __global__ void k_risk_select(const double* __restrict__ q, int N, const double*
   }
 }
 
-// Pass 3 (many CTAs): weights w[r][i] and per-block partial sums of s_eps and s'_eps.
+// Pass 3 (many CTAs): weights w[r][i] and per-block partial sums of s_eps and s'_eps; the
+// last block to finish (an arrival counter, reset for the next call) combines the partial
+// sums into the risk values and d rho / dt.  out[3r..3r+2] = value, dt, t.
 __global__ void k_risk_apply(const double* __restrict__ q, int N, const RiskDev* __restrict__ risks, int n_risks,
-                             const double* __restrict__ params, double* __restrict__ w, double* __restrict__ part) {
+                             const double* __restrict__ params, double* __restrict__ w, double* __restrict__ part,
+                             unsigned* __restrict__ arrivals, double* __restrict__ out) {
   __shared__ double red[40];
+  __shared__ bool last;
   BlockRed br{red};
   for (int r = 0; r < n_risks; ++r) {
     const RiskDev R = risks[r];
@@ -319,53 +481,104 @@ __global__ void k_risk_apply(const double* __restrict__ q, int N, const RiskDev*
         sv += splus(x, R.eps, ie);
         sd += d1;
       }
-    }
-    const double tv = br.sum(sv);
-    const double td = br.sum(sd);
-    if (threadIdx.x == 0) {
-      part[(2 * r) * gridDim.x + blockIdx.x] = tv;
-      part[(2 * r + 1) * gridDim.x + blockIdx.x] = td;
+      const double tv = br.sum(sv);
+      const double td = br.sum(sd);
+      if (threadIdx.x == 0) {
+        part[(2 * r) * gridDim.x + blockIdx.x] = tv;
+        part[(2 * r + 1) * gridDim.x + blockIdx.x] = td;
+      }
     }
   }
-}
-
-// Pass 4 (one CTA): risk values and d rho / dt.  out[3r..3r+2] = value, dt, t.
-__global__ void k_risk_finish(int N, const RiskDev* __restrict__ risks, int n_risks, const double* __restrict__ params,
-                              const double* __restrict__ part, int nparts, double* __restrict__ out) {
-  __shared__ double red[40];
-  BlockRed br{red};
-  for (int r = 0; r < n_risks; ++r) {
-    const RiskDev R = risks[r];
-    double sv = 0.0, sd = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-      sv += part[(2 * r) * nparts + i];
-      sd += part[(2 * r + 1) * nparts + i];
-    }
-    const double tv = br.sum(sv), td = br.sum(sd);
-    if (threadIdx.x == 0) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(arrivals, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    for (int r = 0; r < n_risks; ++r) {
+      const RiskDev R = risks[r];
       const double t = params[3 * r], qbar = params[3 * r + 1], var = params[3 * r + 2];
       if (R.kind == OUU_RISK_MEAN_VAR) {
-        out[3 * r + 0] = qbar + R.kappa * var;
-        out[3 * r + 1] = 0.0;
-        out[3 * r + 2] = 0.0;
-      } else {
+        if (lane == 0) {
+          out[3 * r + 0] = qbar + R.kappa * var;
+          out[3 * r + 1] = 0.0;
+          out[3 * r + 2] = 0.0;
+        }
+        continue;
+      }
+      double sv = 0.0, sd = 0.0;
+      for (int i = lane; i < (int)gridDim.x; i += 32) {
+        sv += __ldcg(&part[(2 * r) * gridDim.x + i]);
+        sd += __ldcg(&part[(2 * r + 1) * gridDim.x + i]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+      }
+      if (lane == 0) {
         const double scale = 1.0 / ((double)N * (1.0 - R.beta));
-        out[3 * r + 0] = t + tv * scale;
-        out[3 * r + 1] = 1.0 - td * scale;
+        out[3 * r + 0] = t + sv * scale;
+        out[3 * r + 1] = 1.0 - sd * scale;
         out[3 * r + 2] = t;
       }
     }
-    __syncthreads();
+    if (lane == 0) *arrivals = 0u;
   }
 }
 
 void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
                          double* scratch, cudaStream_t s) {
-  static_assert(OUU_RISK_SCRATCH >= 3 * OUU_MAX_RISKS + 2 * OUU_MAX_RISKS * RISK_BLOCKS, "risk scratch size");
+  static_assert(OUU_RISK_SCRATCH >= 3 * OUU_MAX_RISKS + 2 * OUU_MAX_RISKS * RISK_BLOCKS + 1, "risk scratch size");
   double* params = scratch;
   double* part = scratch + 3 * OUU_MAX_RISKS;
   k_risk_moments<<<RISK_BLOCKS, 256, 0, s>>>(q, N, part);
   k_risk_select<<<1, 1024, 0, s>>>(q, N, part, RISK_BLOCKS, risks_dev, n_risks, params);
-  k_risk_apply<<<RISK_BLOCKS, 256, 0, s>>>(q, N, risks_dev, n_risks, params, w, part);
-  k_risk_finish<<<1, 256, 0, s>>>(N, risks_dev, n_risks, params, part, RISK_BLOCKS, out);
+  unsigned* arrivals = (unsigned*)(scratch + OUU_RISK_SCRATCH - 1);   // zeroed at problem creation
+  k_risk_apply<<<RISK_BLOCKS, 256, 0, s>>>(q, N, risks_dev, n_risks, params, w, part, arrivals, out);
+}
+
+// Kernel-level entry used by the risk-weight numerics test (declared in include/ouu_kernels.h).
+extern "C" ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const ouu_risk_desc* risks, int n_risks,
+                                              double* w_dev, double* out_host, void* stream) {
+  OUU_CHECK_ARG(q_dev && risks && w_dev && out_host, "null argument");
+  OUU_CHECK_ARG(N >= 1 && n_risks >= 1 && n_risks <= OUU_MAX_RISKS, "N >= 1 and 1 <= n_risks <= 4");
+  RiskDev rd[OUU_MAX_RISKS];
+  for (int r = 0; r < n_risks; ++r) {
+    rd[r].kind = risks[r].kind;
+    rd[r].kappa = risks[r].kappa;
+    rd[r].beta = risks[r].beta;
+    rd[r].eps = risks[r].eps;
+    rd[r].t = risks[r].t;
+    rd[r].t_optimal = risks[r].t_optimal;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  RiskDev* d_r = nullptr;
+  double* scr = nullptr;
+  double* d_out = nullptr;
+  ouu_status st = OUU_OK;
+  if (cudaMalloc((void**)&d_r, sizeof(rd)) != cudaSuccess || cudaMalloc((void**)&scr, OUU_RISK_SCRATCH * 8) != cudaSuccess ||
+      cudaMalloc((void**)&d_out, 3 * OUU_MAX_RISKS * 8) != cudaSuccess) {
+    ouu_set_error("cudaMalloc failed");
+    st = OUU_ERR_OOM;
+  } else if (cudaMemcpy(d_r, rd, sizeof(RiskDev) * n_risks, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemset(scr, 0, OUU_RISK_SCRATCH * 8) != cudaSuccess) {
+    ouu_set_error("risk set-up copy failed");
+    st = OUU_ERR_CUDA;
+  } else {
+    launch_risk_weights(q_dev, N, d_r, n_risks, w_dev, d_out, scr, s);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, d_out, (size_t)3 * n_risks * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      ouu_set_error(std::string("risk weights: ") + cudaGetErrorString(e));
+      st = OUU_ERR_CUDA;
+    }
+  }
+  cudaFree(d_r);
+  cudaFree(scr);
+  cudaFree(d_out);
+  return st;
 }

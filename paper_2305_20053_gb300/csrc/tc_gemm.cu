@@ -4,7 +4,8 @@
 //   warp 0 (one lane): TMA producer, 4-stage ring of 64-wide K blocks (SWIZZLE_128B)
 //   warp 1 (one lane): tcgen05.mma issuer (kind::f16, BF16 x BF16 -> FP32 in TMEM);
 //                      warp 1 also allocates / frees the tensor memory
-//   warps 2..5       : epilogue, one accumulator row (TMEM lane) per thread
+//   warps 2..5       : TMEM -> shared staging tile, one accumulator row (TMEM lane) per thread
+//   all 12 warps     : the fused epilogue over the staged tile, and the global stores
 // Every mbarrier wait is bounded (about 2 s of SM clock); on a timeout the CTA
 // drains its own TMA copies (bounded), frees its tensor memory and raises *err.
 #include <math.h>
@@ -16,7 +17,7 @@
 
 #define GEMM_BM 128
 #define GEMM_BK 64
-#define GEMM_THREADS 192
+#define GEMM_THREADS 384
 
 static __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 static __device__ __forceinline__ float gelu_d1f(float x) {
@@ -33,7 +34,7 @@ struct GemmStages {
 // Epilogue B: one pass over the staged tile in quads of four consecutive columns,
 // consecutive threads on consecutive quads of a row (16-byte shared loads, 16-byte FP32
 // and 8-byte BF16 global stores when ep.vec).  One compact loop per mode keeps the code
-// that every CTA runs once small.  MODE 3 = split-K partial sums, added atomically.
+// that every CTA runs once small.  MODE 7 = split-K partial sums, added atomically.
 template <int BN, int MODE>
 static __device__ __forceinline__ void epi_quads(float* stage, const float* sbias, const float* sscale, int m0,
                                                  int n0, int M, int N, const EpiParams& ep, bool keep) {
@@ -50,7 +51,7 @@ static __device__ __forceinline__ void epi_quads(float* stage, const float* sbia
     const float4 a4 = *reinterpret_cast<const float4*>(sp);
     const float acc[4] = {a4.x, a4.y, a4.z, a4.w};
     float y[4], o[4];
-    if (MODE == EPI_DGELU_SCALE) {
+    if (MODE == EPI_DGELU_SCALE || MODE == EPI_SCALE) {
       const float* ap = ep.aux + (size_t)(r / ep.aux_rdiv) * ep.ld_aux + c;
       float x[4] = {0.f, 0.f, 0.f, 0.f};
       if (full) {
@@ -59,8 +60,21 @@ static __device__ __forceinline__ void epi_quads(float* stage, const float* sbia
       } else {
         for (int j = 0; j < nv; ++j) x[j] = ap[j];
       }
+      if (MODE == EPI_SCALE) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) o[j] = y[j] = acc[j] * gelu_d1f(x[j]);
+        for (int j = 0; j < 4; ++j) o[j] = y[j] = acc[j] * x[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = y[j] = acc[j] * gelu_d1f(x[j]);
+      }
+    } else if (MODE == EPI_GELU_D) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {   // one erf and one exp give both gelu(a) and gelu'(a)
+        const float a = acc[j] + sbias[cc + j];
+        const float cdf = 0.5f * (1.f + erff(a * 0.70710678118654752f));
+        o[j] = a * cdf;
+        y[j] = cdf + a * 0.3989422804014327f * expf(-0.5f * a * a);
+      }
     } else if (MODE == EPI_GELU) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -72,7 +86,7 @@ static __device__ __forceinline__ void epi_quads(float* stage, const float* sbia
       for (int j = 0; j < 4; ++j) o[j] = y[j] = (alpha * acc[j] + sbias[cc + j]) * sscale[cc + j];
     }
     float* of = ep.out_f32 ? ep.out_f32 + (size_t)r * ep.ld_f32 + c : nullptr;
-    if (MODE == 3) {
+    if (MODE == 7) {
       if (full) {
         atomicAdd(reinterpret_cast<float4*>(of), make_float4(y[0], y[1], y[2], y[3]));
       } else {
@@ -202,7 +216,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       }
       tc_commit(tfull);   // completes once every MMA issued above has finished
     }
-  } else {
+  } else if (warp < 6) {
     // Epilogue A (warps 2..5): TMEM -> shared staging tile, one accumulator row per thread
     // (warp w may read TMEM lanes 32 (w % 4) .. +31).  The pipeline buffers are free once
     // every MMA has completed.
@@ -238,11 +252,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const bool keep = ep.out_t_bf16 != nullptr && !splitk;
     if (run) {
       if (splitk)
-        epi_quads<BN, 3>(stage, s_bias, s_scale, m0, n0, M, N, ep, false);
+        epi_quads<BN, 7>(stage, s_bias, s_scale, m0, n0, M, N, ep, false);
       else if (ep.mode == EPI_LINEAR)
         epi_quads<BN, EPI_LINEAR>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
       else if (ep.mode == EPI_GELU)
         epi_quads<BN, EPI_GELU>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
+      else if (ep.mode == EPI_GELU_D)
+        epi_quads<BN, EPI_GELU_D>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
+      else if (ep.mode == EPI_SCALE)
+        epi_quads<BN, EPI_SCALE>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
       else
         epi_quads<BN, EPI_DGELU_SCALE>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
     }
@@ -335,7 +353,9 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   OUU_CHECK_ARG(M >= 1 && N >= 1 && K >= 1, "GEMM sizes must be positive");
   OUU_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0, "GEMM operands must be 16-byte aligned");
   OUU_CHECK_ARG(lda % 8 == 0 && ldb % 8 == 0 && lda >= K && ldb >= K, "GEMM leading dimensions: multiple of 8, >= K");
-  OUU_CHECK_ARG(ep.mode != EPI_DGELU_SCALE || (ep.aux && ep.aux_rdiv >= 1), "EPI_DGELU_SCALE needs aux");
+  OUU_CHECK_ARG(ep.mode >= EPI_LINEAR && ep.mode <= EPI_SCALE, "unknown epilogue mode");
+  OUU_CHECK_ARG((ep.mode != EPI_DGELU_SCALE && ep.mode != EPI_SCALE) || (ep.aux && ep.aux_rdiv >= 1),
+                "EPI_DGELU_SCALE and EPI_SCALE need aux");
   OUU_CHECK_ARG(splits >= 1 && splits <= 64, "split-K factor in [1, 64]");
   OUU_CHECK_ARG(splits == 1 || (ep.mode == EPI_LINEAR && ep.out_f32 && !ep.out_bf16 && !ep.out_t_bf16 &&
                                 !ep.out2_bf16 && !ep.col_scale && !ep.accumulate),
@@ -345,20 +365,31 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   auto al = [](const void* q, uintptr_t a, int ld) { return q == nullptr || (((uintptr_t)q % a) == 0 && ld % 4 == 0); };
   EpiParams e2 = ep;
   e2.vec = al(ep.out_f32, 16, ep.ld_f32) && al(ep.out_bf16, 8, ep.ld_bf16) && al(ep.out2_bf16, 8, ep.ld2) &&
-           (ep.mode != EPI_DGELU_SCALE || al(ep.aux, 16, ep.ld_aux));
+           ((ep.mode != EPI_DGELU_SCALE && ep.mode != EPI_SCALE) || al(ep.aux, 16, ep.ld_aux));
   CUtensorMap ta;
   if (!ouu_tmap_bf16(&ta, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda, GEMM_BM)) {
     ouu_set_error("tensor map for GEMM operand A failed (alignment or driver entry point)");
     return OUU_ERR_INVALID_ARG;
   }
-  // N tile with the least padding (ties: the wider tile).
+  // N tile: a CTA's time is mostly fixed latency (TMA round trips, MMA commit, epilogue)
+  // plus a part that grows with BN, and tiles beyond one per SM run in a further wave;
+  // pick the tile that minimises waves x (BN + 64) (ties: the wider tile).
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
   static const int cands[] = {256, 208, 128, 112, 80, 64};
   int best = 64;
-  long best_pad = 1L << 40;
+  long best_cost = 1L << 60;
+  const long mt = (long)((M + GEMM_BM - 1) / GEMM_BM) * splits;
   for (int bn : cands) {
-    const long pad = (long)((N + bn - 1) / bn) * bn - N;
-    if (pad < best_pad) {
-      best_pad = pad;
+    const long tiles = mt * ((N + bn - 1) / bn);
+    const long cost = ((tiles + sms - 1) / sms) * (bn + 64);
+    if (cost < best_cost) {
+      best_cost = cost;
       best = bn;
     }
   }

@@ -12,6 +12,8 @@ enum EpiMode {
   EPI_LINEAR = 0,       // y = alpha * acc + bias[c]
   EPI_GELU = 1,         // a = acc + bias[c]; out_f32 = a; bf16 outputs = gelu(a)
   EPI_DGELU_SCALE = 2,  // y = acc * gelu'(aux[(r / aux_rdiv) * ld_aux + c]); out2 = bf16(acc)
+  EPI_GELU_D = 3,       // a = acc + bias[c]; out_f32 = gelu'(a); bf16 outputs = gelu(a)
+  EPI_SCALE = 4,        // y = acc * aux[(r / aux_rdiv) * ld_aux + c]
 };
 
 struct EpiParams {
@@ -28,7 +30,7 @@ struct EpiParams {
   int ld_t;
   __nv_bfloat16* out2_bf16;       // [M][ld2]: bf16(acc) before scaling (EPI_DGELU_SCALE) or null
   int ld2;
-  const float* aux;               // pre-activations for gelu' (EPI_DGELU_SCALE)
+  const float* aux;               // EPI_DGELU_SCALE: pre-activations; EPI_SCALE: factors
   int ld_aux;
   int aux_rdiv;
   int vec;                        // set by ouu_gemm_bf16: vector epilogue accesses are aligned

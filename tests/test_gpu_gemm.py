@@ -112,3 +112,42 @@ def test_tangent_scaling_epilogue():
     scale = _gelu_d1(aux).repeat_interleave(dz, dim=0)
     _close(out, acc * scale, 2 * _tol(K))
     _close(ad.float(), acc, 2 ** -8 + _tol(K))
+
+
+def test_gelu_with_derivative_epilogue():
+    """Mode 3 (forward layer of the evaluation): BF16 gelu(a) and FP32 gelu'(a), a = acc + bias."""
+    from paper_2305_20053_gb300 import capi
+    M, N, K = 300, 400, 200
+    A = _bf((M, K), seed=13)
+    B = _bf((N, K), seed=14, scale=1.0 / 14)
+    bias = 0.1 * torch.randn(N, device="cuda")
+    d = torch.empty(M, N, device="cuda")
+    h = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    capi.ouu_kernel_gemm_bf16(A, B, M, N, K, mode=3, bias=bias, out_f32=d, out_bf16=h, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    a = _ref(A, B, K) + bias
+    # gelu' has slope <= 0.6 in a: the FP32 summation error of a carries over at most that factor
+    _close(d, _gelu_d1(a), _tol(K))
+    g = torch.nn.functional.gelu(a)
+    assert (h.float() - g).abs().max().item() <= 2 ** -8 * g.abs().max().item() + 1e-4
+
+
+def test_scale_epilogue():
+    """Mode 4 (reverse layer of the evaluation): y = acc * aux, per-row factors repeated aux_rdiv times."""
+    from paper_2305_20053_gb300 import capi
+    B_, rd, N, K = 40, 3, 200, 400
+    M = B_ * rd
+    A = _bf((M, K), seed=15)
+    W = _bf((N, K), seed=16, scale=1.0 / 20)
+    aux = torch.randn(B_, N, device="cuda")
+    out = torch.empty(M, N, device="cuda")
+    hb = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    capi.ouu_kernel_gemm_bf16(A, W, M, N, K, mode=4, aux=aux, aux_rdiv=rd, out_f32=out, out_bf16=hb, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = _ref(A, W, K) * aux.repeat_interleave(rd, dim=0)
+    _close(out, ref, 2 * _tol(K))
+    _close(hb.float(), ref, 2 ** -8 + 2 * _tol(K))
