@@ -89,8 +89,7 @@ typedef struct {
   float ms_adjoint;             /* batched adjoint solve */
   float ms_reduce;              /* weighted adjoint sum and G^T */
   float ms_total;               /* whole evaluation on the device */
-  float ms_cast;                /* DINO: FP64 -> BF16 cast of the fields (single-chunk evaluations) */
-  float ms_project;             /* DINO: KL projection GEMM (single-chunk evaluations) */
+  float ms_project;             /* DINO: fused KL projection of the FP64 fields */
   float ms_network;             /* DINO: network forward + reverse-mode gradient */
 } ouu_eval_stats;
 

@@ -52,7 +52,7 @@ class EvalStats(ctypes.Structure):
     _fields_ = [("newton_min", ctypes.c_int), ("newton_max", ctypes.c_int), ("newton_mean", ctypes.c_double),
                 ("cg_total", ctypes.c_int), ("adjoint_solves", ctypes.c_int), ("n_not_converged", ctypes.c_int),
                 ("ms_state", ctypes.c_float), ("ms_weights", ctypes.c_float), ("ms_adjoint", ctypes.c_float),
-                ("ms_reduce", ctypes.c_float), ("ms_total", ctypes.c_float), ("ms_cast", ctypes.c_float),
+                ("ms_reduce", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("ms_project", ctypes.c_float), ("ms_network", ctypes.c_float)]
 
 

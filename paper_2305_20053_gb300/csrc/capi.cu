@@ -477,8 +477,7 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
         cudaEventElapsedTime(&stats->ms_state, p->ev[0], p->ev[1]);
         cudaEventElapsedTime(&stats->ms_weights, p->ev[1], p->ev[2]);
         cudaEventElapsedTime(&stats->ms_reduce, p->ev[2], p->ev[3]);
-        cudaEventElapsedTime(&stats->ms_cast, dino->ev[0], dino->ev[1]);
-        cudaEventElapsedTime(&stats->ms_project, dino->ev[1], dino->ev[2]);
+        cudaEventElapsedTime(&stats->ms_project, dino->ev[0], dino->ev[2]);
         cudaEventElapsedTime(&stats->ms_network, dino->ev[2], dino->ev[3]);
       }
     }

@@ -599,10 +599,7 @@ static ouu_status check_err(ouu_dino* d) {
 // With mark, events ev[0] / ev[1] / ev[2] bracket the first chunk's cast and GEMM.
 static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi, bool mark = false) {
   // one fused pass over the FP64 fields (kl_project.cu); the bias -W mbar carries the prior mean
-  if (mark && !d->capturing) {
-    OUU_CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
-    OUU_CUDA_TRY(cudaEventRecord(d->ev[1], d->stream));
-  }
+  if (mark && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
   DINO_TRY(ouu_kl_project(m, count, d->nn, d->d_wkl, d->nnp, d->rm, d->d_klbias, xi, d->d_err, d->num_sms, d->stream));
   if (mark && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
   return OUU_OK;

@@ -1,9 +1,9 @@
 // Persistent per-sample PDE kernels: one CTA solves one sample at a time and pulls
 // the next sample index from a global counter (samples differ in Newton/CG
 // iteration counts, so the work is balanced dynamically).  A CTA's fine-grid
-// vectors live in its own workspace slot (about 1.5 MB at 129 x 129, so the
-// slots of all resident CTAs stay in the 126 MB L2); multigrid levels of at most
-// 65 x 65 nodes live in shared memory.
+// vectors live in its own workspace slot (about 1.5 MB at 129 x 129, of which the
+// FP32 CG working set is 0.6 MB, so that set of all 152 resident CTAs stays in the
+// 126 MB L2); multigrid levels of at most 65 x 65 nodes live in shared memory.
 #include "ouu_internal.cuh"
 #include "dino.cuh"
 
