@@ -53,8 +53,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--backend", default="dino", choices=["dino", "pde"])
     ap.add_argument("--pde-steps", type=int, default=3)
-    ap.add_argument("--train", type=int, default=16384, help="training pairs for the surrogate")
-    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--train", type=int, default=32768, help="training pairs for the surrogate")
+    ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--lr-final", type=float, default=1e-5,
+                    help="geometric decay of the second half's rate down to this (0: keep 2.5e-4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -302,8 +304,11 @@ def run_ours(args):
         D = T.make_dino(n, L, r=R_M, width=WIDTH, max_batch=256, max_eval=N)
         T.init_params(D)
         data = T.generate_training_data(P, D, args.train)
-        train_s, losses = T.train(D, data, epochs=args.epochs, batch=256, log_every=max(1, args.epochs // 4))
-        recipe = {"train_pairs": args.train, "epochs": args.epochs, "batch": 256, "lr": "1e-3 -> 2.5e-4 at half",
+        lr_final = args.lr_final if args.lr_final > 0 else None
+        train_s, losses = T.train(D, data, epochs=args.epochs, batch=256, log_every=max(1, args.epochs // 4),
+                                  lr_final=lr_final)
+        lr_txt = "1e-3, then 2.5e-4 from half" + (f" decaying geometrically to {lr_final:g}" if lr_final else "")
+        recipe = {"train_pairs": args.train, "epochs": args.epochs, "batch": 256, "lr": lr_txt,
                   "pod_snapshots": min(args.train, 1024), "r_m": R_M, "r_u": R_U, "width": WIDTH,
                   "construction_s": {**{k: round(v, 3) for k, v in data.times.items()}, "train_s": round(train_s, 3)},
                   "final_loss": losses[-1][1] if losses else None}

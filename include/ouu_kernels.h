@@ -20,7 +20,7 @@
  *
  * ouu_kernel_kl_project: the fused KL projection of Sec. 3.3's input reduction,
  *   xi[s][c] = bias[c] + sum_k bf16(m[s][k]) W[c][k],   s < N, c < rm, k < nn,
- * reading the FP64 fields m [N][nn] (device, 16-byte aligned, row-major) once; the
+ * reading the FP64 fields m [N][nn] (device, 8-byte aligned, row-major) once; the
  * rounding to BF16 goes through FP32 (both to nearest even).  W: device BF16
  * [rm][ldw] (ldw a multiple of 8, >= nn).  bias: device FP32 [rm].  xi: device FP32
  * [N][rm], overwritten.  rm <= 240.  err_dev as above.

@@ -385,6 +385,7 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
     rd[r].eps = risks[r].eps;
     rd[r].t = risks[r].t;
     rd[r].t_optimal = risks[r].t_optimal;
+    risk_dev_finish(rd[r], n_samples);
   }
   const int dz = p->dz;
   double* d_res = p->d_out;                         // [n_risks][3]

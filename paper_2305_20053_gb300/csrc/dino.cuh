@@ -78,7 +78,7 @@ ouu_status dino_install_bases(ouu_dino* d);
 void dino_weighted_grads(ouu_dino* d, const double* w, int N, int n_w, double* out);
 // Jacobian-data solves (pde.cu): jy[i][j][r] = h^2 Phi_r . J(u_i)^-1 g_j.
 // Fused KL projection of FP64 fields (kl_project.cu): xi[N][rm] = bf16(m) W^T + bias with
-// W = [rm][ldw] BF16 (K = nn contiguous); xi is zeroed here.  m 16-byte aligned, rm <= 240.
+// W = [rm][ldw] BF16 (K = nn contiguous); xi is zeroed here.  m 8-byte aligned, rm <= 240.
 ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W, int ldw, int rm, const float* bias,
                           float* xi, int* err, int num_sms, cudaStream_t s);
 

@@ -9,8 +9,9 @@
 //                  a tensor map needs; the fields are then read as rows of sample PAIRS
 //                  (stride 2 n^2 * 8 bytes), even samples from x = k0 and odd samples from
 //                  x = n^2 + k0 - 1 (one element early, so that x stays 16-byte aligned),
-//                  66 elements each: two copies per K block.  A last unpaired sample (N odd)
-//                  is read with plain loads.
+//                  66 elements each: two copies per K block.  A last unpaired sample (N odd),
+//                  and every sample when the base is not 16-byte aligned, is read with plain
+//                  loads.
 //   warps 0..15  : converters.  FP64 -> BF16 (round to FP32, then to BF16, both to nearest
 //                  even; the first step in integer arithmetic, as the FP64 pipe is narrow)
 //                  written straight into the swizzled K-major A tile that tcgen05.mma reads.
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
         }
         uint8_t* dst = sF + s * KLP_F64_STAGE;
         if (a.n_tma == 0) {
-          mbar_arrive(&f64_full[s]);   // a single sample with n^2 odd: plain loads only
+          mbar_arrive(&f64_full[s]);   // plain loads only
         } else if (a.pair) {
           mbar_expect_tx(&f64_full[s], fbytes);
           tma_load_2d(dst, &tm, k0, t * 64, &f64_full[s]);
@@ -320,7 +321,7 @@ ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W
                           float* xi, int* err, int num_sms, cudaStream_t s) {
   OUU_CHECK_ARG(m && W && bias && xi && err, "null argument");
   OUU_CHECK_ARG(N >= 1 && nn >= 1 && rm >= 1 && rm <= 240, "KL projection sizes: N, n^2 >= 1, 1 <= r_m <= 240");
-  OUU_CHECK_ARG(((uintptr_t)m & 15) == 0, "fields must be 16-byte aligned");
+  OUU_CHECK_ARG(((uintptr_t)m & 7) == 0, "fields must be 8-byte aligned");
   const int BN = (rm + 15) / 16 * 16;
   CUtensorMap tw;
   if (!ouu_tmap_bf16(&tw, W, (uint64_t)nn, (uint64_t)rm, (uint64_t)ldw, (uint32_t)BN)) {
@@ -328,8 +329,10 @@ ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W
     return OUU_ERR_INVALID_ARG;
   }
   // fields tensor map: sample rows (n^2 even) or sample pairs (n^2 odd)
+  // A base that is not 16-byte aligned (a slice starting at an odd sample) cannot be a
+  // tensor map's base: every row then goes by plain loads.
   const int pair = nn & 1;
-  const int n_tma = pair ? N / 2 * 2 : N;
+  const int n_tma = ((uintptr_t)m & 15) ? 0 : (pair ? N / 2 * 2 : N);
   CUtensorMap tm;
   if (n_tma > 0) {
     const bool okm = pair ? ouu_tmap_2d(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, m, 2 * (uint64_t)nn, (uint64_t)(N / 2),
@@ -341,7 +344,7 @@ ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W
       return OUU_ERR_INVALID_ARG;
     }
   } else {
-    tm = tw;   // never read: N = 1 with n^2 odd goes by plain loads
+    tm = tw;   // never read: every row goes by plain loads
   }
   KlpArgs a;
   a.pair = pair;

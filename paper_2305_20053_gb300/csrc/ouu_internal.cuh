@@ -127,7 +127,21 @@ struct RiskDev {
   int kind;
   double kappa, beta, eps, t;
   int t_optimal;
+  // set on the host for the call's N (risk_dev_finish), so that no device thread divides in
+  // FP64: K = N (1 - beta), the rank kq = floor(K) + 1 (clamped to [1, N]) of the sample that
+  // opens the CVaR window, 1 / eps, 1 / K and 1 / N
+  double K, inv_eps, inv_K, inv_N;
+  int kq;
 };
+
+inline void risk_dev_finish(RiskDev& r, int N) {
+  r.K = (double)N * (1.0 - r.beta);
+  int kq = (int)(r.K) + 1;   // floor for K >= 0
+  r.kq = kq > N ? N : (kq < 1 ? 1 : kq);
+  r.inv_eps = r.eps > 0.0 ? 1.0 / r.eps : 0.0;
+  r.inv_K = r.K > 0.0 ? 1.0 / r.K : 0.0;
+  r.inv_N = 1.0 / (double)N;
+}
 
 // Per-risk weights w[r][i], value[r], dt[r], t[r] from q[N] (moments on many CTAs, t*
 // selection on one, weights on many).  out layout: value[r], dt[r], t[r] at out[3r+0..2].

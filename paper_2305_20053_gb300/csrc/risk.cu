@@ -170,18 +170,22 @@ static __device__ __forceinline__ float warp_sum_active_f(float v, int active) {
   return __shfl_sync(0xffffffffu, v, 0);
 }
 
-// k-th largest (1-based) of q[0, N) for N <= 16 * blockDim.x: an 11/11/10-bit radix select
-// on the top 32 bits of the order-preserving keys (held in registers), then an exact choice
-// among the samples that share those 32 bits (at most 32 of them; otherwise *ok = false).
-static __device__ double kth_largest_prefix(const double* q, int N, int k, unsigned* hist, unsigned* sel,
-                                            double* cand, int* ncand, bool* ok) {
-  constexpr int KPT = 16;
-  uint32_t kr[KPT];
+// Top 32 bits of the order-preserving keys of q[0, N), N <= KEYS_PER_THREAD * blockDim.x.
+#define KEYS_PER_THREAD 16
+static __device__ __forceinline__ void load_key_prefixes(const double* q, int N, uint32_t (&kr)[KEYS_PER_THREAD]) {
 #pragma unroll
-  for (int j = 0; j < KPT; ++j) {
+  for (int j = 0; j < KEYS_PER_THREAD; ++j) {
     const int i = j * blockDim.x + threadIdx.x;
     kr[j] = i < N ? (uint32_t)(dkey(q[i]) >> 32) : 0u;
   }
+}
+
+// k-th largest (1-based) of q[0, N) for N <= 16 * blockDim.x: an 11/11/10-bit radix select
+// on the top 32 bits of the order-preserving keys (held in registers), then an exact choice
+// among the samples that share those 32 bits (at most 32 of them; otherwise *ok = false).
+static __device__ double kth_largest_prefix(const double* q, int N, int k, const uint32_t (&kr)[KEYS_PER_THREAD],
+                                            unsigned* hist, unsigned* sel, double* cand, int* ncand, bool* ok) {
+  constexpr int KPT = KEYS_PER_THREAD;
   uint32_t prefix = 0, mask = 0;
   unsigned kk = (unsigned)k;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -287,11 +291,16 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
   __shared__ double win[RISK_WINDOW_MAX];
   __shared__ float winf[RISK_WINDOW_MAX];
   __shared__ int nwin;
-  __shared__ double s_par[6];   // qbar, var, K, v, t
-  __shared__ int s_kq;
+  __shared__ double s_par[6];   // qbar, var, -, v + eps, v - eps, t
   __shared__ bool s_ok;
   __shared__ double red[40];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // key prefixes first: their loads are in flight while warp 0 combines the moments
+  bool need_select = false;
+  for (int r = 0; r < n_risks; ++r) need_select |= risks[r].kind == OUU_RISK_CVAR_SMOOTH && risks[r].t_optimal;
+  const bool prefix_path = need_select && N <= KEYS_PER_THREAD * (int)blockDim.x;
+  uint32_t kr[KEYS_PER_THREAD];
+  if (prefix_path) load_key_prefixes(q, N, kr);
   if (warp == 0) {   // moments from the per-block partial sums
     double s = 0.0, s2 = 0.0;
     for (int i = lane; i < nparts; i += 32) {
@@ -315,19 +324,12 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
     const RiskDev R = risks[r];
     double t = R.t;
     if (R.kind == OUU_RISK_CVAR_SMOOTH && R.t_optimal) {
-      const double eps = R.eps, ie = 1.0 / eps;
-      if (threadIdx.x == 0) {
-        const double K = (double)N * (1.0 - R.beta);
-        int kq = (int)floor(K) + 1;
-        s_kq = kq > N ? N : (kq < 1 ? 1 : kq);
-        s_par[2] = K;
-      }
-      __syncthreads();
-      const int kq = s_kq;
+      const double eps = R.eps, ie = R.inv_eps;
+      const int kq = R.kq;
       double v = 0.0;
       bool okp = false;
-      if (N <= 16 * (int)blockDim.x) {
-        v = kth_largest_prefix(q, N, kq, hist, sel, cand, &ncand, &s_ok);
+      if (prefix_path) {
+        v = kth_largest_prefix(q, N, kq, kr, hist, sel, cand, &ncand, &s_ok);
         okp = s_ok;
       }
       if (!okp) v = kth_largest<8>(q, N, kq, hist, sel);
@@ -354,82 +356,91 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
         C += __syncthreads_count(above);
       }
       const int W = nwin;
-      const double K = s_par[2];
+      const double K = R.K;
       if (W <= RISK_WINDOW_MAX) {
         if (warp == 0) {
           for (int i = lane; i < W; i += 32) winf[i] = (float)((win[i] - v) * ie);
           __syncwarp();
-          // FP32 Illinois on F(theta) = sum_window s'(y_i + theta) - (K - C), non-decreasing on [0, 1]
+          // Safeguarded Newton, first in FP32 on theta in [0, 1] (F(theta) = sum_window
+          // s'(y_i + theta) - (K - C), non-decreasing, F' = sum 6 y (1 - y)), then in FP64 on
+          // G(t) = (K - C) - S_window(t) (the sign of d rho/dt = 1 - S(t)/K without a
+          // division; G' = sum 6 y (1 - y) / eps): a step that leaves the bracket, or meets
+          // G' = 0, bisects instead.  The end rule then walks to adjacent doubles.
           const int act = W < 32 ? W : 32;
           const float Tf = (float)(K - (double)C);
-          auto F = [&](float th) {
-            float sp = 0.f;
+          float th = 0.5f, tlo = 0.f, thi = 1.f;
+          for (int it = 0; it < 4; ++it) {
+            float f = 0.f, fp = 0.f;
             for (int i = lane; i < W; i += 32) {
               const float y = winf[i] + th;
-              sp += y <= 0.f ? 0.f : (y >= 1.f ? 1.f : y * y * (3.f - 2.f * y));
-            }
-            return warp_sum_active_f(sp, act) - Tf;
-          };
-          float th_lo = 0.f, th_hi = 1.f, flo = F(0.f), fhi = F(1.f);
-          if (flo < 0.f && fhi >= 0.f) {
-            int side = 0;
-            for (int it = 0; it < 24 && th_hi - th_lo > 1e-6f; ++it) {
-              float c = th_hi - fhi * (th_hi - th_lo) / (fhi - flo);
-              if (!(c > th_lo && c < th_hi)) c = 0.5f * (th_lo + th_hi);
-              const float fc = F(c);
-              if (fc < 0.f) {
-                th_lo = c;
-                flo = fc;
-                if (side == -1) fhi *= 0.5f;
-                side = -1;
-              } else {
-                th_hi = c;
-                fhi = fc;
-                if (side == 1) flo *= 0.5f;
-                side = 1;
+              if (y >= 1.f) f += 1.f;
+              else if (y > 0.f) {
+                f += y * y * (3.f - 2.f * y);
+                fp += 6.f * y * (1.f - y);
               }
             }
+            f = warp_sum_active_f(f, act) - Tf;
+            fp = warp_sum_active_f(fp, act);
+            if (f < 0.f) tlo = th;
+            else thi = th;
+            float nt = fp > 0.f ? th - f / fp : 0.5f * (tlo + thi);
+            if (!(nt > tlo && nt < thi)) nt = 0.5f * (tlo + thi);
+            th = nt;
           }
-          // FP64 on G(t) = (K - C) - S_window(t), which has the sign of d rho/dt = 1 - S(t)/K
-          // without a division: bracket check, then Illinois regula falsi (secant ratio in
-          // FP32) until the bracket (lo: G < 0, hi: G >= 0) is a few ulps wide.
           const double KC = K - (double)C;
-          auto G = [&](double tt) {
-            double S = 0.0;
-            for (int i = lane; i < W; i += 32) S += splus_d1(win[i] - tt, eps, ie);
+          double lo = v - eps, hi = v, t = v - eps * (double)th;
+          bool lo_neg = false;   // G(lo) < 0 was evaluated
+          auto G = [&](double tt, double* dG) {
+            double S = 0.0, Sp = 0.0;
+            for (int i = lane; i < W; i += 32) {
+              const double x = win[i] - tt;
+              if (x >= eps) S += 1.0;
+              else if (x > 0.0) {
+                const double y = x * ie;
+                S += y * y * (3.0 - 2.0 * y);
+                Sp += 6.0 * y * (1.0 - y);
+              }
+            }
+            if (dG) *dG = warp_sum_active(Sp, act) * ie;
             return KC - warp_sum_active(S, act);
           };
-          double lo = v - eps * (double)th_hi, hi = v - eps * (double)th_lo;
-          double glo = G(lo), ghi = G(hi);
-          if (!(glo < 0.0)) {
-            lo = v - eps;
-            glo = G(lo);
-          }
-          if (!(ghi >= 0.0)) {
-            hi = v;
-            ghi = G(hi);
-          }
-          int side = 0;
-          for (int it = 0; it < 60 && glo < 0.0; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi || hi - lo <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) break;
-            const float ratio = (float)ghi / ((float)ghi - (float)glo);
-            double c = hi - (double)ratio * (hi - lo);
-            if (!(c > lo && c < hi)) c = mid;
-            const double gc = G(c);
-            if (gc < 0.0) {
-              lo = c;
-              glo = gc;
-              if (side == -1) ghi *= 0.5;
-              side = -1;
+          for (int it = 0; it < 64; ++it) {
+            double dg;
+            const double g = G(t, &dg);
+            if (g < 0.0) {
+              lo = t;
+              lo_neg = true;
             } else {
-              hi = c;
-              ghi = gc;
-              if (side == 1) glo *= 0.5;
-              side = 1;
+              hi = t;
             }
+            if (hi - lo <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) break;
+            const double step = dg > 0.0 ? g / dg : INFINITY;
+            double nt;
+            if (fabs(step) <= 2.220446049250313e-16 * fabs(t)) {   // converged: bracket t tightly
+              const double a = nextafter(t, -INFINITY), b = nextafter(t, INFINITY);
+              if (G(a, nullptr) < 0.0) {
+                lo = fmax(lo, a);
+                lo_neg = true;
+              } else {
+                hi = fmin(hi, a);
+              }
+              if (G(b, nullptr) < 0.0) {
+                lo = fmax(lo, b);
+                lo_neg = true;
+              } else {
+                hi = fmin(hi, b);
+              }
+              if (hi - lo <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) break;
+              nt = 0.5 * (lo + hi);
+            } else {
+              nt = t - step;
+              if (!(nt > lo && nt < hi) || (it >= 8 && it % 2 == 0)) nt = 0.5 * (lo + hi);   // bisect when slow
+            }
+            t = nt;
           }
-          if (lane == 0) s_par[5] = glo >= 0.0 ? lo : hi;
+          // bisection end rule: lo if G(lo) >= 0 (possible only for the unevaluated v - eps), else hi
+          const bool take_lo = !lo_neg && G(lo, nullptr) >= 0.0;
+          if (lane == 0) s_par[5] = take_lo ? lo : hi;
         }
         __syncthreads();
         t = s_par[5];
@@ -469,11 +480,11 @@ __global__ void k_risk_apply(const double* __restrict__ q, int N, const RiskDev*
     double* wr = w + (int64_t)r * N;
     double sv = 0.0, sd = 0.0;
     if (R.kind == OUU_RISK_MEAN_VAR) {
-      const double invN = 1.0 / N, k2 = 2.0 * R.kappa;
+      const double invN = R.inv_N, k2 = 2.0 * R.kappa;
       for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
         wr[i] = (1.0 + k2 * (q[i] - qbar)) * invN;
     } else {
-      const double scale = 1.0 / ((double)N * (1.0 - R.beta)), ie = 1.0 / R.eps;
+      const double scale = R.inv_K, ie = R.inv_eps;
       for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const double x = q[i] - t;
         const double d1 = splus_d1(x, R.eps, ie);
@@ -519,7 +530,7 @@ __global__ void k_risk_apply(const double* __restrict__ q, int N, const RiskDev*
         sd += __shfl_xor_sync(0xffffffffu, sd, o);
       }
       if (lane == 0) {
-        const double scale = 1.0 / ((double)N * (1.0 - R.beta));
+        const double scale = R.inv_K;
         out[3 * r + 0] = t + sv * scale;
         out[3 * r + 1] = 1.0 - sd * scale;
         out[3 * r + 2] = t;
@@ -545,6 +556,10 @@ extern "C" ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const 
                                               double* w_dev, double* out_host, void* stream) {
   OUU_CHECK_ARG(q_dev && risks && w_dev && out_host, "null argument");
   OUU_CHECK_ARG(N >= 1 && n_risks >= 1 && n_risks <= OUU_MAX_RISKS, "N >= 1 and 1 <= n_risks <= 4");
+  for (int r = 0; r < n_risks; ++r)
+    OUU_CHECK_ARG(risks[r].kind == OUU_RISK_MEAN_VAR ||
+                      (risks[r].kind == OUU_RISK_CVAR_SMOOTH && risks[r].eps > 0 && risks[r].beta >= 0 && risks[r].beta < 1),
+                  "risk descriptor: kind, and for CVaR eps > 0 and beta in [0, 1)");
   RiskDev rd[OUU_MAX_RISKS];
   for (int r = 0; r < n_risks; ++r) {
     rd[r].kind = risks[r].kind;
@@ -553,6 +568,7 @@ extern "C" ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const 
     rd[r].eps = risks[r].eps;
     rd[r].t = risks[r].t;
     rd[r].t_optimal = risks[r].t_optimal;
+    risk_dev_finish(rd[r], N);
   }
   cudaStream_t s = (cudaStream_t)stream;
   RiskDev* d_r = nullptr;

@@ -89,9 +89,20 @@ def generate_training_data(P, D, n_train, seed_fields=SEED_TRAIN_FIELDS, seed_z=
     return TrainData(xi, z.float(), y, jy, eig, t)
 
 
-def train(D, data, epochs=200, batch=256, lr0=1e-3, lr1=2.5e-4, seed=SEED_NET, log_every=0):
-    """Adam over `epochs` passes of seeded shuffles; the rate drops from lr0 to lr1 at
-    half of the epochs (Sec. 4.2).  Returns (seconds, per-epoch losses sampled)."""
+def lr_at(ep, epochs, lr0=1e-3, lr1=2.5e-4, lr_final=None):
+    """lr0 for the first half of the epochs, then lr1 (Sec. 4.2); with lr_final the second
+    half decays geometrically from lr1 to lr_final instead of staying at lr1."""
+    half = epochs // 2
+    if ep < half:
+        return lr0
+    if lr_final is None or epochs - half <= 1:
+        return lr1
+    return lr1 * (lr_final / lr1) ** ((ep - half) / (epochs - half - 1))
+
+
+def train(D, data, epochs=200, batch=256, lr0=1e-3, lr1=2.5e-4, seed=SEED_NET, log_every=0, lr_final=None):
+    """Adam over `epochs` passes of seeded shuffles with the rate of lr_at.
+    Returns (seconds, per-epoch losses sampled)."""
     import torch
     n_train = data.xi.shape[0]
     steps = n_train // batch
@@ -100,7 +111,7 @@ def train(D, data, epochs=200, batch=256, lr0=1e-3, lr1=2.5e-4, seed=SEED_NET, l
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for ep in range(epochs):
-        lr = lr0 if ep < epochs // 2 else lr1
+        lr = lr_at(ep, epochs, lr0, lr1, lr_final)
         for s in range(steps):
             idx = orders[ep, s * batch:(s + 1) * batch]
             want = log_every and (ep % log_every == 0 or ep == epochs - 1) and s == steps - 1

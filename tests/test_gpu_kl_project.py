@@ -5,9 +5,9 @@ FP32, so only the FP32 summation order differs: tolerance, relative to the large
 entry of each row, 1e-5 + 5e-7 sqrt(n^2).
 
 Cases: n^2 odd (sample-pair tensor map) and even (row tensor map); N even, odd (a
-last unpaired sample read with plain loads), one sample (plain loads only), a ragged
-last 128-sample tile, a ragged last 64-wide K block, r_m not a multiple of 16, and
-the 129 x 129 width.
+last unpaired sample read with plain loads), one sample (plain loads only), a base
+8 bytes off a 16-byte boundary (plain loads), a ragged last 128-sample tile, a ragged
+last 64-wide K block, r_m not a multiple of 16, and the 129 x 129 width.
 """
 import math
 
@@ -51,16 +51,23 @@ def test_kl_project_parity(N, nn, rm):
     assert np.all(np.abs(got - ref) <= (1e-5 + 5e-7 * math.sqrt(nn)) * scale)
 
 
-def test_kl_project_rejects_unaligned_fields():
+def test_kl_project_offset_base():
+    """Fields starting 8 bytes off a 16-byte boundary (a slice at an odd sample) go by plain loads."""
     from paper_2305_20053_gb300 import capi
-    N, nn, rm = 4, 289, 16
-    buf = torch.zeros(N * nn + 1, device="cuda", dtype=torch.float64)
-    W = torch.zeros(rm, 320, device="cuda", dtype=torch.bfloat16)
-    b = torch.zeros(rm, device="cuda")
-    xi = torch.zeros(N, rm, device="cuda")
-    lib = capi.load()
-    import ctypes
-    rc = lib.ouu_kernel_kl_project(ctypes.c_void_p(buf.data_ptr() + 8), N, nn, ctypes.c_void_p(W.data_ptr()), 320,
-                                   rm, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(xi.data_ptr()),
-                                   ctypes.c_void_p(b.data_ptr()), None)
-    assert rc == 1   # OUU_ERR_INVALID_ARG
+    N, nn, rm = 5, 289, 16
+    rng = np.random.default_rng(77)
+    full = torch.tensor(rng.standard_normal((N + 1, nn)), device="cuda")
+    m_d = full[1:]                       # starts at 289 * 8 bytes: 8 mod 16
+    assert m_d.data_ptr() % 16 == 8
+    W = np.zeros((rm, 320))
+    W[:, :nn] = round_bf16(rng.standard_normal((rm, nn)) / 17.0)
+    W_d = torch.tensor(W, device="cuda").to(torch.bfloat16)
+    b_d = torch.zeros(rm, device="cuda")
+    xi = torch.empty(N, rm, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    capi.ouu_kernel_kl_project(m_d, N, nn, W_d, rm, b_d, xi, err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = round_bf16(m_d.cpu().numpy()) @ W[:, :nn].T
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(xi.cpu().numpy() - ref) <= (1e-5 + 5e-7 * math.sqrt(nn)) * scale)
