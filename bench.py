@@ -379,9 +379,9 @@ def run_ours(args):
                 "phases": {k: {"kernel": v[0], "bound": v[1], "ms": v[3],
                                "achieved": v[2] / (v[3] / 1000.0) / (1e9 if v[1] == "hbm" else 1e12)}
                            for k, v in kern.items()}}
-        # per step: k_kl_project, k_build_x0, 4 forward GEMMs, k_qoi_seed, 4 reverse GEMMs,
-        # k_risk_moments, k_risk_select, k_risk_apply, k_weighted_grads
-        launches = 15 * args.steps
+        # per step: k_kl_project, k_build_x0, 4 forward GEMMs (the last with the reduced-QoI
+        # epilogue), 4 reverse GEMMs, k_risk_moments, k_risk_select, k_risk_apply
+        launches = 13 * args.steps
         e2e = None
         if not args.no_e2e:
             m_host = m.cpu().pin_memory()

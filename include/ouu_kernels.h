@@ -9,6 +9,9 @@
  *   2 DGELU_SCALE: y = acc * gelu'(aux[(r / aux_rdiv) * ld_aux + c]); out2 = bf16(acc)
  *   3 GELU_D     : a = acc + bias[c]; out_f32 = gelu'(a); BF16 outputs = gelu(a)
  *   4 SCALE      : y = acc * aux[(r / aux_rdiv) * ld_aux + c]
+ *   5 QOI        : phi = (acc + bias[c]) s[c] -> out_f32, v = phi + c_add[c], BF16 outputs = v s[c],
+ *                  out_q[r] = qconst + 1/2 sum_c v^2 (the reduced QoI of Sec. 3.3 and its seed);
+ *                  N <= 256; s, c_add, out_q given by ouu_kernel_gemm_qoi_bf16
  * These are the dense layers of the reduced-basis network of Sec. 3.3 (forward
  * values, forward-mode control-Jacobian tangents, and their adjoints).
  * A, B: device BF16 row-major with leading dimensions lda, ldb (multiples of 8,
@@ -30,6 +33,8 @@
  * w_dev[r][i] (device FP64, [n_risks][N]) with grad rho = sum_i w[r][i] grad Q_i, and on the
  * host out_host[3r + 0..2] = rho, d rho / dt, t (t = t* when t_optimal).  Mean + variance:
  * w = (1 + 2 kappa (Q_i - Qbar)) / N; smoothed CVaR: w = s'_eps(Q_i - t) / (N (1 - beta)).
+ * With gq_dev (device FP32 per-sample gradients [N][ldg], dz columns used), also
+ * grad_host[r][j] = sum_i w[r][i] gq[i][j] (FP64 sums), the SAA gradient of the risk.
  * Synchronises `stream`; allocates its own scratch (test entry only). */
 #ifndef OUU_KERNELS_H
 #define OUU_KERNELS_H
@@ -45,8 +50,14 @@ ouu_status ouu_kernel_gemm_bf16(const void* A, int lda, const void* B, int ldb, 
                                 float* out_f32, int ld_f32, int accumulate, void* out_bf16, int ld_bf16,
                                 void* out_t_bf16, int ld_t, void* out2_bf16, int ld2, int* err_dev, void* stream);
 
+ouu_status ouu_kernel_gemm_qoi_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
+                                   const float* bias, const float* col_scale, const float* col_add, double qconst,
+                                   float* out_f32, int ld_f32, void* out_bf16, int ld_bf16, double* out_q, int* err_dev,
+                                   void* stream);
+
 ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const ouu_risk_desc* risks, int n_risks, double* w_dev,
-                                   double* out_host, void* stream);
+                                   double* out_host, const float* gq_dev, int ldg, int dz, double* grad_host,
+                                   void* stream);
 
 ouu_status ouu_kernel_kl_project(const double* m, int N, int nn, const void* W, int ldw, int rm, const float* bias,
                                  float* xi, int* err_dev, void* stream);

@@ -94,7 +94,9 @@ SIGNATURES = {
     "ouu_kernel_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _i, _i, _vp, _i, _i,
                                   _vp, _i, _vp, _i, _vp, _i, _vp, _vp]),
     "ouu_kernel_kl_project": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _vp]),
-    "ouu_kernel_risk_weights": (_i, [_vp, _i, ctypes.POINTER(RiskDesc), _i, _vp, _dp, _vp]),
+    "ouu_kernel_risk_weights": (_i, [_vp, _i, ctypes.POINTER(RiskDesc), _i, _vp, _dp, _vp, _i, _i, _dp, _vp]),
+    "ouu_kernel_gemm_qoi_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _vp, _vp, _vp, ctypes.c_double, _vp, _i, _vp, _i,
+                                      _vp, _vp, _vp]),
     "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "ouu_problem_slots": (_i, [_vp]),
 }
@@ -246,17 +248,39 @@ def ouu_kernel_gemm_bf16(A, B, M, N, K, mode=0, alpha=1.0, bias=None, aux=None, 
                                       _stream_handle(stream)))
 
 
-def ouu_kernel_risk_weights(q, risks, w, stream=None):
-    """Per-sample risk weights and (rho, d rho/dt, t) per risk (kernel-level test entry)."""
+def ouu_kernel_risk_weights(q, risks, w, gq=None, stream=None):
+    """Per-sample risk weights and (rho, d rho/dt, t) per risk; with per-sample gradients gq
+    (FP32 [N][d]) also the risk gradients (kernel-level test entry).  Returns out [n, 3] or
+    (out, grad [n, d])."""
     import numpy as np
     import torch
     stream = stream if stream is not None else torch.cuda.current_stream()
     n = len(risks)
     arr = (RiskDesc * n)(*risks)
     out = np.zeros(3 * n)
+    dz = gq.shape[1] if gq is not None else 0
+    grad = np.zeros(n * max(dz, 1))
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     check(load().ouu_kernel_risk_weights(dev_ptr(q, torch.float64), q.numel(), arr, n, dev_ptr(w, torch.float64),
-                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream)))
-    return out.reshape(n, 3)
+                                         P(out), dev_ptr(gq, torch.float32), dz, dz, P(grad) if gq is not None else None,
+                                         _stream_handle(stream)))
+    if gq is None:
+        return out.reshape(n, 3)
+    return out.reshape(n, 3), grad.reshape(n, dz)
+
+
+def ouu_kernel_gemm_qoi_bf16(A, B, M, N, K, bias, col_scale, col_add, qconst, out_f32, out_bf16, out_q, err,
+                             stream=None):
+    """Output layer with the reduced-QoI epilogue (kernel-level test entry)."""
+    import torch
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    check(load().ouu_kernel_gemm_qoi_bf16(dev_ptr(A, torch.bfloat16), A.stride(0), dev_ptr(B, torch.bfloat16),
+                                          B.stride(0), M, N, K, dev_ptr(bias, torch.float32),
+                                          dev_ptr(col_scale, torch.float32), dev_ptr(col_add, torch.float32), qconst,
+                                          dev_ptr(out_f32, torch.float32), out_f32.stride(0),
+                                          dev_ptr(out_bf16, torch.bfloat16), out_bf16.stride(0),
+                                          dev_ptr(out_q, torch.float64), dev_ptr(err, torch.int32),
+                                          _stream_handle(stream)))
 
 
 def ouu_kernel_kl_project(m, N, nn, W, rm, bias, xi, err=None, stream=None):

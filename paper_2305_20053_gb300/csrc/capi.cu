@@ -410,9 +410,10 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
     auto enqueue = [&]() -> ouu_status {
       if (ouu_status st = dino_eval_core(dino, m_dev, n_samples, z_host, true)) return st;
       if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[1], dino->stream));
-      launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream);
+      // weights, risk values and sum_i w_i grad Q_i in one pass over the samples
+      launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream,
+                          dino->GQe, (dz + 7) / 8 * 8, dz, d_grad);
       if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[2], dino->stream));
-      dino_weighted_grads(dino, p->d_w, n_samples, n_risks, d_grad);
       OUU_CUDA_TRY(cudaGetLastError());
       OUU_CUDA_TRY(cudaMemcpyAsync(p->h_out, p->d_out, ob, cudaMemcpyDeviceToHost, dino->stream));
       OUU_CUDA_TRY(cudaMemcpyAsync(p->h_stat, dino->d_err, 4, cudaMemcpyDeviceToHost, dino->stream));

@@ -37,15 +37,26 @@ static int grid_for(int64_t total, int threads = 256) {
 __global__ void k_build_x0(const float* __restrict__ xi, const int* __restrict__ idx, const float* __restrict__ z,
                            int64_t z_stride, int rm, int dz, int in0p, int B, __nv_bfloat16* __restrict__ x0,
                            __nv_bfloat16* __restrict__ x0t) {
-  GRID_STRIDE(e, (int64_t)B * in0p) {
-    const int b = (int)(e / in0p), k = (int)(e % in0p);
+  // four consecutive columns per thread (in0p is a multiple of 8): one 8-byte store
+  const int q4 = in0p >> 2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * q4; e += gridDim.x * blockDim.x) {
+    const int b = e / q4, k0 = 4 * (e - b * q4);
     const int64_t src = idx ? idx[b] : b;
-    float v = 0.f;
-    if (k < rm) v = xi[src * rm + k];
-    else if (k < rm + dz) v = z[src * z_stride + (k - rm)];
-    const __nv_bfloat16 bv = __float2bfloat16(v);
-    x0[e] = bv;
-    if (x0t) x0t[(int64_t)k * B + b] = bv;
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + j;
+      v[j] = k < rm ? xi[src * rm + k] : (k < rm + dz ? z[src * z_stride + (k - rm)] : 0.f);
+    }
+    const __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+    *reinterpret_cast<uint2*>(x0 + (int64_t)b * in0p + k0) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+    if (x0t) {
+      x0t[(int64_t)(k0 + 0) * B + b] = p0.x;
+      x0t[(int64_t)(k0 + 1) * B + b] = p0.y;
+      x0t[(int64_t)(k0 + 2) * B + b] = p1.x;
+      x0t[(int64_t)(k0 + 3) * B + b] = p1.y;
+    }
   }
 }
 
@@ -196,34 +207,6 @@ __global__ void k_weight_bf16(const float* __restrict__ W, int out, int in, int 
   }
 }
 
-// Reduced QoI (Sec. 3.3): Q_i = 1/2 ||phi_i + c||^2 + const and the reverse-mode seed phi_i + c.
-__global__ void k_qoi_seed(const float* __restrict__ phi, int ldp, const double* __restrict__ c, double qconst, int N,
-                           int ru, const float* __restrict__ oscale, double* __restrict__ Q,
-                           __nv_bfloat16* __restrict__ seed, int lds) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= N) return;
-  double s = 0.0;
-  for (int r = lane; r < ru; r += 32) {
-    const double v = (double)phi[(int64_t)warp * ldp + r] + c[r];
-    s += v * v;
-    if (seed) seed[(int64_t)warp * lds + r] = __float2bfloat16((float)v * oscale[r]);
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) Q[warp] = 0.5 * s + qconst;
-}
-
-// out[r][j] = sum_i w[r][i] gq[i][j]
-__global__ void k_weighted_grads(const double* __restrict__ w, const float* __restrict__ gq, int ldg, int N, int dz,
-                                 double* __restrict__ out) {
-  __shared__ double red[40];
-  const int r = blockIdx.y, j = blockIdx.x;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) s += w[(int64_t)r * N + i] * (double)gq[(int64_t)i * ldg + j];
-  CtaCtx c{red};
-  const double t = c.sum_d(s);
-  if (threadIdx.x == 0) out[r * dz + j] = t;
-}
-
 __global__ void k_f32_to_f64(const float* __restrict__ in, int ld_in, int rows, int cols, double* __restrict__ out) {
   GRID_STRIDE(e, (int64_t)rows * cols) {
     const int64_t r = e / cols;
@@ -334,7 +317,7 @@ extern "C" void ouu_default_dino_desc(ouu_dino_desc* d) {
 static void free_dino(ouu_dino* d) {
   if (!d) return;
   void* ptrs[] = {d->d_params, d->d_grad, d->d_adam_m, d->d_adam_v, d->d_phi, d->d_phi64, d->d_ubar, d->d_ut,
-                  d->d_c, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
+                  d->d_c, d->d_cf, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
                   d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
                   d->Ge, d->GQe, d->Qe, d->d_zf, d->d_err, d->d_gov, d->d_oscale, d->d_klbias};
   for (void* p : ptrs) cudaFree(p);
@@ -429,6 +412,7 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   al((void**)&d->d_ubar, (size_t)d->nn * 8);
   al((void**)&d->d_ut, (size_t)d->nn * 8);
   al((void**)&d->d_c, (size_t)d->ru * 8 + 16);
+  al((void**)&d->d_cf, (size_t)d->ru * 4 + 16);
   al((void**)&d->d_oscale, (size_t)d->ru * 4);
   al((void**)&d->d_wkl, (size_t)d->rm * d->nnp * 2);
   al((void**)&d->d_kl_order, (size_t)d->rm * 4);
@@ -560,8 +544,13 @@ ouu_status dino_install_bases(ouu_dino* d) {
   OUU_CUDA_TRY(cudaMemcpyAsync(c.data(), d->d_c, (d->ru + 1) * 8, cudaMemcpyDeviceToHost, d->stream));
   OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
   double cc = 0.0;
-  for (int r = 0; r < d->ru; ++r) cc += c[r] * c[r];
+  std::vector<float> cf(d->ru);
+  for (int r = 0; r < d->ru; ++r) {
+    cc += c[r] * c[r];
+    cf[r] = (float)c[r];
+  }
   d->qconst = 0.5 * (c[d->ru] - cc);
+  OUU_CUDA_TRY(cudaMemcpy(d->d_cf, cf.data(), (size_t)d->ru * 4, cudaMemcpyHostToDevice));
   d->bases_ready = 1;
   return OUU_OK;
 }
@@ -632,7 +621,7 @@ static ouu_status forward_tangent(ouu_dino* d, const float* xi, const float* z, 
                                   int B, float* jout, int ld_jout, bool transposed) {
   const int wd = d->wd, wdp = d->wd, rup = pad8(d->ru), in0p = d->inp_l[0], dz = d->dz;
   const int R = B * dz, BR = B + R;
-  k_build_x0<<<grid_for((int64_t)B * in0p), 256, 0, d->stream>>>(xi, idx, z, z_stride, d->rm, dz, in0p, B, d->X0,
+  k_build_x0<<<grid_for((int64_t)B * (in0p / 4)), 256, 0, d->stream>>>(xi, idx, z, z_stride, d->rm, dz, in0p, B, d->X0,
                                                                   transposed ? d->X0T : nullptr);
   {  // layer 0 values
     EpiParams ep = epi(EPI_GELU);
@@ -796,7 +785,7 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
   for (int j = 0; j < dz; ++j) zh[j] = (float)z_host[j];
   OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)dz * 4, cudaMemcpyHostToDevice, d->stream));
   DINO_TRY(project_fields(d, m_dev, N, d->XIe, true));
-  k_build_x0<<<grid_for((int64_t)N * in0p), 256, 0, d->stream>>>(d->XIe, nullptr, d->d_zf, 0, d->rm, dz, in0p, N,
+  k_build_x0<<<grid_for((int64_t)N * (in0p / 4)), 256, 0, d->stream>>>(d->XIe, nullptr, d->d_zf, 0, d->rm, dz, in0p, N,
                                                                   d->X0e, nullptr);
   __nv_bfloat16* hin = d->X0e;
   int ldin = in0p, kin = d->in0;
@@ -813,16 +802,19 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
     ldin = wdp;
     kin = wd;
   }
-  {
-    EpiParams e = epi(EPI_LINEAR);
+  {  // output layer with the reduced QoI (Sec. 3.3): phi, Q = 1/2 ||phi + c||^2 + const, seed s (phi + c)
+    EpiParams e = epi(EPI_QOI);
     e.bias = d->d_params + d->offb[3];
     e.col_scale = d->d_oscale;
+    e.col_add = d->d_cf;
+    e.qconst = d->qconst;
     e.out_f32 = d->OUTe;
     e.ld_f32 = rup;
+    e.out_bf16 = want_grad ? d->Ge : nullptr;
+    e.ld_bf16 = rup;
+    e.out_q = d->Qe;
     DINO_TRY(gemm(d, hin, wdp, d->Wb[3], wdp, N, d->ru, wd, e));
   }
-  k_qoi_seed<<<(N * 32 + 255) / 256, 256, 0, d->stream>>>(d->OUTe, rup, d->d_c, d->qconst, N, d->ru, d->d_oscale, d->Qe,
-                                                           want_grad ? d->Ge : nullptr, rup);
   if (want_grad) {
     const __nv_bfloat16* gin = d->Ge;
     int ldg = rup, kg = d->ru;
@@ -872,11 +864,6 @@ extern "C" ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_sam
   }
   OUU_CUDA_TRY(cudaGetLastError());
   return check_err(d);
-}
-
-void dino_weighted_grads(ouu_dino* d, const double* w, int N, int n_w, double* out) {
-  dim3 g(d->dz, n_w);
-  k_weighted_grads<<<g, 256, 0, d->stream>>>(w, d->GQe, pad8(d->dz), N, d->dz, out);
 }
 
 extern "C" ouu_status ouu_dino_set_output_scale(ouu_dino_t d, const float* s_host) {

@@ -27,6 +27,7 @@ struct ouu_dino {
   double* d_ubar = nullptr;        // [nn]
   double* d_ut = nullptr;          // [nn] target state
   double* d_c = nullptr;           // [ru]  c = h^2 Phi^T (ubar - ut)
+  float* d_cf = nullptr;           // [ru]  c in FP32 (the output layer's QoI epilogue)
   float* d_oscale = nullptr;       // [ru]  fixed output scale: phi = s * (W3 h3 + b3)
   double qconst = 0.0;
   __nv_bfloat16* d_wkl = nullptr;  // [rm][nnp] KL projection rows
@@ -75,7 +76,6 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
 // Completes a basis whose FP64 Phi and ubar are in place (FP32 copy, reduced-QoI terms).
 ouu_status dino_install_bases(ouu_dino* d);
 // Sum_i w[r][i] grad_z Q_i of the last evaluation into out [n_w][d_Z] (device).
-void dino_weighted_grads(ouu_dino* d, const double* w, int N, int n_w, double* out);
 // Jacobian-data solves (pde.cu): jy[i][j][r] = h^2 Phi_r . J(u_i)^-1 g_j.
 // Fused KL projection of FP64 fields (kl_project.cu): xi[N][rm] = bf16(m) W^T + bias with
 // W = [rm][ldw] BF16 (K = nn contiguous); xi is zeroed here.  m 8-byte aligned, rm <= 240.

@@ -145,10 +145,12 @@ inline void risk_dev_finish(RiskDev& r, int N) {
 
 // Per-risk weights w[r][i], value[r], dt[r], t[r] from q[N] (moments on many CTAs, t*
 // selection on one, weights on many).  out layout: value[r], dt[r], t[r] at out[3r+0..2].
+// With per-sample gradients gq [N][ldg] (FP32), also grad_out[r][j] = sum_i w[r][i] gq[i][j].
 // scratch: OUU_RISK_SCRATCH doubles of device memory.
 #define OUU_RISK_SCRATCH 2048
-void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w,
-                         double* out, double* scratch, cudaStream_t s);
+void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
+                         double* scratch, cudaStream_t s, const float* gq = nullptr, int ldg = 0, int dz = 0,
+                         double* grad_out = nullptr);
 
 // ------------------------------------------------------------------ fields
 void launch_sample_fields(int n, uint64_t seed, int64_t first, int count, const double* invlam,

@@ -283,7 +283,8 @@ static __device__ double kth_largest_prefix(const double* q, int N, int k, const
 // GB300's narrow FP64 pipe for a whole warp, so the FP64 work stays on one warp and the
 // block-wide parts are integer.  params[r] = {t, mean, var}.
 __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restrict__ q, int N, const double* __restrict__ part, int nparts,
-                              const RiskDev* __restrict__ risks, int n_risks, double* __restrict__ params) {
+                              const RiskDev* __restrict__ risks, int n_risks, double* __restrict__ params,
+                              double* __restrict__ zero_out, int n_zero) {
   __shared__ unsigned hist[2048];
   __shared__ unsigned sel[2 + 64];
   __shared__ double cand[32];
@@ -295,6 +296,8 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
   __shared__ bool s_ok;
   __shared__ double red[40];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (zero_out)   // the weighted-gradient sums of the next pass start from 0
+    for (int i = threadIdx.x; i < n_zero; i += blockDim.x) zero_out[i] = 0.0;
   // key prefixes first: their loads are in flight while warp 0 combines the moments
   bool need_select = false;
   for (int r = 0; r < n_risks; ++r) need_select |= risks[r].kind == OUU_RISK_CVAR_SMOOTH && risks[r].t_optimal;
@@ -465,39 +468,89 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
   }
 }
 
-// Pass 3 (many CTAs): weights w[r][i] and per-block partial sums of s_eps and s'_eps; the
-// last block to finish (an arrival counter, reset for the next call) combines the partial
-// sums into the risk values and d rho / dt.  out[3r..3r+2] = value, dt, t.
-__global__ void k_risk_apply(const double* __restrict__ q, int N, const RiskDev* __restrict__ risks, int n_risks,
-                             const double* __restrict__ params, double* __restrict__ w, double* __restrict__ part,
-                             unsigned* __restrict__ arrivals, double* __restrict__ out) {
+// Pass 3 (many CTAs, each a contiguous range of samples): weights w[r][i] and per-block
+// partial sums of s_eps and s'_eps; with per-sample gradients gq [N][ldg] (FP32), also
+// grad_out[r][j] += sum_i w[r][i] gq[i][j] (per-block FP64 sums added atomically; the
+// select pass zeroed grad_out).  The last block to finish (an arrival counter, reset for the
+// next call) combines the partial sums into the risk values and d rho / dt.
+// out[3r..3r+2] = value, dt, t.
+#define APPLY_SUB 128
+__global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q, int N,
+                                                    const RiskDev* __restrict__ risks, int n_risks,
+                                                    const double* __restrict__ params, double* __restrict__ w,
+                                                    double* __restrict__ part, unsigned* __restrict__ arrivals,
+                                                    double* __restrict__ out, const float* __restrict__ gq, int ldg,
+                                                    int dz, double* __restrict__ grad_out) {
   __shared__ double red[40];
   __shared__ bool last;
+  __shared__ double ws[OUU_MAX_RISKS][APPLY_SUB];
+  __shared__ double gsum[OUU_MAX_RISKS][128];
   BlockRed br{red};
-  for (int r = 0; r < n_risks; ++r) {
-    const RiskDev R = risks[r];
-    const double t = params[3 * r], qbar = params[3 * r + 1];
-    double* wr = w + (int64_t)r * N;
-    double sv = 0.0, sd = 0.0;
-    if (R.kind == OUU_RISK_MEAN_VAR) {
-      const double invN = R.inv_N, k2 = 2.0 * R.kappa;
-      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        wr[i] = (1.0 + k2 * (q[i] - qbar)) * invN;
-    } else {
-      const double scale = R.inv_K, ie = R.inv_eps;
-      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const double x = q[i] - t;
-        const double d1 = splus_d1(x, R.eps, ie);
-        wr[i] = d1 * scale;
-        sv += splus(x, R.eps, ie);
-        sd += d1;
+  const int chunk = (N + gridDim.x - 1) / gridDim.x;
+  const int i0 = min(N, (int)blockIdx.x * chunk), i1 = min(N, i0 + chunk);
+  double sv[OUU_MAX_RISKS], sd[OUU_MAX_RISKS];
+#pragma unroll
+  for (int r = 0; r < OUU_MAX_RISKS; ++r) sv[r] = sd[r] = 0.0;
+  for (int s0 = i0; s0 < i1; s0 += APPLY_SUB) {
+    const int s1 = min(i1, s0 + APPLY_SUB);
+    for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+      const double qi = q[i];
+#pragma unroll
+      for (int r = 0; r < OUU_MAX_RISKS; ++r) {
+        if (r >= n_risks) break;
+        const RiskDev& R = risks[r];
+        const double t = params[3 * r], qbar = params[3 * r + 1];
+        double wi;
+        if (R.kind == OUU_RISK_MEAN_VAR) {
+          wi = (1.0 + 2.0 * R.kappa * (qi - qbar)) * R.inv_N;
+        } else {
+          const double x = qi - t;
+          const double d1 = splus_d1(x, R.eps, R.inv_eps);
+          wi = d1 * R.inv_K;
+          sv[r] += splus(x, R.eps, R.inv_eps);
+          sd[r] += d1;
+        }
+        w[(int64_t)r * N + i] = wi;
+        ws[r][i - s0] = wi;
       }
-      const double tv = br.sum(sv);
-      const double td = br.sum(sd);
-      if (threadIdx.x == 0) {
-        part[(2 * r) * gridDim.x + blockIdx.x] = tv;
-        part[(2 * r + 1) * gridDim.x + blockIdx.x] = td;
+    }
+    if (gq) {
+      __syncthreads();
+      const int g = threadIdx.x >> 7, jl = threadIdx.x & 127;   // two sample halves x 128 columns
+      for (int jb = 0; jb < dz; jb += 128) {
+        const int j = jb + jl;
+        double acc[OUU_MAX_RISKS];
+#pragma unroll
+        for (int r = 0; r < OUU_MAX_RISKS; ++r) acc[r] = 0.0;
+        if (j < dz && g < 2)
+          for (int i = s0 + g; i < s1; i += 2) {
+            const double gv = (double)gq[(int64_t)i * ldg + j];
+#pragma unroll
+            for (int r = 0; r < OUU_MAX_RISKS; ++r)
+              if (r < n_risks) acc[r] += ws[r][i - s0] * gv;
+          }
+        if (g == 1)
+#pragma unroll
+          for (int r = 0; r < OUU_MAX_RISKS; ++r) gsum[r][jl] = acc[r];
+        __syncthreads();
+        if (g == 0 && j < dz)
+#pragma unroll
+          for (int r = 0; r < OUU_MAX_RISKS; ++r)
+            if (r < n_risks) atomicAdd(&grad_out[r * dz + j], acc[r] + gsum[r][jl]);
+        __syncthreads();
       }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < OUU_MAX_RISKS; ++r) {
+    if (r >= n_risks) break;
+    if (risks[r].kind == OUU_RISK_MEAN_VAR) continue;
+    const double tv = br.sum(sv[r]);
+    const double td = br.sum(sd[r]);
+    if (threadIdx.x == 0) {
+      part[(2 * r) * gridDim.x + blockIdx.x] = tv;
+      part[(2 * r + 1) * gridDim.x + blockIdx.x] = td;
     }
   }
   __threadfence();
@@ -519,20 +572,19 @@ __global__ void k_risk_apply(const double* __restrict__ q, int N, const RiskDev*
         }
         continue;
       }
-      double sv = 0.0, sd = 0.0;
+      double a = 0.0, b = 0.0;
       for (int i = lane; i < (int)gridDim.x; i += 32) {
-        sv += __ldcg(&part[(2 * r) * gridDim.x + i]);
-        sd += __ldcg(&part[(2 * r + 1) * gridDim.x + i]);
+        a += __ldcg(&part[(2 * r) * gridDim.x + i]);
+        b += __ldcg(&part[(2 * r + 1) * gridDim.x + i]);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        sv += __shfl_xor_sync(0xffffffffu, sv, o);
-        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
       }
       if (lane == 0) {
-        const double scale = R.inv_K;
-        out[3 * r + 0] = t + sv * scale;
-        out[3 * r + 1] = 1.0 - sd * scale;
+        out[3 * r + 0] = t + a * R.inv_K;
+        out[3 * r + 1] = 1.0 - b * R.inv_K;
         out[3 * r + 2] = t;
       }
     }
@@ -541,20 +593,24 @@ __global__ void k_risk_apply(const double* __restrict__ q, int N, const RiskDev*
 }
 
 void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
-                         double* scratch, cudaStream_t s) {
+                         double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out) {
   static_assert(OUU_RISK_SCRATCH >= 3 * OUU_MAX_RISKS + 2 * OUU_MAX_RISKS * RISK_BLOCKS + 1, "risk scratch size");
   double* params = scratch;
   double* part = scratch + 3 * OUU_MAX_RISKS;
   k_risk_moments<<<RISK_BLOCKS, 256, 0, s>>>(q, N, part);
-  k_risk_select<<<1, 1024, 0, s>>>(q, N, part, RISK_BLOCKS, risks_dev, n_risks, params);
+  k_risk_select<<<1, 1024, 0, s>>>(q, N, part, RISK_BLOCKS, risks_dev, n_risks, params, gq ? grad_out : nullptr,
+                                   n_risks * dz);
   unsigned* arrivals = (unsigned*)(scratch + OUU_RISK_SCRATCH - 1);   // zeroed at problem creation
-  k_risk_apply<<<RISK_BLOCKS, 256, 0, s>>>(q, N, risks_dev, n_risks, params, w, part, arrivals, out);
+  k_risk_apply<<<RISK_BLOCKS, 256, 0, s>>>(q, N, risks_dev, n_risks, params, w, part, arrivals, out, gq, ldg, dz,
+                                           grad_out);
 }
 
 // Kernel-level entry used by the risk-weight numerics test (declared in include/ouu_kernels.h).
 extern "C" ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const ouu_risk_desc* risks, int n_risks,
-                                              double* w_dev, double* out_host, void* stream) {
+                                              double* w_dev, double* out_host, const float* gq_dev, int ldg, int dz,
+                                              double* grad_host, void* stream) {
   OUU_CHECK_ARG(q_dev && risks && w_dev && out_host, "null argument");
+  OUU_CHECK_ARG(!gq_dev || (grad_host && dz >= 1 && ldg >= dz), "gradients: grad_host, dz >= 1, ldg >= dz");
   OUU_CHECK_ARG(N >= 1 && n_risks >= 1 && n_risks <= OUU_MAX_RISKS, "N >= 1 and 1 <= n_risks <= 4");
   for (int r = 0; r < n_risks; ++r)
     OUU_CHECK_ARG(risks[r].kind == OUU_RISK_MEAN_VAR ||
@@ -574,9 +630,11 @@ extern "C" ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const 
   RiskDev* d_r = nullptr;
   double* scr = nullptr;
   double* d_out = nullptr;
+  double* d_grad = nullptr;
   ouu_status st = OUU_OK;
+  const size_t gbytes = gq_dev ? (size_t)n_risks * dz * 8 : 8;
   if (cudaMalloc((void**)&d_r, sizeof(rd)) != cudaSuccess || cudaMalloc((void**)&scr, OUU_RISK_SCRATCH * 8) != cudaSuccess ||
-      cudaMalloc((void**)&d_out, 3 * OUU_MAX_RISKS * 8) != cudaSuccess) {
+      cudaMalloc((void**)&d_out, 3 * OUU_MAX_RISKS * 8) != cudaSuccess || cudaMalloc((void**)&d_grad, gbytes) != cudaSuccess) {
     ouu_set_error("cudaMalloc failed");
     st = OUU_ERR_OOM;
   } else if (cudaMemcpy(d_r, rd, sizeof(RiskDev) * n_risks, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -584,9 +642,10 @@ extern "C" ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const 
     ouu_set_error("risk set-up copy failed");
     st = OUU_ERR_CUDA;
   } else {
-    launch_risk_weights(q_dev, N, d_r, n_risks, w_dev, d_out, scr, s);
+    launch_risk_weights(q_dev, N, d_r, n_risks, w_dev, d_out, scr, s, gq_dev, ldg, dz, gq_dev ? d_grad : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, d_out, (size_t)3 * n_risks * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && gq_dev) e = cudaMemcpyAsync(grad_host, d_grad, gbytes, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
       ouu_set_error(std::string("risk weights: ") + cudaGetErrorString(e));
@@ -596,5 +655,6 @@ extern "C" ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const 
   cudaFree(d_r);
   cudaFree(scr);
   cudaFree(d_out);
+  cudaFree(d_grad);
   return st;
 }

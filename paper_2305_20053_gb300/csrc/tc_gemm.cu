@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "tc_gemm.cuh"
 #include "tc_ptx.cuh"
@@ -36,11 +37,55 @@ struct GemmStages {
 // and 8-byte BF16 global stores when ep.vec).  One compact loop per mode keeps the code
 // that every CTA runs once small.  MODE 7 = split-K partial sums, added atomically.
 template <int BN, int MODE>
-static __device__ __forceinline__ void epi_quads(float* stage, const float* sbias, const float* sscale, int m0,
-                                                 int n0, int M, int N, const EpiParams& ep, bool keep) {
+static __device__ __forceinline__ void epi_quads(float* stage, const float* sbias, const float* sscale,
+                                                 const float* sadd, float* rowsum, int m0, int n0, int M, int N,
+                                                 const EpiParams& ep, bool keep) {
   constexpr int SROW = BN + 4, QPR = BN / 4;
   const bool vec = ep.vec != 0;
   const float alpha = ep.alpha;
+  if (MODE == EPI_QOI) {
+    // whole rows per warp, lanes over quads, the row's quadratic by a warp reduction
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int tr = warp; tr < GEMM_BM; tr += GEMM_THREADS / 32) {
+      const int r = m0 + tr;
+      if (r >= M) break;
+      float sq = 0.f;
+      for (int qd = lane; qd < QPR; qd += 32) {
+        const int cc = 4 * qd, c = n0 + cc;
+        if (c >= N) break;
+        const int nv = min(4, N - c);
+        const float4 a4 = *reinterpret_cast<const float4*>(stage + tr * SROW + cc);
+        const float acc[4] = {a4.x, a4.y, a4.z, a4.w};
+        float y[4], o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          y[j] = (acc[j] + sbias[cc + j]) * sscale[cc + j];
+          const float v = j < nv ? y[j] + sadd[cc + j] : 0.f;
+          o[j] = v * sscale[cc + j];
+          sq += v * v;
+        }
+        float* of = ep.out_f32 ? ep.out_f32 + (size_t)r * ep.ld_f32 + c : nullptr;
+        __nv_bfloat16* ob = ep.out_bf16 ? ep.out_bf16 + (size_t)r * ep.ld_bf16 + c : nullptr;
+        if (vec && nv == 4) {
+          if (of) *reinterpret_cast<float4*>(of) = make_float4(y[0], y[1], y[2], y[3]);
+          if (ob) {
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(o[0], o[1]), p1 = __floats2bfloat162_rn(o[2], o[3]);
+            *reinterpret_cast<uint2*>(ob) =
+                make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+          }
+        } else {
+          for (int j = 0; j < nv; ++j) {
+            if (of) of[j] = y[j];
+            if (ob) ob[j] = __float2bfloat16(o[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) rowsum[tr] = sq;
+    }
+    return;
+  }
 #pragma unroll 2
   for (int e = threadIdx.x; e < GEMM_BM * QPR; e += GEMM_THREADS) {
     const int tr = e / QPR, cc = (e - tr * QPR) * 4, r = m0 + tr, c = n0 + cc;
@@ -145,7 +190,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint64_t* tfull = empty + GEMM_STAGES;
   uint32_t* tslot = (uint32_t*)(tfull + 1);
   __shared__ volatile int s_fail;
-  __shared__ __align__(16) float s_bias[BN], s_scale[BN];
+  __shared__ __align__(16) float s_bias[BN], s_scale[BN], s_add[BN];
+  __shared__ float s_rowsum[GEMM_BM];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * GEMM_BM, n0 = blockIdx.x * BN;
@@ -171,7 +217,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int c = n0 + i;
     s_bias[i] = (c < N && ep.bias && blockIdx.z == 0) ? ep.bias[c] : 0.f;
     s_scale[i] = (c < N && ep.col_scale) ? ep.col_scale[c] : 1.f;
+    s_add[i] = (c < N && ep.col_add) ? ep.col_add[c] : 0.f;
   }
+  for (int i = threadIdx.x; i < GEMM_BM; i += GEMM_THREADS) s_rowsum[i] = 0.f;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -252,17 +300,24 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const bool keep = ep.out_t_bf16 != nullptr && !splitk;
     if (run) {
       if (splitk)
-        epi_quads<BN, 7>(stage, s_bias, s_scale, m0, n0, M, N, ep, false);
+        epi_quads<BN, 7>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, false);
       else if (ep.mode == EPI_LINEAR)
-        epi_quads<BN, EPI_LINEAR>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
+        epi_quads<BN, EPI_LINEAR>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
       else if (ep.mode == EPI_GELU)
-        epi_quads<BN, EPI_GELU>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
+        epi_quads<BN, EPI_GELU>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
       else if (ep.mode == EPI_GELU_D)
-        epi_quads<BN, EPI_GELU_D>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
+        epi_quads<BN, EPI_GELU_D>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
       else if (ep.mode == EPI_SCALE)
-        epi_quads<BN, EPI_SCALE>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
+        epi_quads<BN, EPI_SCALE>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
+      else if (ep.mode == EPI_QOI)
+        epi_quads<BN, EPI_QOI>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
       else
-        epi_quads<BN, EPI_DGELU_SCALE>(stage, s_bias, s_scale, m0, n0, M, N, ep, keep);
+        epi_quads<BN, EPI_DGELU_SCALE>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
+    }
+    if (ep.mode == EPI_QOI && run) {   // the tile holds whole rows: finish the per-row quadratic
+      __syncthreads();
+      for (int tr = threadIdx.x; tr < GEMM_BM; tr += GEMM_THREADS)
+        if (m0 + tr < M) ep.out_q[m0 + tr] = ep.qconst + 0.5 * (double)s_rowsum[tr];
     }
     if (ep.out_t_bf16 && !splitk) {
       // Epilogue C (all warps): transposed output, consecutive threads on consecutive rows.
@@ -353,7 +408,10 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   OUU_CHECK_ARG(M >= 1 && N >= 1 && K >= 1, "GEMM sizes must be positive");
   OUU_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0, "GEMM operands must be 16-byte aligned");
   OUU_CHECK_ARG(lda % 8 == 0 && ldb % 8 == 0 && lda >= K && ldb >= K, "GEMM leading dimensions: multiple of 8, >= K");
-  OUU_CHECK_ARG(ep.mode >= EPI_LINEAR && ep.mode <= EPI_SCALE, "unknown epilogue mode");
+  OUU_CHECK_ARG(ep.mode >= EPI_LINEAR && ep.mode <= EPI_QOI, "unknown epilogue mode");
+  OUU_CHECK_ARG(ep.mode != EPI_QOI || (N <= 256 && ep.out_q && ep.col_scale && ep.col_add && splits == 1 &&
+                                       !ep.accumulate && !ep.out_t_bf16),
+                "EPI_QOI needs N <= 256, out_q, col_scale and col_add, and no split-K");
   OUU_CHECK_ARG((ep.mode != EPI_DGELU_SCALE && ep.mode != EPI_SCALE) || (ep.aux && ep.aux_rdiv >= 1),
                 "EPI_DGELU_SCALE and EPI_SCALE need aux");
   OUU_CHECK_ARG(splits >= 1 && splits <= 64, "split-K factor in [1, 64]");
@@ -386,6 +444,7 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   long best_cost = 1L << 60;
   const long mt = (long)((M + GEMM_BM - 1) / GEMM_BM) * splits;
   for (int bn : cands) {
+    if (ep.mode == EPI_QOI && bn < N) continue;   // whole rows in one tile
     const long tiles = mt * ((N + bn - 1) / bn);
     const long cost = ((tiles + sms - 1) / sms) * (bn + 64);
     if (cost < best_cost) {
@@ -410,6 +469,7 @@ extern "C" ouu_status ouu_kernel_gemm_bf16(const void* A, int lda, const void* B
                                            int ld_bf16, void* out_t_bf16, int ld_t, void* out2_bf16, int ld2,
                                            int* err_dev, void* stream) {
   EpiParams ep;
+  std::memset(&ep, 0, sizeof(ep));
   ep.mode = mode;
   ep.alpha = alpha;
   ep.bias = bias;
@@ -426,6 +486,30 @@ extern "C" ouu_status ouu_kernel_gemm_bf16(const void* A, int lda, const void* B
   ep.aux = aux;
   ep.ld_aux = ld_aux;
   ep.aux_rdiv = aux_rdiv;
+  OUU_CHECK_ARG(err_dev != nullptr, "err_dev is required");
+  return ouu_gemm_bf16((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)B, ldb, M, N, K, ep, err_dev,
+                       (cudaStream_t)stream, 1);
+}
+
+// Kernel-level entry of the reduced-QoI epilogue (declared in include/ouu_kernels.h).
+extern "C" ouu_status ouu_kernel_gemm_qoi_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
+                                               const float* bias, const float* col_scale, const float* col_add,
+                                               double qconst, float* out_f32, int ld_f32, void* out_bf16, int ld_bf16,
+                                               double* out_q, int* err_dev, void* stream) {
+  EpiParams ep;
+  std::memset(&ep, 0, sizeof(ep));
+  ep.mode = EPI_QOI;
+  ep.alpha = 1.f;
+  ep.bias = bias;
+  ep.col_scale = col_scale;
+  ep.col_add = col_add;
+  ep.qconst = qconst;
+  ep.out_f32 = out_f32;
+  ep.ld_f32 = ld_f32;
+  ep.out_bf16 = (__nv_bfloat16*)out_bf16;
+  ep.ld_bf16 = ld_bf16;
+  ep.out_q = out_q;
+  ep.aux_rdiv = 1;
   OUU_CHECK_ARG(err_dev != nullptr, "err_dev is required");
   return ouu_gemm_bf16((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)B, ldb, M, N, K, ep, err_dev,
                        (cudaStream_t)stream, 1);

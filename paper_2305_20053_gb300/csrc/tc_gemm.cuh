@@ -14,6 +14,9 @@ enum EpiMode {
   EPI_DGELU_SCALE = 2,  // y = acc * gelu'(aux[(r / aux_rdiv) * ld_aux + c]); out2 = bf16(acc)
   EPI_GELU_D = 3,       // a = acc + bias[c]; out_f32 = gelu'(a); bf16 outputs = gelu(a)
   EPI_SCALE = 4,        // y = acc * aux[(r / aux_rdiv) * ld_aux + c]
+  EPI_QOI = 5,          // phi = (acc + bias[c]) * col_scale[c] -> out_f32; v = phi + col_add[c];
+                        // bf16 outputs = v * col_scale[c]; out_q[r] = qconst + 1/2 sum_c v^2
+                        // (one N tile: N <= 256)
 };
 
 struct EpiParams {
@@ -34,6 +37,9 @@ struct EpiParams {
   int ld_aux;
   int aux_rdiv;
   int vec;                        // set by ouu_gemm_bf16: vector epilogue accesses are aligned
+  const float* col_add;           // EPI_QOI: per-column shift c
+  double* out_q;                  // EPI_QOI: [M] per-row quadratic
+  double qconst;                  // EPI_QOI: added to every out_q
 };
 
 // Tensor map of a row-major BF16 matrix [rows][ld] (K = inner, contiguous), box 64 x box_rows.

@@ -242,7 +242,10 @@ def test_dino_risk_path(setup):
 
 
 def test_graph_replay_matches_eager(setup):
-    """The captured graph of the DINO risk evaluation gives the eager results, also after z changes."""
+    """The captured graph of the DINO risk evaluation gives the eager results, also after z changes.
+    The per-block partial sums of the weighted gradient are added atomically in FP64, whose
+    order varies from run to run: gradients agree to 1e-12 relative, risk values exactly
+    (their partial sums are combined in a fixed order)."""
     from paper_2305_20053_gb300 import capi
     D, P, n, N = setup["D"], setup["P"], N_GRID, 40
     m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
@@ -256,4 +259,4 @@ def test_graph_replay_matches_eager(setup):
     graphed = [P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)[:2] for z in zs]   # capture, replay, replay
     for (v0, g0), (v1, g1) in zip(eager, graphed):
         np.testing.assert_array_equal(v0, v1)
-        np.testing.assert_array_equal(g0, g1)
+        np.testing.assert_allclose(g1, g0, rtol=1e-12, atol=1e-15 * np.abs(g0).max())

@@ -151,3 +151,30 @@ def test_scale_epilogue():
     ref = _ref(A, W, K) * aux.repeat_interleave(rd, dim=0)
     _close(out, ref, 2 * _tol(K))
     _close(hb.float(), ref, 2 ** -8 + 2 * _tol(K))
+
+
+def test_reduced_qoi_epilogue():
+    """Mode 5 (output layer of the evaluation, Sec. 3.3 reduced QoI): phi = (acc + b) s,
+    Q = qconst + 1/2 sum (phi + c)^2 per row (FP32 row sums), BF16 seed (phi + c) s."""
+    from paper_2305_20053_gb300 import capi
+    M, N, K = 300, 200, 400
+    A = _bf((M, K), seed=21)
+    B = _bf((N, K), seed=22, scale=1.0 / 20)
+    g = torch.Generator(device="cuda").manual_seed(23)
+    bias = 0.1 * torch.randn(N, device="cuda", generator=g)
+    s = 0.5 + torch.rand(N, device="cuda", generator=g)
+    c = 0.2 * torch.randn(N, device="cuda", generator=g)
+    phi = torch.empty(M, N, device="cuda")
+    seed = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+    q = torch.empty(M, device="cuda", dtype=torch.float64)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    capi.ouu_kernel_gemm_qoi_bf16(A, B, M, N, K, bias, s, c, 0.75, phi, seed, q, err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref_phi = ((A[:, :K].double() @ B[:, :K].double().T) + bias.double()) * s.double()
+    v = ref_phi + c.double()
+    ref_q = 0.75 + 0.5 * (v * v).sum(dim=1)
+    _close(phi, ref_phi.float(), 2 * _tol(K))
+    assert ((q - ref_q).abs() / ref_q.abs()).max().item() <= 1e-5
+    ref_seed = (v * s.double()).float()
+    _close(seed.float(), ref_seed, 2 ** -8 + 2 * _tol(K))

@@ -6,7 +6,8 @@ register-held keys cover, tiny N, and a fixed t.
 
 Tolerances: t* within 1e-12 relative (the GPU stops its bracket a few ulps wide, the
 oracle bisects to adjacent doubles); rho and d rho/dt within 1e-12 and 1e-9 absolute;
-the weights, applied to three seeded gradient columns, within 1e-9 relative.
+the weights applied to three seeded gradient columns, and the kernel's own weighted
+gradient sums, within 1e-9 relative.
 """
 import zlib
 
@@ -62,18 +63,22 @@ def test_risk_weights_parity(case):
              capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.9, eps=1e-3, t=float(np.median(Q)), t_optimal=0)]
     q = torch.tensor(Q, device="cuda")
     w = torch.empty(len(risks), N, device="cuda", dtype=torch.float64)
-    out = capi.ouu_kernel_risk_weights(q, risks, w)
+    G32 = G.astype(np.float32)
+    out, grad = capi.ouu_kernel_risk_weights(q, risks, w, gq=torch.tensor(G32, device="cuda"))
     W = w.cpu().numpy()
+    G = G32.astype(np.float64)   # the gradients the kernel sums
 
     rho, g, dt, t = risk.cvar(Q, G, beta=beta, eps=eps, t_optimal=True)
     assert abs(out[0, 2] - t) <= 1e-12 * max(1.0, abs(t))
     assert abs(out[0, 0] - rho) <= 1e-12 * max(1.0, abs(rho))
     assert abs(out[0, 1] - dt) <= 1e-9
     np.testing.assert_allclose(W[0] @ G, g, rtol=1e-9, atol=1e-12 * np.abs(G).sum())
+    np.testing.assert_allclose(grad[0], g, rtol=1e-9, atol=1e-12 * np.abs(G).sum())
 
     rho_mv, g_mv = risk.mean_var(Q, G, kappa=kappa)
     assert abs(out[1, 0] - rho_mv) <= 1e-12 * max(1.0, abs(rho_mv))
     np.testing.assert_allclose(W[1] @ G, g_mv, rtol=1e-9, atol=1e-12 * np.abs(G).sum())
+    np.testing.assert_allclose(grad[1], g_mv, rtol=1e-9, atol=1e-12 * np.abs(G).sum())
 
     tf = float(np.median(Q))
     rho_f, g_f, dt_f, _ = risk.cvar(Q, G, beta=0.9, eps=1e-3, t=tf, t_optimal=False)
@@ -81,6 +86,7 @@ def test_risk_weights_parity(case):
     assert abs(out[2, 0] - rho_f) <= 1e-12 * max(1.0, abs(rho_f))
     assert abs(out[2, 1] - dt_f) <= 1e-9
     np.testing.assert_allclose(W[2] @ G, g_f, rtol=1e-9, atol=1e-12 * np.abs(G).sum())
+    np.testing.assert_allclose(grad[2], g_f, rtol=1e-9, atol=1e-12 * np.abs(G).sum())
 
 
 def test_risk_weights_repeat_calls_agree():
