@@ -38,6 +38,7 @@ __global__ void k_build_x0(const float* __restrict__ xi, const int* __restrict__
                            int64_t z_stride, int rm, int dz, int in0p, int B, __nv_bfloat16* __restrict__ x0,
                            __nv_bfloat16* __restrict__ x0t) {
   // four consecutive columns per thread (in0p is a multiple of 8): one 8-byte store
+  pdl_wait();
   const int q4 = in0p >> 2;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * q4; e += gridDim.x * blockDim.x) {
     const int b = e / q4, k0 = 4 * (e - b * q4);
@@ -785,8 +786,9 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
   for (int j = 0; j < dz; ++j) zh[j] = (float)z_host[j];
   OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)dz * 4, cudaMemcpyHostToDevice, d->stream));
   DINO_TRY(project_fields(d, m_dev, N, d->XIe, true));
-  k_build_x0<<<grid_for((int64_t)N * (in0p / 4)), 256, 0, d->stream>>>(d->XIe, nullptr, d->d_zf, 0, d->rm, dz, in0p, N,
-                                                                  d->X0e, nullptr);
+  OUU_CUDA_TRY(launch_pdl(k_build_x0, dim3(grid_for((int64_t)N * (in0p / 4))), dim3(256), 0, d->stream,
+                          (const float*)d->XIe, (const int*)nullptr, (const float*)d->d_zf, (int64_t)0, d->rm, dz, in0p,
+                          N, d->X0e, (__nv_bfloat16*)nullptr));
   __nv_bfloat16* hin = d->X0e;
   int ldin = in0p, kin = d->in0;
   __nv_bfloat16* hbuf[2] = {d->He0, d->He1};

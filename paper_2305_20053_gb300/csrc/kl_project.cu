@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
     fence_async_smem();
   }
   if (warp == KLP_MMA_WARP) tmem_alloc(tslot, 512);
+  pdl_wait();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -367,8 +368,7 @@ ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W
   }
   const int grid = (int)std::min<long long>(a.U, (long long)std::max(1, num_sms));
   OUU_CUDA_TRY(cudaMemsetAsync(xi, 0, (size_t)N * rm * 4, s));
-  k_kl_project<<<grid, KLP_THREADS, smem, s>>>(tw, tm, a);
-  OUU_CUDA_TRY(cudaGetLastError());
+  OUU_CUDA_TRY(launch_pdl(k_kl_project, dim3(grid), dim3(KLP_THREADS), smem, s, tw, tm, a));
   return OUU_OK;
 }
 

@@ -10,6 +10,29 @@
 // ------------------------------------------------------------------ errors
 void ouu_set_error(const std::string& msg);
 
+// ------------------------------------------------------------------ programmatic dependent launch
+// Kernels launched with launch_pdl may start while the previous kernel in the stream drains
+// (their set-up overlaps its tail); each calls pdl_wait() before it reads or writes global
+// memory that earlier kernels touch.  No kernel triggers its dependents early, so a kernel's
+// completion still implies the completion of every kernel before it.
+static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 #define OUU_CUDA_TRY(expr)                                                              \
   do {                                                                                  \
     cudaError_t e_ = (expr);                                                            \

@@ -144,6 +144,7 @@ static __device__ double kth_largest(const double* q, int N, int k, unsigned* hi
 __global__ void k_risk_moments(const double* __restrict__ q, int N, double* __restrict__ part) {
   __shared__ double red[40];
   BlockRed br{red};
+  pdl_wait();
   double s = 0.0, s2 = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const double v = q[i];
@@ -296,6 +297,7 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
   __shared__ bool s_ok;
   __shared__ double red[40];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  pdl_wait();
   if (zero_out)   // the weighted-gradient sums of the next pass start from 0
     for (int i = threadIdx.x; i < n_zero; i += blockDim.x) zero_out[i] = 0.0;
   // key prefixes first: their loads are in flight while warp 0 combines the moments
@@ -486,6 +488,7 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
   __shared__ double ws[OUU_MAX_RISKS][APPLY_SUB];
   __shared__ double gsum[OUU_MAX_RISKS][128];
   BlockRed br{red};
+  pdl_wait();
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int i0 = min(N, (int)blockIdx.x * chunk), i1 = min(N, i0 + chunk);
   double sv[OUU_MAX_RISKS], sd[OUU_MAX_RISKS];
@@ -597,12 +600,12 @@ void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n
   static_assert(OUU_RISK_SCRATCH >= 3 * OUU_MAX_RISKS + 2 * OUU_MAX_RISKS * RISK_BLOCKS + 1, "risk scratch size");
   double* params = scratch;
   double* part = scratch + 3 * OUU_MAX_RISKS;
-  k_risk_moments<<<RISK_BLOCKS, 256, 0, s>>>(q, N, part);
-  k_risk_select<<<1, 1024, 0, s>>>(q, N, part, RISK_BLOCKS, risks_dev, n_risks, params, gq ? grad_out : nullptr,
-                                   n_risks * dz);
+  launch_pdl(k_risk_moments, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, part);
+  launch_pdl(k_risk_select, dim3(1), dim3(1024), 0, s, q, N, (const double*)part, RISK_BLOCKS, risks_dev, n_risks,
+             params, gq ? grad_out : nullptr, n_risks * dz);
   unsigned* arrivals = (unsigned*)(scratch + OUU_RISK_SCRATCH - 1);   // zeroed at problem creation
-  k_risk_apply<<<RISK_BLOCKS, 256, 0, s>>>(q, N, risks_dev, n_risks, params, w, part, arrivals, out, gq, ldg, dz,
-                                           grad_out);
+  launch_pdl(k_risk_apply, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, risks_dev, n_risks, (const double*)params, w,
+             part, arrivals, out, gq, ldg, dz, grad_out);
 }
 
 // Kernel-level entry used by the risk-weight numerics test (declared in include/ouu_kernels.h).

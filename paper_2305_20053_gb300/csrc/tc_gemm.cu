@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tslot, TMEM_COLS);
+  pdl_wait();   // everything below reads or writes what earlier kernels produce or consume
   for (int i = threadIdx.x; i < BN; i += GEMM_THREADS) {   // per-column epilogue constants
     const int c = n0 + i;
     s_bias[i] = (c < N && ep.bias && blockIdx.z == 0) ? ep.bias[c] : 0.f;
@@ -398,8 +399,7 @@ static ouu_status launch_bn(const CUtensorMap& ta, const __nv_bfloat16* B, int l
     attr_set = true;
   }
   dim3 grid((N + BN - 1) / BN, (M + GEMM_BM - 1) / GEMM_BM, splits);
-  k_gemm_bf16<BN><<<grid, GEMM_THREADS, smem, s>>>(ta, tb, M, N, K, ep, err);
-  OUU_CUDA_TRY(cudaGetLastError());
+  OUU_CUDA_TRY(launch_pdl(k_gemm_bf16<BN>, grid, dim3(GEMM_THREADS), smem, s, ta, tb, M, N, K, ep, err));
   return OUU_OK;
 }
 
