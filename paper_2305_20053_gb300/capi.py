@@ -206,21 +206,27 @@ class Problem:
                                        dev_ptr(gradq_dev, torch.float64)))
 
     def ouu_risk_and_grad(self, backend, dino, m_dev, n_samples, risks, z_host):
-        """Returns (risk[n_risks], grad_z[n_risks, d_Z], grad_t[n_risks], t[n_risks], stats)."""
+        """Returns (risk[n_risks], grad_z[n_risks, d_Z], grad_t[n_risks], t[n_risks], stats).
+        The ctypes argument blocks are kept between calls with the same risk descriptors
+        (marshalling only; the returned arrays are fresh copies)."""
         import torch
-        nr = len(risks)
-        arr = (RiskDesc * nr)(*risks)
-        z = np.ascontiguousarray(z_host, dtype=np.float64)
-        risk = np.zeros(nr)
-        grad = np.zeros((nr, self.d_z))
-        gt = np.zeros(nr)
-        t = np.zeros(nr)
-        st = EvalStats()
-        P = lambda a: a.ctypes.data_as(_dp)
+        key = tuple(bytes(r) for r in risks)
+        c = getattr(self, "_rg_cache", None)
+        if c is None or c["key"] != key:
+            nr = len(risks)
+            bufs = dict(z=np.zeros(self.d_z), risk=np.zeros(nr), grad=np.zeros((nr, self.d_z)), gt=np.zeros(nr),
+                        t=np.zeros(nr))
+            c = dict(key=key, nr=nr, arr=(RiskDesc * nr)(*risks), st=EvalStats(), **bufs,
+                     ptr={k: v.ctypes.data_as(_dp) for k, v in bufs.items()})
+            c["st_ref"] = ctypes.byref(c["st"])
+            self._rg_cache = c
+        c["z"][:] = z_host
+        p = c["ptr"]
         check(load().ouu_risk_and_grad(self.handle, backend, dino.handle if dino is not None else None,
-                                       dev_ptr(m_dev, torch.float64), n_samples, arr, nr, P(z), P(risk), P(grad),
-                                       P(gt), P(t), ctypes.byref(st)))
-        return risk, grad, gt, t, st
+                                       dev_ptr(m_dev, torch.float64), n_samples, c["arr"], c["nr"], p["z"], p["risk"],
+                                       p["grad"], p["gt"], p["t"], c["st_ref"]))
+        return (c["risk"].copy(), c["grad"].copy(), c["gt"].copy(), c["t"].copy(),
+                EvalStats.from_buffer_copy(c["st"]))
 
 
 def ouu_pde_solve_batch_noalloc(desc, m_dev, n_samples, z_dev, z_stride, u_dev, q_dev, status_dev, stream=None):
