@@ -284,6 +284,52 @@ size_t ouu_last_error(char* buf, size_t len);
 /* Number of samples one persistent launch keeps in flight (one per CTA). */
 int ouu_problem_slots(ouu_problem_t p);
 
+/* ---------------------------------------------------------------------------------------
+ * Uneven batches: many OUU problems (different grids, sample counts, control counts,
+ * risks, plain or MR-DINO backend) evaluated together, the risk and z-gradient of each at
+ * its own z (Sec. 2.1-2.3 per problem).  The paper evaluates one problem at a time; this
+ * is a throughput interface for many concurrent problems.
+ *
+ * Execution, captured once into one CUDA graph and replayed by later runs:
+ *   - the state solves of every sample of every plain problem in ONE persistent launch
+ *     (tasks (problem, sample), largest grids first, pulled by one CTA per SM), then each
+ *     problem's risk weights, then the adjoint solves in one persistent launch, then each
+ *     problem's G^T sum;
+ *   - each MR-DINO problem's evaluation on a concurrent branch of the graph.
+ * With autotune != 0, ouu_batch_create first runs every MR-DINO problem once eagerly
+ * with the GEMM tile autotuner on (each network layer shape gets the fastest measured
+ * tile width).
+ *
+ * Each item names its own problem handle (items must not share one; the handle's arena
+ * holds the item's results), its fields m_dev [n_samples][n][n] (device, caller-owned,
+ * unchanged between runs) and 1..4 risk descriptors; MR-DINO items name a network built
+ * for the same grid and controls with max_eval >= n_samples.  The batch runs on the
+ * stream of the first item's problem. */
+typedef struct ouu_batch* ouu_batch_t;
+
+typedef struct {
+  ouu_problem_t problem;
+  ouu_backend backend;
+  ouu_dino_t dino;              /* OUU_BACKEND_DINO items, else NULL */
+  const double* m_dev;
+  int n_samples;
+  const ouu_risk_desc* risks;   /* copied at create */
+  int n_risks;
+} ouu_batch_item;
+
+ouu_status ouu_batch_create(const ouu_batch_item* items, int n_items, int autotune, ouu_batch_t* out);
+void ouu_batch_destroy(ouu_batch_t b);
+
+/* One evaluation of every item.  z_hosts[k]: item k's controls (host, d_Z of its problem).
+ * Outputs per item k (host arrays, like ouu_risk_and_grad): risk_out[k][n_risks],
+ * grad_z_out[k][n_risks * d_Z], grad_t_out[k][n_risks], t_out[k][n_risks] (t_out may be
+ * NULL).  item_ms (may be NULL): per item, MR-DINO items their graph branch's time, plain
+ * items their share of the two persistent launches (SM cycles of their tasks / SM count /
+ * clock).  total_ms (may be NULL): the whole batch on the device.  Synchronises. */
+ouu_status ouu_batch_run(ouu_batch_t b, const double* const* z_hosts, double* const* risk_out,
+                         double* const* grad_z_out, double* const* grad_t_out, double* const* t_out,
+                         double* item_ms, double* total_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,6 +59,10 @@ ouu_status ouu_kernel_risk_weights(const double* q_dev, int N, const ouu_risk_de
                                    double* out_host, const float* gq_dev, int ldg, int dz, double* grad_host,
                                    void* stream);
 
+/* Number of GEMM shapes the tile autotuner has timed so far (ouu_batch_create with
+ * autotune != 0 tunes the MR-DINO layer shapes). */
+int ouu_kernel_gemm_tuned_shapes(void);
+
 ouu_status ouu_kernel_kl_project(const double* m, int N, int nn, const void* W, int ldw, int rm, const float* bias,
                                  float* xi, int* err_dev, void* stream);
 

@@ -56,6 +56,12 @@ class EvalStats(ctypes.Structure):
                 ("ms_project", ctypes.c_float), ("ms_network", ctypes.c_float)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("problem", ctypes.c_void_p), ("backend", ctypes.c_int), ("dino", ctypes.c_void_p),
+                ("m_dev", ctypes.c_void_p), ("n_samples", ctypes.c_int), ("risks", ctypes.POINTER(RiskDesc)),
+                ("n_risks", ctypes.c_int)]
+
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _i64 = ctypes.c_int64
@@ -97,6 +103,11 @@ SIGNATURES = {
     "ouu_kernel_risk_weights": (_i, [_vp, _i, ctypes.POINTER(RiskDesc), _i, _vp, _dp, _vp, _i, _i, _dp, _vp]),
     "ouu_kernel_gemm_qoi_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _vp, _vp, _vp, ctypes.c_double, _vp, _i, _vp, _i,
                                       _vp, _vp, _vp]),
+    "ouu_batch_create": (_i, [ctypes.POINTER(BatchItem), _i, _i, ctypes.POINTER(_vp)]),
+    "ouu_batch_destroy": (None, [_vp]),
+    "ouu_batch_run": (_i, [_vp, ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
+                           ctypes.POINTER(_dp), _dp, _dp]),
+    "ouu_kernel_gemm_tuned_shapes": (_i, []),
     "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "ouu_problem_slots": (_i, [_vp]),
 }
@@ -423,3 +434,58 @@ def unflatten_params(p, widths):
         bs.append(np.asarray(p[o:o + fo], np.float64))
         o += fo
     return Ws, bs
+
+
+class Batch:
+    """Owns an ouu_batch_t: many problems evaluated together (one CUDA graph per batch).
+    items: sequence of dicts with keys problem (Problem), backend, dino (Dino or None),
+    m (device FP64 fields), n (samples), risks (list of RiskDesc)."""
+
+    def __init__(self, items, autotune=False):
+        import torch
+        self._keep = []
+        arr = (BatchItem * len(items))()
+        self.d_z, self.n_risks = [], []
+        for k, it in enumerate(items):
+            rk = (RiskDesc * len(it["risks"]))(*it["risks"])
+            self._keep += [it["problem"], it.get("dino"), it["m"], rk]
+            arr[k].problem = it["problem"].handle
+            arr[k].backend = it["backend"]
+            arr[k].dino = it["dino"].handle if it.get("dino") is not None else None
+            arr[k].m_dev = dev_ptr(it["m"], torch.float64)
+            arr[k].n_samples = it["n"]
+            arr[k].risks = rk
+            arr[k].n_risks = len(it["risks"])
+            self.d_z.append(it["problem"].d_z)
+            self.n_risks.append(len(it["risks"]))
+        h = ctypes.c_void_p()
+        check(load().ouu_batch_create(arr, len(items), 1 if autotune else 0, ctypes.byref(h)))
+        self.handle = h
+        self.n_items = len(items)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ouu_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, zs):
+        """One evaluation of every item at its control zs[k].  Returns (results, item_ms,
+        total_ms); results[k] = (risk[n_risks], grad_z[n_risks, d_Z], grad_t[n_risks], t[n_risks])."""
+        K = self.n_items
+        z = [np.ascontiguousarray(zs[k], dtype=np.float64) for k in range(K)]
+        risk = [np.zeros(self.n_risks[k]) for k in range(K)]
+        grad = [np.zeros((self.n_risks[k], self.d_z[k])) for k in range(K)]
+        gt = [np.zeros(self.n_risks[k]) for k in range(K)]
+        t = [np.zeros(self.n_risks[k]) for k in range(K)]
+        ptrs = lambda arrs: (_dp * K)(*[a.ctypes.data_as(_dp) for a in arrs])
+        ms = np.zeros(K)
+        total = np.zeros(1)
+        check(load().ouu_batch_run(self.handle, ptrs(z), ptrs(risk), ptrs(grad), ptrs(gt), ptrs(t),
+                                   ms.ctypes.data_as(_dp), total.ctypes.data_as(_dp)))
+        return [(risk[k], grad[k], gt[k], t[k]) for k in range(K)], ms, float(total[0])

@@ -263,7 +263,7 @@ extern "C" ouu_status ouu_sample_fields(ouu_problem_t p, uint64_t seed, int64_t 
   return OUU_OK;
 }
 
-static PdeArgs base_args(ouu_problem* p, int n_samples) {
+PdeArgs ouu_base_args(ouu_problem* p, int n_samples) {
   PdeArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = p->n;
@@ -319,7 +319,7 @@ extern "C" ouu_status ouu_pde_solve_batch(ouu_problem_t p, const double* m_dev, 
   if (n_samples == 0) return OUU_OK;
   OUU_CHECK_ARG(m_dev && z_dev && q_dev, "m_dev, z_dev and q_dev are required");
   OUU_CHECK_ARG(z_stride == 0 || z_stride >= p->dz, "z_stride must be 0 or >= d_Z");
-  PdeArgs a = base_args(p, n_samples);
+  PdeArgs a = ouu_base_args(p, n_samples);
   a.m = m_dev;
   a.z = z_dev;
   a.z_stride = z_stride;
@@ -340,7 +340,7 @@ extern "C" ouu_status ouu_adjoint_batch(ouu_problem_t p, const double* m_dev, co
   OUU_CHECK_ARG(n_samples >= 0 && n_samples <= p->desc.max_samples, "n_samples outside [0, max_samples]");
   if (n_samples == 0 || (!lambda_dev && !gradq_dev)) return OUU_OK;
   OUU_CHECK_ARG(m_dev && u_dev, "m_dev and u_dev are required");
-  PdeArgs a = base_args(p, n_samples);
+  PdeArgs a = ouu_base_args(p, n_samples);
   a.m = m_dev;
   a.u = const_cast<double*>(u_dev);
   a.lam_out = lambda_dev;
@@ -365,6 +365,28 @@ static ouu_status check_risks(const ouu_risk_desc* risks, int n_risks) {
       OUU_CHECK_ARG(std::isfinite(R.t), "t must be finite");
     }
   }
+  return OUU_OK;
+}
+
+// The MR-DINO risk evaluation as one stream-ordered sequence on dino->stream: projection +
+// network + reduced QoI + reverse-mode gradient, risk weights with the weighted gradient
+// sum, results (and the GEMM error flag) to the problem's pinned host mirror.  The risk
+// descriptors must already be in p->d_risks.
+ouu_status dino_enqueue_risk(ouu_problem* p, ouu_dino* dino, const double* m_dev, int n_samples, int n_risks,
+                             const double* z_host) {
+  const int dz = p->dz;
+  double* d_res = p->d_out;
+  double* d_grad = p->d_out + 3 * OUU_MAX_RISKS;
+  const size_t ob = (size_t)(OUU_MAX_RISKS * (3 + dz) + 8) * 8;
+  if (ouu_status st = dino_eval_core(dino, m_dev, n_samples, z_host, true)) return st;
+  if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[1], dino->stream));
+  // weights, risk values and sum_i w_i grad Q_i in one pass over the samples
+  launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream, dino->GQe,
+                      (dz + 7) / 8 * 8, dz, d_grad);
+  if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[2], dino->stream));
+  OUU_CUDA_TRY(cudaGetLastError());
+  OUU_CUDA_TRY(cudaMemcpyAsync(p->h_out, p->d_out, ob, cudaMemcpyDeviceToHost, dino->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(p->h_stat, dino->d_err, 4, cudaMemcpyDeviceToHost, dino->stream));
   return OUU_OK;
 }
 
@@ -404,21 +426,7 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
       return OUU_ERR_STATE;
     }
     cudaStream_t ds = dino->stream;
-    const size_t ob = (size_t)(OUU_MAX_RISKS * (3 + dz) + 8) * 8;
-    // The evaluation as one stream-ordered sequence: projection + network + reduced QoI +
-    // reverse-mode gradient, risk weights, weighted gradient sum, results to pinned host memory.
-    auto enqueue = [&]() -> ouu_status {
-      if (ouu_status st = dino_eval_core(dino, m_dev, n_samples, z_host, true)) return st;
-      if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[1], dino->stream));
-      // weights, risk values and sum_i w_i grad Q_i in one pass over the samples
-      launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream,
-                          dino->GQe, (dz + 7) / 8 * 8, dz, d_grad);
-      if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[2], dino->stream));
-      OUU_CUDA_TRY(cudaGetLastError());
-      OUU_CUDA_TRY(cudaMemcpyAsync(p->h_out, p->d_out, ob, cudaMemcpyDeviceToHost, dino->stream));
-      OUU_CUDA_TRY(cudaMemcpyAsync(p->h_stat, dino->d_err, 4, cudaMemcpyDeviceToHost, dino->stream));
-      return OUU_OK;
-    };
+    auto enqueue = [&]() -> ouu_status { return dino_enqueue_risk(p, dino, m_dev, n_samples, n_risks, z_host); };
     const bool replay = dino->use_graphs && dino->gexec && dino->gkey_p == p && dino->gkey_m == m_dev &&
                         dino->gkey_N == n_samples && dino->gkey_nr == n_risks;
     OUU_CUDA_TRY(cudaEventRecord(p->ev[0], ds));
@@ -486,7 +494,7 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
     return OUU_OK;
   }
   OUU_CHECK_ARG(backend == OUU_BACKEND_PDE, "unknown backend");
-  PdeArgs a = base_args(p, n_samples);
+  PdeArgs a = ouu_base_args(p, n_samples);
   a.m = m_dev;
   a.z = p->d_z;
   a.z_stride = 0;
@@ -570,7 +578,7 @@ extern "C" ouu_status ouu_dino_jacobian_data(ouu_problem_t p, ouu_dino_t d, cons
     return OUU_ERR_STATE;
   }
   if (n_samples == 0) return OUU_OK;
-  PdeArgs a = base_args(p, n_samples);
+  PdeArgs a = ouu_base_args(p, n_samples);
   a.m = m_dev;
   a.u = const_cast<double*>(u_dev);
   OUU_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, 4, p->stream));

@@ -73,6 +73,11 @@ struct ouu_dino {
 
 // DINO forward/backward pieces used by the C ABI (dino.cu).
 ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad);
+
+// The whole MR-DINO risk evaluation enqueued on d->stream (capi.cu); the problem's risk
+// descriptors must be in p->d_risks.
+ouu_status dino_enqueue_risk(ouu_problem* p, ouu_dino* d, const double* m_dev, int n_samples, int n_risks,
+                             const double* z_host);
 // Completes a basis whose FP64 Phi and ubar are in place (FP32 copy, reduced-QoI terms).
 ouu_status dino_install_bases(ouu_dino* d);
 // Sum_i w[r][i] grad_z Q_i of the last evaluation into out [n_w][d_Z] (device).

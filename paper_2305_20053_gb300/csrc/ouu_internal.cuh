@@ -134,13 +134,25 @@ struct PdeArgs {
   char* slots;
   SlotLayout lay;
   int* counter;
+  double* acc_out;            // batch adjoint: [n_w][n*n] sums the slots are flushed into
 };
 
+struct ouu_problem;
+PdeArgs ouu_base_args(ouu_problem* p, int n_samples);
 void launch_pde_state(const PdeArgs& a, int nslots, cudaStream_t s);
+// One persistent launch over tasks (problem, sample) of many problems (probs_dev: device
+// array of per-problem arguments; tasks_dev: device int2 array).  adjoint: adjoint solves
+// with weighted sums flushed into probs[p].acc_out (zeroed beforehand); else state solves.
+void launch_pde_batch(const PdeArgs* probs_dev, const int2* tasks_dev, int n_tasks, char* slots, int64_t slot_bytes,
+                      int64_t smem_bytes, int nslots, int* counter, unsigned long long* cycles, bool adjoint,
+                      cudaStream_t s);
 void launch_pde_adjoint(const PdeArgs& a, int nslots, cudaStream_t s);
 
 // Sum the per-slot FP64 accumulators [slot][n_w][n*n] into s_out [n_w][n*n], then
 // grad[r][j] = scale * sum_{iy,ix} gy[jy][iy] gx[jx][ix] s[r][iy*n+ix].
+// grad[r][j] = gscale * sum_{iy,ix} gy[jy][iy] gx[jx][ix] s[r][iy*n+ix] for r < n_w.
+void launch_sources_transpose(int n, int L, int n_w, const double* gx, const double* gy, double gscale,
+                              const double* s, double* grad, cudaStream_t st);
 void launch_reduce_slots_and_gradient(const char* slots, const SlotLayout& lay, int nslots, int n, int L,
                                       int n_w, const double* gx, const double* gy, double gscale,
                                       double* s_out, double* grad, cudaStream_t st);

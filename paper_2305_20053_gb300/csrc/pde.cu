@@ -51,7 +51,37 @@ static __device__ void zero_smem(unsigned char* smem, int64_t bytes) {
   __syncthreads();
 }
 
-// State solve + QoI for every sample (Sec. 4.2 state equation, Newton).
+// State solve + QoI of sample i (Sec. 4.2 state equation, Newton), collective over the CTA.
+static __device__ void state_task(const PdeArgs& a, CtaCtx& c, Hierarchy& H, char* slot, int i) {
+  double* E = (double*)(slot + a.lay.E);
+  double* f = (double*)(slot + a.lay.f);
+  double* tmp = (double*)(slot + a.lay.tmp);
+  float* x = (float*)(slot + a.lay.x);
+  float* p = (float*)(slot + a.lay.p);
+  float* q = (float*)(slot + a.lay.q);
+  const int n = a.n;
+  const int64_t nn = (int64_t)n * n;
+  const double* m = a.m + (int64_t)i * nn;
+  double* u = a.u + (int64_t)i * nn;
+  build_fine_coeffs(c, n, m, E, H.lev[0]);
+  c.sync();
+  setup_coarse_coeffs(c, H);
+  build_forcing(c, n, a.L, a.gx, a.gy, a.gscale, a.z + (int64_t)i * a.z_stride, tmp, f);
+  for (int64_t k = threadIdx.x; k < nn; k += blockDim.x) u[k] = 0.0;
+  c.sync();
+  NewtonResult nr = newton_solve(c, H, a.rr, E, f, u, x, p, q, a.newton_rtol, a.newton_maxit, a.cg_rtol, a.cg_maxit);
+  const double Q = qoi_and_grad(c, n, u, a.ut, (double*)nullptr);
+  if (threadIdx.x == 0) {
+    a.q[i] = Q;
+    a.status[i] = nr.status;
+    a.iters[3 * i + 0] = nr.newton_iters;
+    a.iters[3 * i + 1] = nr.cg_iters;
+    a.iters[3 * i + 2] = 0;
+  }
+  c.sync();
+}
+
+// State solves of every sample of one problem.
 __global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1) k_pde_state(PdeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[40];
@@ -61,52 +91,18 @@ __global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1) k_pde_state(PdeArgs a) 
   char* slot = a.slots + (int64_t)blockIdx.x * a.lay.bytes;
   Hierarchy H;
   build_hierarchy(a, slot, smem, H);
-  double* E = (double*)(slot + a.lay.E);
-  double* f = (double*)(slot + a.lay.f);
-  double* tmp = (double*)(slot + a.lay.tmp);
-  float* x = (float*)(slot + a.lay.x);
-  float* p = (float*)(slot + a.lay.p);
-  float* q = (float*)(slot + a.lay.q);
-  const int n = a.n;
-  const int64_t nn = (int64_t)n * n;
   for (;;) {
     const int i = next_sample(a.counter, &s_idx);
     if (i >= a.n_samples) break;
-    const double* m = a.m + (int64_t)i * nn;
-    double* u = a.u + (int64_t)i * nn;
-    build_fine_coeffs(c, n, m, E, H.lev[0]);
-    c.sync();
-    setup_coarse_coeffs(c, H);
-    build_forcing(c, n, a.L, a.gx, a.gy, a.gscale, a.z + (int64_t)i * a.z_stride, tmp, f);
-    for (int64_t k = threadIdx.x; k < nn; k += blockDim.x) u[k] = 0.0;
-    c.sync();
-    NewtonResult nr = newton_solve(c, H, a.rr, E, f, u, x, p, q, a.newton_rtol, a.newton_maxit, a.cg_rtol,
-                                   a.cg_maxit);
-    const double Q = qoi_and_grad(c, n, u, a.ut, (double*)nullptr);
-    if (threadIdx.x == 0) {
-      a.q[i] = Q;
-      a.status[i] = nr.status;
-      a.iters[3 * i + 0] = nr.newton_iters;
-      a.iters[3 * i + 1] = nr.cg_iters;
-      a.iters[3 * i + 2] = 0;
-    }
-    c.sync();
+    state_task(a, c, H, slot, i);
   }
 }
 
-// Adjoint solve (Sec. 2.3) per sample: J(u_i) lam_i = h^2 (u_i - u_t).  With risk
-// weights w[r][i], samples whose weights are all zero are skipped and
-// sum_i w[r][i] lam_i is accumulated per slot; per-sample lam_i and
-// grad_z Q_i = G^T lam_i are written when requested.
-__global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1) k_pde_adjoint(PdeArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[40];
-  __shared__ int s_idx;
-  CtaCtx c{red};
-  zero_smem(smem, a.lay.smem_bytes);
-  char* slot = a.slots + (int64_t)blockIdx.x * a.lay.bytes;
-  Hierarchy H;
-  build_hierarchy(a, slot, smem, H);
+// Adjoint solve (Sec. 2.3) of sample i: J(u_i) lam_i = h^2 (u_i - u_t).  With risk
+// weights w[r][i], a sample whose weights are all zero is skipped and sum_i w[r][i] lam_i
+// is accumulated in the slot; per-sample lam_i and grad_z Q_i = G^T lam_i are written when
+// requested.  Collective over the CTA.
+static __device__ void adjoint_task(const PdeArgs& a, CtaCtx& c, Hierarchy& H, char* slot, int i) {
   double* E = (double*)(slot + a.lay.E);
   double* b = (double*)(slot + a.lay.f);
   double* tmp = (double*)(slot + a.lay.tmp);
@@ -117,62 +113,145 @@ __global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1) k_pde_adjoint(PdeArgs a
   float* q = (float*)(slot + a.lay.q);
   const int n = a.n, L = a.L;
   const int64_t nn = (int64_t)n * n;
+  bool need = a.lam_out != nullptr || a.grad_out != nullptr;
   if (a.w)
-    for (int64_t k = threadIdx.x; k < (int64_t)a.n_w * nn; k += blockDim.x) acc[k] = 0.0;
+    for (int r = 0; r < a.n_w; ++r) need = need || a.w[(int64_t)r * a.n_samples + i] != 0.0;
+  if (!need) return;
+  const double* m = a.m + (int64_t)i * nn;
+  const double* u = a.u + (int64_t)i * nn;
+  build_fine_coeffs(c, n, m, E, H.lev[0]);
+  c.sync();
+  setup_coarse_coeffs(c, H);
+  setup_jacobian(c, H, a.rr, u);
+  qoi_and_grad(c, n, u, a.ut, b);
+  double* lam = a.lam_out ? a.lam_out + (int64_t)i * nn : lam_slot;
+  for (int64_t k = threadIdx.x; k < nn; k += blockDim.x) lam[k] = 0.0;
+  c.sync();
+  NewtonResult rr = refine_solve(c, H, a.rr, E, u, b, lam, x, p, q, a.refine_rtol, a.refine_maxit, a.cg_rtol,
+                                 a.cg_maxit);
+  if (a.w) {
+    for (int r = 0; r < a.n_w; ++r) {
+      const double wr = a.w[(int64_t)r * a.n_samples + i];
+      if (wr == 0.0) continue;
+      double* ar = acc + (int64_t)r * nn;
+      OUU_FOR_INTERIOR(c, n, iy, ix) {
+        const int k = iy * n + ix;
+        ar[k] += wr * lam[k];
+      }
+    }
+  }
+  if (a.grad_out) {
+    // tmp[jx][iy] = sum_ix gx[jx][ix] lam[iy][ix]; grad[jy L + jx] = s sum_iy gy[jy][iy] tmp[jx][iy]
+    for (int jx = c.row0(); jx < L; jx += c.rowstep())
+      for (int iy = c.col0(); iy < n; iy += c.colstep()) {
+        double s = 0.0;
+        for (int ix = 1; ix < n - 1; ++ix) s += a.gx[jx * n + ix] * lam[iy * n + ix];
+        tmp[jx * n + iy] = s;
+      }
+    c.sync();
+    for (int j = threadIdx.x; j < L * L; j += blockDim.x) {
+      const int jy = j / L, jx = j % L;
+      double s = 0.0;
+      for (int iy = 1; iy < n - 1; ++iy) s += a.gy[jy * n + iy] * tmp[jx * n + iy];
+      a.grad_out[(int64_t)i * L * L + j] = a.gscale * s;
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (a.solved) atomicAdd(a.solved, 1);
+    if (rr.status > a.status[i]) a.status[i] = rr.status;
+    a.iters[3 * i + 2] = rr.newton_iters;
+    a.iters[3 * i + 1] += rr.cg_iters;
+  }
+  c.sync();
+}
+
+// Adjoint solves of every sample of one problem; the slot accumulators are summed over the
+// slots afterwards (launch_reduce_slots_and_gradient).
+__global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1) k_pde_adjoint(PdeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[40];
+  __shared__ int s_idx;
+  CtaCtx c{red};
+  zero_smem(smem, a.lay.smem_bytes);
+  char* slot = a.slots + (int64_t)blockIdx.x * a.lay.bytes;
+  Hierarchy H;
+  build_hierarchy(a, slot, smem, H);
+  if (a.w) {
+    double* acc = (double*)(slot + a.lay.acc);
+    for (int64_t k = threadIdx.x; k < (int64_t)a.n_w * a.n * a.n; k += blockDim.x) acc[k] = 0.0;
+  }
   __syncthreads();
   for (;;) {
     const int i = next_sample(a.counter, &s_idx);
     if (i >= a.n_samples) break;
-    bool need = a.lam_out != nullptr || a.grad_out != nullptr;
-    if (a.w)
-      for (int r = 0; r < a.n_w; ++r) need = need || a.w[(int64_t)r * a.n_samples + i] != 0.0;
-    if (!need) continue;
-    const double* m = a.m + (int64_t)i * nn;
-    const double* u = a.u + (int64_t)i * nn;
-    build_fine_coeffs(c, n, m, E, H.lev[0]);
-    c.sync();
-    setup_coarse_coeffs(c, H);
-    setup_jacobian(c, H, a.rr, u);
-    qoi_and_grad(c, n, u, a.ut, b);
-    double* lam = a.lam_out ? a.lam_out + (int64_t)i * nn : lam_slot;
-    for (int64_t k = threadIdx.x; k < nn; k += blockDim.x) lam[k] = 0.0;
-    c.sync();
-    NewtonResult rr = refine_solve(c, H, a.rr, E, u, b, lam, x, p, q, a.refine_rtol, a.refine_maxit,
-                                   a.cg_rtol, a.cg_maxit);
-    if (a.w) {
-      for (int r = 0; r < a.n_w; ++r) {
-        const double wr = a.w[(int64_t)r * a.n_samples + i];
-        if (wr == 0.0) continue;
-        double* ar = acc + (int64_t)r * nn;
-        OUU_FOR_INTERIOR(c, n, iy, ix) {
-          const int k = iy * n + ix;
-          ar[k] += wr * lam[k];
-        }
-      }
+    adjoint_task(a, c, H, slot, i);
+  }
+}
+
+// ------------------------------------------------------------------ many problems, one launch
+// Tasks (problem, sample) of many problems of different grids, control counts and sample
+// counts, pulled from one counter by persistent CTAs.  A CTA's slot (sized for the largest
+// grid) and shared-memory levels are re-zeroed and the multigrid hierarchy rebuilt whenever
+// its next task belongs to another problem.  Per task, the SM clock cycles it took are
+// added to cycles[problem] (the problem's share of the launch).
+static __device__ void zero_region(char* p, int64_t bytes) {
+  float4* q = (float4*)p;
+  for (int64_t k = threadIdx.x; k < bytes / 16; k += blockDim.x) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+}
+
+// Adds the slot's weighted-adjoint accumulators into the problem's sum (FP64 atomics).
+static __device__ void flush_acc(const PdeArgs& a, char* slot) {
+  const double* acc = (const double*)(slot + a.lay.acc);
+  const int64_t cnt = (int64_t)a.n_w * a.n * a.n;
+  for (int64_t k = threadIdx.x; k < cnt; k += blockDim.x)
+    if (acc[k] != 0.0) atomicAdd(&a.acc_out[k], acc[k]);
+  __syncthreads();
+}
+
+template <bool ADJOINT>
+__global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1)
+    k_pde_batch(const PdeArgs* __restrict__ probs, const int2* __restrict__ tasks, int n_tasks, char* slots,
+                int64_t slot_bytes, int* counter, unsigned long long* cycles) {
+  constexpr bool adjoint = ADJOINT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[40];
+  __shared__ int s_idx;
+  CtaCtx c{red};
+  char* slot = slots + (int64_t)blockIdx.x * slot_bytes;
+  Hierarchy H;
+  int cur = -1;
+  for (;;) {
+    const int t = next_sample(counter, &s_idx);
+    if (t >= n_tasks) break;
+    const int2 tk = tasks[t];
+    if (tk.x != cur) {
+      if (adjoint && cur >= 0 && probs[cur].w) flush_acc(probs[cur], slot);
+      cur = tk.x;
+      const PdeArgs& a = probs[cur];
+      zero_region(slot, a.lay.bytes);
+      zero_region((char*)smem, a.lay.smem_bytes);
+      build_hierarchy(a, slot, smem, H);
     }
-    if (a.grad_out) {
-      // tmp[jx][iy] = sum_ix gx[jx][ix] lam[iy][ix]; grad[jy L + jx] = s sum_iy gy[jy][iy] tmp[jx][iy]
-      for (int jx = c.row0(); jx < L; jx += c.rowstep())
-        for (int iy = c.col0(); iy < n; iy += c.colstep()) {
-          double s = 0.0;
-          for (int ix = 1; ix < n - 1; ++ix) s += a.gx[jx * n + ix] * lam[iy * n + ix];
-          tmp[jx * n + iy] = s;
-        }
-      c.sync();
-      for (int j = threadIdx.x; j < L * L; j += blockDim.x) {
-        const int jy = j / L, jx = j % L;
-        double s = 0.0;
-        for (int iy = 1; iy < n - 1; ++iy) s += a.gy[jy * n + iy] * tmp[jx * n + iy];
-        a.grad_out[(int64_t)i * L * L + j] = a.gscale * s;
-      }
-    }
-    if (threadIdx.x == 0) {
-      if (a.solved) atomicAdd(a.solved, 1);
-      if (rr.status > a.status[i]) a.status[i] = rr.status;
-      a.iters[3 * i + 2] = rr.newton_iters;
-      a.iters[3 * i + 1] += rr.cg_iters;
-    }
-    c.sync();
+    const long long t0 = clock64();
+    if (adjoint) adjoint_task(probs[cur], c, H, slot, tk.y);
+    else state_task(probs[cur], c, H, slot, tk.y);
+    if (threadIdx.x == 0) atomicAdd(&cycles[cur], (unsigned long long)(clock64() - t0));
+  }
+  if (adjoint && cur >= 0 && probs[cur].w) flush_acc(probs[cur], slot);
+}
+
+void launch_pde_batch(const PdeArgs* probs_dev, const int2* tasks_dev, int n_tasks, char* slots, int64_t slot_bytes,
+                      int64_t smem_bytes, int nslots, int* counter, unsigned long long* cycles, bool adjoint,
+                      cudaStream_t s) {
+  if (adjoint) {
+    cudaFuncSetAttribute((const void*)k_pde_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    k_pde_batch<true><<<nslots, OUU_SOLVER_THREADS, (size_t)smem_bytes, s>>>(probs_dev, tasks_dev, n_tasks, slots,
+                                                                              slot_bytes, counter, cycles);
+  } else {
+    cudaFuncSetAttribute((const void*)k_pde_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    k_pde_batch<false><<<nslots, OUU_SOLVER_THREADS, (size_t)smem_bytes, s>>>(probs_dev, tasks_dev, n_tasks, slots,
+                                                                               slot_bytes, counter, cycles);
   }
 }
 
@@ -218,6 +297,15 @@ __global__ void k_sources_transpose_apply(int n, int L, const double* gx, const 
     for (int iy = 0; iy < n; ++iy) a += gy[jy * n + iy] * tmp[jx * n + iy];
     grad[(int64_t)r * L * L + j] = gscale * a;
   }
+}
+
+void launch_sources_transpose(int n, int L, int n_w, const double* gx, const double* gy, double gscale,
+                              const double* s, double* grad, cudaStream_t st) {
+  const size_t sm = (size_t)L * n * sizeof(double);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute((const void*)k_sources_transpose_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+  k_sources_transpose_apply<<<n_w, 256, sm, st>>>(n, L, gx, gy, gscale, s, grad);
 }
 
 void launch_reduce_slots_and_gradient(const char* slots, const SlotLayout& lay, int nslots, int n, int L, int n_w,

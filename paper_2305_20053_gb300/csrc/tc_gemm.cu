@@ -12,6 +12,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "tc_gemm.cuh"
 #include "tc_ptx.cuh"
@@ -403,6 +406,29 @@ static ouu_status launch_bn(const CUtensorMap& ta, const __nv_bfloat16* B, int l
   return OUU_OK;
 }
 
+static ouu_status launch_by_bn(int bn, const CUtensorMap& ta, const __nv_bfloat16* B, int ldb, int M, int N, int K,
+                               const EpiParams& e2, int* err, cudaStream_t s, int splits) {
+  switch (bn) {
+    case 256: return launch_bn<256>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    case 208: return launch_bn<208>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    case 128: return launch_bn<128>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    case 112: return launch_bn<112>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    case 80: return launch_bn<80>(ta, B, ldb, M, N, K, e2, err, s, splits);
+    default: return launch_bn<64>(ta, B, ldb, M, N, K, e2, err, s, splits);
+  }
+}
+
+// Autotuner state: the measured best N tile per (M, N, K, epilogue mode, split) shape.
+struct GemmKey {
+  int M, N, K, mode, splits;
+  bool operator<(const GemmKey& o) const {
+    return std::tie(M, N, K, mode, splits) < std::tie(o.M, o.N, o.K, o.mode, o.splits);
+  }
+};
+static std::map<GemmKey, int> g_tuned;
+static std::mutex g_tune_mu;
+static int g_autotune = 0;
+
 ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                          const EpiParams& ep, int* err, cudaStream_t s, int splits) {
   OUU_CHECK_ARG(M >= 1 && N >= 1 && K >= 1, "GEMM sizes must be positive");
@@ -429,6 +455,44 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
     ouu_set_error("tensor map for GEMM operand A failed (alignment or driver entry point)");
     return OUU_ERR_INVALID_ARG;
   }
+  // Autotuned tile for this shape, if the tuner has timed it (see ouu_gemm_set_autotune).
+  const GemmKey key{M, N, K, ep.mode, splits};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return launch_by_bn(it->second, ta, B, ldb, M, N, K, e2, err, s, splits);
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  // Timing runs would add into outputs that accumulate (accumulate flag, split-K atomics).
+  if (g_autotune && cap == cudaStreamCaptureStatusNone && !ep.accumulate && splits == 1) {
+    int best_bn = 0;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int bn : {256, 208, 128, 112, 80, 64}) {
+      if (ep.mode == EPI_QOI && bn < N) continue;
+      if (launch_by_bn(bn, ta, B, ldb, M, N, K, e2, err, s, splits) != OUU_OK) continue;   // warm-up
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3; ++r) launch_by_bn(bn, ta, B, ldb, M, N, K, e2, err, s, splits);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_bn = bn;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_bn) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned[key] = best_bn;
+      return launch_by_bn(best_bn, ta, B, ldb, M, N, K, e2, err, s, splits);
+    }
+  }
   // N tile: a CTA's time is mostly fixed latency (TMA round trips, MMA commit, epilogue)
   // plus a part that grows with BN, and tiles beyond one per SM run in a further wave;
   // pick the tile that minimises waves x (BN + 64) (ties: the wider tile).
@@ -452,14 +516,14 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
       best = bn;
     }
   }
-  switch (best) {
-    case 256: return launch_bn<256>(ta, B, ldb, M, N, K, e2, err, s, splits);
-    case 208: return launch_bn<208>(ta, B, ldb, M, N, K, e2, err, s, splits);
-    case 128: return launch_bn<128>(ta, B, ldb, M, N, K, e2, err, s, splits);
-    case 112: return launch_bn<112>(ta, B, ldb, M, N, K, e2, err, s, splits);
-    case 80: return launch_bn<80>(ta, B, ldb, M, N, K, e2, err, s, splits);
-    default: return launch_bn<64>(ta, B, ldb, M, N, K, e2, err, s, splits);
-  }
+  return launch_by_bn(best, ta, B, ldb, M, N, K, e2, err, s, splits);
+}
+
+void ouu_gemm_set_autotune(int on) { g_autotune = on; }
+
+int ouu_gemm_tuned_count() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tuned.size();
 }
 
 // Kernel-level entry used by the GEMM numerics test (declared in include/ouu_kernels.h).
@@ -514,3 +578,5 @@ extern "C" ouu_status ouu_kernel_gemm_qoi_bf16(const void* A, int lda, const voi
   return ouu_gemm_bf16((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)B, ldb, M, N, K, ep, err_dev,
                        (cudaStream_t)stream, 1);
 }
+
+extern "C" int ouu_kernel_gemm_tuned_shapes(void) { return ouu_gemm_tuned_count(); }

@@ -58,3 +58,10 @@ bool ouu_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, uint32_t esize, const
 // CTAs accumulate atomically and which must be zeroed beforehand.
 ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                          const EpiParams& ep, int* err, cudaStream_t s, int splits = 1);
+
+// Autotuning of the N tile: while on, the first call of each (M, N, K, mode, split) shape
+// outside stream capture times every candidate tile (a warm-up and three timed launches,
+// CUDA events on the call's stream) and keeps the fastest for all later calls of that shape.
+// Shapes whose outputs accumulate (accumulate flag, split-K) are not tuned.
+void ouu_gemm_set_autotune(int on);
+int ouu_gemm_tuned_count();
