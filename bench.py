@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--epochs", type=int, default=600)
     ap.add_argument("--lr-final", type=float, default=1e-5,
                     help="geometric decay of the second half's rate down to this (0: keep 2.5e-4)")
+    ap.add_argument("--batch", action="store_true",
+                    help="the uneven batch: 64 problems (grids 65/129/257, N 256-8192 log-uniform, d_Z 25-400), "
+                         "half MR-DINO where a network for (n, d_Z) exists, one CUDA graph; per-problem and "
+                         "aggregate evals/s")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -462,9 +466,77 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """64 seeded problems evaluated together (ouu_batch_*): plain problems in the two
+    persistent launches, MR-DINO problems (those drawn as DINO whose (n, d_Z) has a network:
+    129 x 129 with 100 controls, trained here with a short recipe) on graph branches."""
+    import torch
+    from paper_2305_20053_gb300 import capi
+    from paper_2305_20053_gb300 import train as T
+    from synthetic_inputs import SEED_EVAL_Z, SEED_SAA, controls
+    torch.cuda.set_device(0)
+    capi.load()
+    rng = np.random.Generator(np.random.PCG64(20535))   # seeded problem table
+    grids = rng.choice([65, 129, 257], size=64)
+    Ns = np.round(np.exp(rng.uniform(np.log(256), np.log(8192), size=64))).astype(int)
+    lat = rng.choice([5, 7, 10, 14, 20], size=64)
+    want_dino = rng.uniform(size=64) < 0.5
+    risks = [capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.95, eps=1e-4, t_optimal=1),
+             capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0)]
+    # the one network: 129 x 129, d_Z = 100
+    nets = {}
+    if any(want_dino[k] and grids[k] == 129 and lat[k] == 10 for k in range(64)):
+        Pt = capi.Problem(n=129, lattice_L=10, max_samples=4096)
+        D = T.make_dino(129, 10, max_eval=8192)
+        T.init_params(D)
+        data = T.generate_training_data(Pt, D, 4096)
+        T.train(D, data, epochs=100, lr_final=1e-5)
+        del data
+        nets[(129, 10)] = D
+    items, keep = [], []
+    for k in range(64):
+        n, L, N = int(grids[k]), int(lat[k]), int(Ns[k])
+        P = capi.Problem(n=n, lattice_L=L, max_samples=N)
+        m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
+        P.ouu_sample_fields(SEED_SAA, 10000 * k, N, m)
+        D = nets.get((n, L)) if want_dino[k] else None
+        if D is not None and any(it["dino"] is D for it in items):   # one network serves one item at a time
+            D = None
+        items.append(dict(problem=P, backend=capi.BACKEND_DINO if D is not None else capi.BACKEND_PDE, dino=D,
+                          m=m, n=N, risks=risks))
+        keep.append((P, m))
+    t0 = time.perf_counter()
+    B = capi.Batch(items, autotune=True)
+    zs = [controls(SEED_EVAL_Z, 1 + k, int(lat[k]) ** 2)[k] for k in range(64)]
+    B.run(zs)                                     # capture + first replay
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    steps = max(1, args.steps if args.steps != 20 else 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        res, item_ms, total_ms = B.run(zs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    per = [{"n": int(grids[k]), "N": int(Ns[k]), "d_z": int(lat[k]) ** 2,
+            "backend": "dino" if items[k]["backend"] == capi.BACKEND_DINO else "pde",
+            "evals_per_s_equiv": 1000.0 / item_ms[k] if item_ms[k] > 0 else None} for k in range(64)]
+    line = {"metric": "uneven batch: 64 OUU problems per graph replay", "value": 64 * 1000.0 / ms,
+            "unit": "problem-evals/s", "batch_evals_per_s": 1000.0 / ms, "ms_per_batch": ms,
+            "device_ms": total_ms, "steps": steps, "setup_s": setup_s,
+            "n_dino": sum(1 for it in items if it["backend"] == capi.BACKEND_DINO),
+            "samples_total": int(Ns.sum()), "per_problem": per,
+            "note": "per-problem evals/s: MR-DINO its graph branch; plain its share of the persistent launches"}
+    print(json.dumps(line), flush=True)
+    B.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.batch:
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

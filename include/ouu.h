@@ -300,8 +300,9 @@ int ouu_problem_slots(ouu_problem_t p);
  * with the GEMM tile autotuner on (each network layer shape gets the fastest measured
  * tile width).
  *
- * Each item names its own problem handle (items must not share one; the handle's arena
- * holds the item's results), its fields m_dev [n_samples][n][n] (device, caller-owned,
+ * Each item names its own problem handle and, for MR-DINO, its own network (items must
+ * not share either: the handle's arena holds the item's results, the network's buffers
+ * its evaluation), its fields m_dev [n_samples][n][n] (device, caller-owned,
  * unchanged between runs) and 1..4 risk descriptors; MR-DINO items name a network built
  * for the same grid and controls with max_eval >= n_samples.  The batch runs on the
  * stream of the first item's problem. */

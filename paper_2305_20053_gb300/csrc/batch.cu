@@ -122,7 +122,12 @@ extern "C" ouu_status ouu_batch_create(const ouu_batch_item* items, int n_items,
   *out = nullptr;
   for (int k = 0; k < n_items; ++k) {
     if (ouu_status st = check_item(items[k])) return st;
-    for (int j = 0; j < k; ++j) OUU_CHECK_ARG(items[j].problem != items[k].problem, "batch items must not share a problem");
+    for (int j = 0; j < k; ++j) {
+      OUU_CHECK_ARG(items[j].problem != items[k].problem, "batch items must not share a problem");
+      OUU_CHECK_ARG(items[k].backend != OUU_BACKEND_DINO || items[j].backend != OUU_BACKEND_DINO ||
+                        items[j].dino != items[k].dino,
+                    "batch items must not share a network (concurrent branches would share its buffers)");
+    }
   }
   ouu_batch* b = new ouu_batch();
   b->stream = items[0].problem->stream;
@@ -196,7 +201,9 @@ extern "C" ouu_status ouu_batch_create(const ouu_batch_item* items, int n_items,
     }
     b->slot_bytes = (b->slot_bytes + 255) / 256 * 256;
     b->n_tasks = (int)tasks.size();
-    b->nslots = std::max(1, std::min(sms, b->n_tasks));
+    // the persistent launch holds its SMs until it ends: leave some to the MR-DINO branches
+    const int reserve = b->dino.empty() ? 0 : std::min(16, sms / 4);
+    b->nslots = std::max(1, std::min(sms - reserve, b->n_tasks));
     BATCH_CUDA(cudaMalloc((void**)&b->d_args, sizeof(PdeArgs) * args.size()));
     BATCH_CUDA(cudaMemcpy(b->d_args, args.data(), sizeof(PdeArgs) * args.size(), cudaMemcpyHostToDevice));
     BATCH_CUDA(cudaMalloc((void**)&b->d_tasks, sizeof(int2) * tasks.size()));

@@ -450,7 +450,10 @@ __device__ NewtonResult newton_solve(const C& c, Hierarchy& H, double rr, const 
 }
 
 // Adjoint (or any linear) solve J(u) lam = b by FP32 MG-PCG inside FP64 iterative
-// refinement: lam += J^-1 (b - J lam) until ||b - J lam|| <= rtol ||b||.
+// refinement: lam += J^-1 (b - J lam) until ||b - J lam|| <= rtol ||b||, or, once below
+// 1e-9 ||b||, until a refinement step no longer halves the residual: the FP64 residual
+// has then reached its rounding floor (eps times the stencil terms, which on fine grids
+// and high-contrast fields exceeds 1e-12 ||b||).
 // lam's interior must be zero on entry.  J's levels must already be set up for u.
 template <class C>
 __device__ NewtonResult refine_solve(const C& c, Hierarchy& H, double rr, const double* E,
@@ -469,14 +472,17 @@ __device__ NewtonResult refine_solve(const C& c, Hierarchy& H, double rr, const 
     return res;
   }
   if (!(bnorm > 0.0)) return res;
+  double prev = INFINITY;
   for (int it = 0;; ++it) {
     if (!(rn == rn) || isinf(rn)) { res.status = 2; break; }
     if (rn <= rtol * bnorm) break;
+    if (rn <= 1e-9 * bnorm && rn > 0.5 * prev) break;   // rounding floor
     if (it >= maxit) { res.status = 1; break; }
     CgResult cg = pcg_solve(c, H, x, p, q, rn, cg_rtol, cg_maxit);
     res.cg_iters += cg.iters;
     axpy_interior(c, n, cg.scale, x, lam);
     c.sync();
+    prev = rn;
     rn = sqrt(linear_residual(c, n, ih2, rr, E, u, b, lam, L0.b));
     c.sync();
     res.newton_iters = it + 1;
