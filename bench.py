@@ -374,11 +374,16 @@ def run_ours(args):
                         N * n * n * 8 + R_M * nnp * 2 + N * R_M * 4, ph["ms_project"]),
             "network": ("k_gemm_bf16 x 8 (MLP forward + reverse-mode gradient)", "tensor", flops_net, ph["ms_network"]),
         }
-        name, bound, work, kms = max(kern.values(), key=lambda x: x[3])
+        # DRAM bytes per launch from the committed ncu capture of the same kernel
+        # (profiles/kl_project_129x129_N1024_ncu.md: N = 1024, scaled by the 4x samples)
+        traffic = {"project": 4 * (148.111872e6 + 3.392512e6)}
+        key = max(kern, key=lambda k: kern[k][3])
+        name, bound, work, kms = kern[key]
         achieved = work / (kms / 1000.0) / (1e9 if bound == "hbm" else 1e12)
         peak = hbm if bound == "hbm" else tc
         roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak,
-                "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic.get(key), "algorithmic_bytes": work if bound == "hbm" else None,
                 "peak_source": f"{src} (burst)",
                 "phases": {k: {"kernel": v[0], "bound": v[1], "ms": v[3],
                                "achieved": v[2] / (v[3] / 1000.0) / (1e9 if v[1] == "hbm" else 1e12)}
