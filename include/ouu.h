@@ -277,6 +277,14 @@ ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_samples, const
  * enqueues its kernels eagerly and reports per-phase times in ouu_eval_stats). */
 ouu_status ouu_dino_set_graphs(ouu_dino_t d, int enable);
 
+/* The evaluation network with a gradient (projection output -> forward layers -> reduced QoI
+ * -> reverse-mode z-gradient) runs as one fused tensor-core kernel per 128-sample tile when
+ * the network fits it (width, r_U, d_Z <= 416, r_M + d_Z <= 448); enable = 0 selects the
+ * per-layer GEMM kernels instead (same arithmetic).  Default 0: one CTA per 128 samples
+ * leaves the GELU epilogues of a layer to one SM, which at thousands of samples is slower
+ * than the per-layer kernels; ouu_batch_create with autotune picks per network by timing. */
+ouu_status ouu_dino_set_fused_network(ouu_dino_t d, int enable);
+
 /* Thread-local message of the last failed call ("" if none).  Copies at most
  * len-1 bytes plus a terminating zero into buf; returns the full length. */
 size_t ouu_last_error(char* buf, size_t len);
@@ -296,9 +304,9 @@ int ouu_problem_slots(ouu_problem_t p);
  *     problem's risk weights, then the adjoint solves in one persistent launch, then each
  *     problem's G^T sum;
  *   - each MR-DINO problem's evaluation on a concurrent branch of the graph.
- * With autotune != 0, ouu_batch_create first runs every MR-DINO problem once eagerly
- * with the GEMM tile autotuner on (each network layer shape gets the fastest measured
- * tile width).
+ * With autotune != 0, ouu_batch_create times every MR-DINO problem's evaluation with the
+ * per-layer GEMM kernels (their N tiles tuned per layer shape by measurement) and with the
+ * one-kernel network, and keeps the faster for that network (ouu_dino_set_fused_network).
  *
  * Each item names its own problem handle and, for MR-DINO, its own network (items must
  * not share either: the handle's arena holds the item's results, the network's buffers

@@ -97,6 +97,7 @@ SIGNATURES = {
     "ouu_dino_loss_grad": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(ctypes.c_float), _dp]),
     "ouu_dino_eval": (_i, [_vp, _vp, _i, _dp, _vp, _vp, _vp, _vp]),
     "ouu_dino_set_graphs": (_i, [_vp, _i]),
+    "ouu_dino_set_fused_network": (_i, [_vp, _i]),
     "ouu_kernel_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _i, _i, _vp, _i, _i,
                                   _vp, _i, _vp, _i, _vp, _i, _vp, _vp]),
     "ouu_kernel_kl_project": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _vp]),
@@ -369,6 +370,9 @@ class Dino:
         s = np.zeros(self.desc.r_u, dtype=np.float32)
         check(load().ouu_dino_get_output_scale(self.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
         return s
+
+    def ouu_dino_set_fused_network(self, enable):
+        check(load().ouu_dino_set_fused_network(self.handle, 1 if enable else 0))
 
     def ouu_dino_set_graphs(self, enable):
         check(load().ouu_dino_set_graphs(self.handle, int(enable)))

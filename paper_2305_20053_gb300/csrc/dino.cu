@@ -786,6 +786,12 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
   for (int j = 0; j < dz; ++j) zh[j] = (float)z_host[j];
   OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)dz * 4, cudaMemcpyHostToDevice, d->stream));
   DINO_TRY(project_fields(d, m_dev, N, d->XIe, true));
+  if (want_grad && d->fused_mlp && mlp_fused_fits(d)) {   // the whole network in one kernel
+    DINO_TRY(mlp_fused_eval(d, N));
+    if (!d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[3], d->stream));
+    OUU_CUDA_TRY(cudaGetLastError());
+    return OUU_OK;
+  }
   OUU_CUDA_TRY(launch_pdl(k_build_x0, dim3(grid_for((int64_t)N * (in0p / 4))), dim3(256), 0, d->stream,
                           (const float*)d->XIe, (const int*)nullptr, (const float*)d->d_zf, (int64_t)0, d->rm, dz, in0p,
                           N, d->X0e, (__nv_bfloat16*)nullptr));
@@ -880,6 +886,16 @@ extern "C" ouu_status ouu_dino_get_output_scale(ouu_dino_t d, float* s_host) {
   OUU_CHECK_ARG(d && s_host, "null argument");
   OUU_CUDA_TRY(cudaMemcpyAsync(s_host, d->d_oscale, (size_t)d->ru * 4, cudaMemcpyDeviceToHost, d->stream));
   OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_set_fused_network(ouu_dino_t d, int enable) {
+  OUU_CHECK_ARG(d != nullptr, "null argument");
+  d->fused_mlp = enable ? 1 : 0;
+  if (d->gexec) {   // a captured evaluation holds the other path's kernels
+    cudaGraphExecDestroy(d->gexec);
+    d->gexec = nullptr;
+  }
   return OUU_OK;
 }
 

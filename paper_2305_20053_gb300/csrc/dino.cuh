@@ -68,11 +68,18 @@ struct ouu_dino {
   const double* gkey_m = nullptr;
   int gkey_N = 0, gkey_nr = 0;
   int use_graphs = 1;
+  int fused_mlp = 0;               // evaluation network in one kernel (mlp_fused.cu) when it fits
   bool capturing = false;
 };
 
 // DINO forward/backward pieces used by the C ABI (dino.cu).
 ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad);
+
+// The evaluation network in one fused kernel per 128-sample tile (mlp_fused.cu): layer-0
+// input from XIe and d_zf, forward with GELU (gelu' to Ae), reduced QoI (Qe, OUTe), reverse
+// mode to GQe.  mlp_fused_fits: the handle's sizes fit the kernel (width, r_u, d_Z <= 416).
+bool mlp_fused_fits(const ouu_dino* d);
+ouu_status mlp_fused_eval(ouu_dino* d, int N);
 
 // The whole MR-DINO risk evaluation enqueued on d->stream (capi.cu); the problem's risk
 // descriptors must be in p->d_risks.

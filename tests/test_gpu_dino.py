@@ -260,3 +260,31 @@ def test_graph_replay_matches_eager(setup):
     for (v0, g0), (v1, g1) in zip(eager, graphed):
         np.testing.assert_array_equal(v0, v1)
         np.testing.assert_allclose(g1, g0, rtol=1e-12, atol=1e-15 * np.abs(g0).max())
+
+
+def test_fused_network_matches_layer_kernels(setup):
+    """The one-kernel evaluation network gives the per-layer GEMM path's results (the same BF16
+    roundings and K order; only FP32 sums of the QoI and the FP64 risk reductions may differ)."""
+    from paper_2305_20053_gb300 import capi
+    D, P, n, N = setup["D"], setup["P"], N_GRID, 40
+    m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
+    P.ouu_sample_fields(SEED_SAA, 0, N, m)
+    z = controls(SEED_EVAL_Z, 1, DZ)[0]
+    out = {}
+    for fused in (1, 0):
+        D.ouu_dino_set_fused_network(fused)
+        q = torch.empty(N, dtype=torch.float64, device="cuda")
+        gq = torch.empty(N, DZ, dtype=torch.float64, device="cuda")
+        phi = torch.empty(N, RU, dtype=torch.float32, device="cuda")
+        D.ouu_dino_eval(m, N, z, phi, None, q, gq)
+        risks = [capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0),
+                 capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.9, eps=1e-4, t_optimal=1)]
+        v, g, _, _, _ = P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)
+        out[fused] = (q.cpu().numpy(), gq.cpu().numpy(), phi.cpu().numpy(), v, g)
+    D.ouu_dino_set_fused_network(0)
+    (q1, g1, p1, v1, r1), (q0, g0, p0, v0, r0) = out[1], out[0]
+    np.testing.assert_allclose(p1, p0, rtol=1e-5, atol=1e-6 * np.abs(p0).max())
+    np.testing.assert_allclose(q1, q0, rtol=1e-5)
+    assert rel(g1, g0) <= 1e-5
+    np.testing.assert_allclose(v1, v0, rtol=1e-5)
+    assert rel(r1, r0) <= 1e-5
