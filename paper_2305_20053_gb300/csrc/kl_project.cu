@@ -3,18 +3,22 @@
 // reading the FP64 fields once.  One persistent CTA per SM; the (128-sample tile, 64-wide
 // K block) units are dealt to the CTAs in equal contiguous ranges ("stream-K"), so every
 // SM streams the same number of bytes whatever N and n^2 are.  Per CTA:
-//   warp 16      : producer.  Per K block, TMA loads of the FP64 slice m[tile rows][k0, k0+64)
-//                  and of the BF16 basis block W[0, BN) x [k0, k0 + 64) (128-byte swizzle).
-//                  With n^2 odd the row stride n^2 * 8 bytes is not a multiple of 16, which
-//                  a tensor map needs; the fields are then read as rows of sample PAIRS
-//                  (stride 2 n^2 * 8 bytes), even samples from x = k0 and odd samples from
-//                  x = n^2 + k0 - 1 (one element early, so that x stays 16-byte aligned),
-//                  66 elements each: two copies per K block.  A last unpaired sample (N odd),
-//                  and every sample when the base is not 16-byte aligned, is read with plain
-//                  loads.
-//   warps 0..15  : converters.  FP64 -> BF16 (round to FP32, then to BF16, both to nearest
-//                  even; the first step in integer arithmetic, as the FP64 pipe is narrow)
-//                  written straight into the swizzled K-major A tile that tcgen05.mma reads.
+//   warp 16      : field producer.  Per K block, TMA loads of the FP64 slice
+//                  m[tile rows][k0, k0+64).  With n^2 odd the row stride n^2 * 8 bytes is
+//                  not a multiple of 16, which a tensor map needs; the fields are then read
+//                  as rows of sample PAIRS (stride 2 n^2 * 8 bytes), even samples from
+//                  x = k0 and odd samples from x = n^2 + k0 - 1 (one element early, so that
+//                  x stays 16-byte aligned), 66 elements each: two copies per K block.  A
+//                  last unpaired sample (N odd), and every sample when the base is not
+//                  16-byte aligned, is read with plain loads.
+//   warp 22      : basis producer.  TMA loads of the BF16 basis block W[0, BN) x [k0, k0+64)
+//                  (128-byte swizzle), paced by the MMA instead of by the field copies.
+//   warps 0..15  : converters.  Each copies its 8 rows of the FP64 stage into registers and
+//                  releases the stage at once (the next field copy then overlaps the
+//                  arithmetic), then converts FP64 -> BF16 (round to FP32, then to BF16,
+//                  both to nearest even; the first step in integer arithmetic, as the FP64
+//                  pipe is narrow) straight into the swizzled K-major A tile that
+//                  tcgen05.mma reads.
 //   warp 17      : tcgen05.mma issuer (M = 128, N = BN, K = 16 per instruction) into one of
 //                  two TMEM accumulators; allocates and frees the tensor memory.
 //   warps 18..21 : epilogue.  TMEM -> registers, + bias on the unit range that holds K block
@@ -32,7 +36,8 @@
 #define KLP_PROD_WARP 16
 #define KLP_MMA_WARP 17
 #define KLP_EPI_WARP0 18
-#define KLP_THREADS (22 * 32)
+#define KLP_BPROD_WARP 22
+#define KLP_THREADS (23 * 32)
 #define KLP_ROWS_PER_WARP (128 / KLP_CONV_WARPS)
 #define KLP_ROW_BYTES 528                    // pair mode: 66 doubles per sample row
 #define KLP_F64_STAGE (128 * KLP_ROW_BYTES)
@@ -61,9 +66,37 @@ static __device__ __forceinline__ float f64_to_f32_slow(uint32_t hi, uint32_t lo
   return __uint_as_float(sign);   // below the normal FP32 range
 }
 
-// True when x rounds into FP32's normal range by the fast path below (exponent in [897, 1150]).
-static __device__ __forceinline__ bool f32_normal(double x) {
-  return ((((uint32_t)__double2hiint(x) >> 20) & 0x7FFu) - 897u) <= 253u;
+// (biased FP64 exponent - 897) << 20, wrapping below 897: under KLP_EXP_SPAN exactly when x
+// rounds into FP32's normal range by the fast path below (exponent in [897, 1150]).  The
+// maximum over many values tests them all with one comparison.
+#define KLP_EXP_SPAN (254u << 20)
+static __device__ __forceinline__ uint32_t f32_exp_offset(double x) {
+  return ((uint32_t)__double2hiint(x) & 0x7FF00000u) - (897u << 20);
+}
+
+// Lane l's two values of one row of the FP64 stage: columns 2l and 2l + 1 of the K block.
+// Row mode: rows of 512 bytes.  Pair mode: even samples in the first half, odd samples in
+// the second, rows of 528 bytes; an odd sample's row starts one element early, so its
+// 16-byte pair holds columns (2l - 1, 2l) and column 2l + 1 comes from the next lane (lane
+// 31 reads column 63 itself, a broadcast load).
+static __device__ __forceinline__ void stage_row(const uint8_t* fst, int pair, int rr, int lane, double& x0,
+                                                 double& x1) {
+  if (!pair) {
+    const double2 v = reinterpret_cast<const double2*>(fst + rr * 512)[lane];
+    x0 = v.x;
+    x1 = v.y;
+  } else if (!(rr & 1)) {
+    const double2 v = reinterpret_cast<const double2*>(fst + (rr >> 1) * KLP_ROW_BYTES)[lane];
+    x0 = v.x;
+    x1 = v.y;
+  } else {
+    const uint8_t* row = fst + KLP_HALF + (rr >> 1) * KLP_ROW_BYTES;
+    const double2 v = reinterpret_cast<const double2*>(row)[lane];
+    const double c63 = reinterpret_cast<const double*>(row)[64];
+    const double nx = __shfl_down_sync(0xffffffffu, v.x, 1);
+    x0 = v.y;
+    x1 = lane == 31 ? c63 : nx;
+  }
 }
 
 // The fast path on its own: rounding the 64-bit pattern to nearest even at bit 29 carries
@@ -112,6 +145,9 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
   const long long u1 = (long long)(blockIdx.x + 1) * a.U / gridDim.x;
   const int nj = (int)(u1 - u0);
   const int nn = a.nn, KBt = a.KBt, N = a.N;
+  // unit u0 + j is (tile t, K block kb); every role steps (t, kb) along with j instead of
+  // dividing
+  const int t_first = (int)(u0 / KBt), kb_first = (int)(u0 % KBt);
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -136,16 +172,15 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
   const uint32_t tmem = *tslot;
 
   if (warp == KLP_PROD_WARP) {
-    // ---------------------------------------------------------------- producer
-    int issued = 0;
-    bool ok = true;
+    // ---------------------------------------------------------------- field producer
     if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
       const uint32_t fbytes = a.pair ? 2u * KLP_HALF : 128u * 512u;
-      for (int j = 0; j < nj; ++j) {
-        const long long u = u0 + j;
-        const int t = (int)(u / KBt), k0 = (int)(u % KBt) * 64, s = j & 1;
+      for (int j = 0, t = t_first, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1, t += kb == 0) {
+        const int k0 = kb * 64, s = j & 1;
         const uint32_t ph = (uint32_t)(j >> 1) & 1u;
-        if (j >= 2 && !(mbar_wait(&f64_empty[s], ph ^ 1u) && mbar_wait(&ab_empty[s], ph ^ 1u))) {
+        if (j >= 2 && !mbar_wait(&f64_empty[s], ph ^ 1u)) {
           ok = false;
           break;
         }
@@ -160,82 +195,108 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
           mbar_expect_tx(&f64_full[s], fbytes);
           tma_load_2d(dst, &tm, k0, t * 128, &f64_full[s]);
         }
+        issued = j + 1;
+      }
+      if (!ok) s_fail = 1;
+      // drain: the copies into both stages must have landed before the CTA exits
+      for (int j = max(0, issued - 2); j < issued; ++j)
+        if (!mbar_wait(&f64_full[j & 1], (uint32_t)(j >> 1) & 1u)) s_fail = 1;
+    }
+  } else if (warp == KLP_BPROD_WARP) {
+    // ---------------------------------------------------------------- basis producer
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int j = 0, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1) {
+        const int k0 = kb * 64, s = j & 1;
+        const uint32_t ph = (uint32_t)(j >> 1) & 1u;
+        if (j >= 2 && !mbar_wait(&ab_empty[s], ph ^ 1u)) {
+          ok = false;
+          break;
+        }
         mbar_expect_tx(&b_full[s], B_BYTES);
         tma_load_2d(sB + s * B_BYTES, &tw, k0, 0, &b_full[s]);
         issued = j + 1;
       }
       if (!ok) s_fail = 1;
-      // drain: the copies into both stages must have landed before the CTA exits
-      for (int j = max(0, issued - 2); j < issued; ++j) {
-        const uint32_t ph = (uint32_t)(j >> 1) & 1u;
-        if (!mbar_wait(&f64_full[j & 1], ph) || !mbar_wait(&b_full[j & 1], ph)) s_fail = 1;
-      }
+      for (int j = max(0, issued - 2); j < issued; ++j)
+        if (!mbar_wait(&b_full[j & 1], (uint32_t)(j >> 1) & 1u)) s_fail = 1;
     }
   } else if (warp < KLP_CONV_WARPS) {
     // ---------------------------------------------------------------- converters
+    // Lane l owns columns 2l and 2l + 1 of the warp's 8 rows: one 16-byte shared load per
+    // row, and its two BF16 values form one 32-bit word of the A tile.
     const int r0 = warp * KLP_ROWS_PER_WARP;
-    for (int j = 0; j < nj; ++j) {
-      const long long u = u0 + j;
-      const int t = (int)(u / KBt), kb = (int)(u % KBt), k0 = kb * 64, s = j & 1;
+    for (int j = 0, t = t_first, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1, t += kb == 0) {
+      const int k0 = kb * 64, s = j & 1;
       const uint32_t ph = (uint32_t)(j >> 1) & 1u;
-      bool ok = mbar_wait(&f64_full[s], ph);
-      if (ok && j >= 2) ok = mbar_wait(&ab_empty[s], ph ^ 1u);
-      if (!__all_sync(0xffffffffu, ok ? 1 : 0)) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&f64_full[s], ph) ? 1 : 0)) {
         if (lane == 0) s_fail = 1;
         break;
       }
       const uint8_t* fst = sF + s * KLP_F64_STAGE;
-      uint8_t* ast = sA + s * KLP_A_STAGE;
-      const bool c0ok = k0 + lane < nn, c1ok = k0 + 32 + lane < nn;
+      const int rb = t * 128 + r0;   // the warp's first sample
+      double x0[KLP_ROWS_PER_WARP], x1[KLP_ROWS_PER_WARP];
+      if (rb + KLP_ROWS_PER_WARP <= a.n_tma) {
 #pragma unroll
-      for (int i = 0; i < KLP_ROWS_PER_WARP; ++i) {
-        const int rr = r0 + i, r = t * 128 + rr;   // r0 is a multiple of 8: rr & 7 == i
-        float fa = 0.f, fb = 0.f;
-        if (r < N) {
-          double x0 = 0.0, x1 = 0.0;
+        for (int i = 0; i < KLP_ROWS_PER_WARP; ++i) stage_row(fst, a.pair, r0 + i, lane, x0[i], x1[i]);
+      } else {   // the tile's end: rows by plain loads (r >= n_tma) or zero rows (r >= N)
+#pragma unroll
+        for (int i = 0; i < KLP_ROWS_PER_WARP; ++i) {
+          const int r = rb + i, c = k0 + 2 * lane;
+          x0[i] = 0.0;
+          x1[i] = 0.0;
           if (r < a.n_tma) {
-            const double* sp = a.pair ? (const double*)(fst + (i & 1) * KLP_HALF + (rr >> 1) * KLP_ROW_BYTES) + (i & 1)
-                                      : (const double*)(fst + rr * 512);
-            x0 = sp[lane];
-            x1 = sp[lane + 32];
-          } else {
-            const double* row = a.m + (size_t)r * nn + k0;
-            if (c0ok) x0 = row[lane];
-            if (c1ok) x1 = row[lane + 32];
-          }
-          if (__all_sync(0xffffffffu, f32_normal(x0) && f32_normal(x1))) {
-            fa = f64_to_f32_fast(x0);
-            fb = f64_to_f32_fast(x1);
-          } else {   // zeros past the last column, or values outside FP32's normal range
-            fa = c0ok ? f64_to_f32_rne(x0) : 0.f;
-            fb = c1ok ? f64_to_f32_rne(x1) : 0.f;
+            stage_row(fst, a.pair, r0 + i, lane, x0[i], x1[i]);
+          } else if (r < N) {
+            const double* row = a.m + (size_t)r * nn;
+            if (c < nn) x0[i] = row[c];
+            if (c + 1 < nn) x1[i] = row[c + 1];
           }
         }
-        // w = bf16(column l) | bf16(column 32 + l) << 16; lane l then writes the word of
-        // columns (2l, 2l + 1), taken from lanes 2 (l mod 16) and 2 (l mod 16) + 1
-        const __nv_bfloat162 pk = __floats2bfloat162_rn(fa, fb);
-        const uint32_t w = *reinterpret_cast<const uint32_t*>(&pk);
-        const int sl = 2 * (lane & 15);
-        const uint32_t xa = __shfl_sync(0xffffffffu, w, sl), xb = __shfl_sync(0xffffffffu, w, sl + 1);
-        const uint32_t word = __byte_perm(xa, xb, lane < 16 ? 0x5410u : 0x7632u);
-        // 128-byte swizzle: 16-byte chunk index XOR (row mod 8) within the 8-row atom
-        *(uint32_t*)(ast + rr * 128 + ((((uint32_t)lane >> 2) ^ (uint32_t)i) << 4) + ((lane & 3) << 2)) = word;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&f64_empty[s]);   // the stage is in registers: refill it
+      if (j >= 2 && !__all_sync(0xffffffffu, mbar_wait(&ab_empty[s], ph ^ 1u) ? 1 : 0)) {
+        if (lane == 0) s_fail = 1;
+        break;
+      }
+      uint8_t* ast = sA + s * KLP_A_STAGE;
+      // 128-byte swizzle: 16-byte chunk index XOR (row mod 8) within the 8-row atom;
+      // r0 is a multiple of 8, so row r0 + i has (row mod 8) = i
+      uint8_t* wp = ast + r0 * 128 + ((lane & 3) << 2);
+      const uint32_t ch = (uint32_t)lane >> 2;
+      uint32_t emax = 0;
+#pragma unroll
+      for (int i = 0; i < KLP_ROWS_PER_WARP; ++i) emax = max(emax, max(f32_exp_offset(x0[i]), f32_exp_offset(x1[i])));
+      // the last K block (columns past n^2 zeroed) and values outside FP32's normal range
+      // take the general rounding
+      if (__all_sync(0xffffffffu, emax < KLP_EXP_SPAN) && k0 + 64 <= nn) {
+#pragma unroll
+        for (int i = 0; i < KLP_ROWS_PER_WARP; ++i) {
+          const __nv_bfloat162 pk = __floats2bfloat162_rn(f64_to_f32_fast(x0[i]), f64_to_f32_fast(x1[i]));
+          *(uint32_t*)(wp + i * 128 + ((ch ^ (uint32_t)i) << 4)) = *reinterpret_cast<const uint32_t*>(&pk);
+        }
+      } else {
+        const int c = k0 + 2 * lane;
+        const uint32_t keep = c + 1 < nn ? 0xFFFFFFFFu : (c < nn ? 0x0000FFFFu : 0u);
+#pragma unroll
+        for (int i = 0; i < KLP_ROWS_PER_WARP; ++i) {
+          const __nv_bfloat162 pk = __floats2bfloat162_rn(f64_to_f32_rne(x0[i]), f64_to_f32_rne(x1[i]));
+          *(uint32_t*)(wp + i * 128 + ((ch ^ (uint32_t)i) << 4)) = *reinterpret_cast<const uint32_t*>(&pk) & keep;
+        }
       }
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&a_full[s]);
-        mbar_arrive(&f64_empty[s]);
-      }
+      if (lane == 0) mbar_arrive(&a_full[s]);
     }
   } else if (warp == KLP_MMA_WARP) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.BN >> 3) << 17) | ((128u >> 4) << 24);
       int seg = 0, issued_any = 0;
-      for (int j = 0; j < nj; ++j) {
-        const long long u = u0 + j;
-        const int kb = (int)(u % KBt), s = j & 1;
+      for (int j = 0, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1) {
+        const int s = j & 1;
         const uint32_t ph = (uint32_t)(j >> 1) & 1u;
         const bool first = j == 0 || kb == 0, last = j == nj - 1 || kb == KBt - 1;
         const int acc = seg & 1;
@@ -269,9 +330,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;
     int seg = 0, first_kb = 0;
-    for (int j = 0; j < nj; ++j) {
-      const long long u = u0 + j;
-      const int t = (int)(u / KBt), kb = (int)(u % KBt);
+    for (int j = 0, t = t_first, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1, t += kb == 0) {
       if (j == 0 || kb == 0) first_kb = kb;
       if (!(j == nj - 1 || kb == KBt - 1)) continue;
       const int acc = seg & 1;
