@@ -140,25 +140,6 @@ static __device__ double kth_largest(const double* q, int N, int k, unsigned* hi
 #define RISK_WINDOW_MAX 2048
 #define RISK_BLOCKS 148
 
-// Pass 1 (many CTAs): per-block partial sums of Q and Q^2 (deterministic order).
-__global__ void k_risk_moments(const double* __restrict__ q, int N, double* __restrict__ part) {
-  __shared__ double red[40];
-  BlockRed br{red};
-  pdl_wait();
-  double s = 0.0, s2 = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const double v = q[i];
-    s += v;
-    s2 += v * v;
-  }
-  const double ts = br.sum(s);
-  const double ts2 = br.sum(s2);
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = ts;
-    part[2 * blockIdx.x + 1] = ts2;
-  }
-}
-
 // Warp sum of v over lanes [0, 2^k) where 2^k >= active (active <= 32): the butterfly runs only
 // as deep as the data, then lane 0's total is broadcast.  (FP64 adds are expensive on
 // GB300's narrow FP64 pipe; a window of one sample needs none.)
@@ -171,6 +152,58 @@ static __device__ __forceinline__ float warp_sum_active_f(float v, int active) {
   return __shfl_sync(0xffffffffu, v, 0);
 }
 
+// Block sums of a and b over threads [0, nact) (the other threads' values are not read):
+// the values pass through shared memory and warp 0 adds them, nact/32 + 5 FP64 adds per
+// lane of one warp instead of a shuffle tree on every warp (each FP64 warp instruction
+// holds GB300's narrow FP64 pipe for many cycles).  buf holds 2 blockDim.x + 2 doubles.
+// Every thread gets both sums.
+static __device__ void block_sum2(double& a, double& b, double* buf, int nact) {
+  const int n = blockDim.x;
+  if ((int)threadIdx.x < nact) {
+    buf[threadIdx.x] = a;
+    buf[n + threadIdx.x] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double sa = 0.0, sb = 0.0;
+    for (int i = threadIdx.x; i < nact; i += 32) {
+      sa += buf[i];
+      sb += buf[n + i];
+    }
+    sa = warp_sum_active(sa, nact < 32 ? nact : 32);
+    sb = warp_sum_active(sb, nact < 32 ? nact : 32);
+    if (threadIdx.x == 0) {
+      buf[2 * n] = sa;
+      buf[2 * n + 1] = sb;
+    }
+  }
+  __syncthreads();
+  a = buf[2 * n];
+  b = buf[2 * n + 1];
+  __syncthreads();   // buf may be reused at once
+}
+
+// Pass 1 (many CTAs): per-block partial sums of Q and Q^2 (deterministic order).
+__global__ void k_risk_moments(const double* __restrict__ q, int N, double* __restrict__ part) {
+  __shared__ double buf[2 * 256 + 2];
+  pdl_wait();
+  double s = 0.0, s2 = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double v = q[i];
+    s += v;
+    s2 += v * v;
+  }
+  // threads that hold samples: all when N covers the grid, else those below N in the first pass
+  const long long first = (long long)blockIdx.x * blockDim.x;
+  const int nact = N >= (long long)gridDim.x * blockDim.x ? (int)blockDim.x
+                                                          : (int)max(0ll, min((long long)blockDim.x, N - first));
+  if (nact > 0) block_sum2(s, s2, buf, nact);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = nact > 0 ? s : 0.0;
+    part[2 * blockIdx.x + 1] = nact > 0 ? s2 : 0.0;
+  }
+}
+
 // Top 32 bits of the order-preserving keys of q[0, N), N <= KEYS_PER_THREAD * blockDim.x.
 #define KEYS_PER_THREAD 16
 static __device__ __forceinline__ void load_key_prefixes(const double* q, int N, uint32_t (&kr)[KEYS_PER_THREAD]) {
@@ -181,18 +214,44 @@ static __device__ __forceinline__ void load_key_prefixes(const double* q, int N,
   }
 }
 
-// k-th largest (1-based) of q[0, N) for N <= 16 * blockDim.x: an 11/11/10-bit radix select
-// on the top 32 bits of the order-preserving keys (held in registers), then an exact choice
-// among the samples that share those 32 bits (at most 32 of them; otherwise *ok = false).
+// k-th largest (1-based) of q[0, N) for N <= 16 * blockDim.x (blockDim.x = 1024), on the
+// top 32 bits of the order-preserving keys (held in registers).  The bits above the keys'
+// highest difference are common to all; radix digits of at most 11 bits follow from there
+// down, each narrowing the prefix to the bin that holds rank k, until at most 32 keys share
+// it; the answer is then chosen exactly among those samples by their full 64-bit keys.
+// *ok = false when more than 32 samples share all 32 bits (the caller falls back).
 static __device__ double kth_largest_prefix(const double* q, int N, int k, const uint32_t (&kr)[KEYS_PER_THREAD],
                                             unsigned* hist, unsigned* sel, double* cand, int* ncand, bool* ok) {
   constexpr int KPT = KEYS_PER_THREAD;
-  uint32_t prefix = 0, mask = 0;
-  unsigned kk = (unsigned)k;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int pass = 0; pass < 3; ++pass) {
-    const int shift = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
-    const uint32_t dmask = pass == 2 ? 1023u : 2047u;
+  uint32_t ka = 0xFFFFFFFFu, ko = 0u;
+#pragma unroll
+  for (int j = 0; j < KPT; ++j)
+    if (j * (int)blockDim.x + (int)threadIdx.x < N) {
+      ka &= kr[j];
+      ko |= kr[j];
+    }
+  ka = __reduce_and_sync(0xffffffffu, ka);
+  ko = __reduce_or_sync(0xffffffffu, ko);
+  if (threadIdx.x == 0) {
+    sel[0] = 0xFFFFFFFFu;
+    sel[1] = 0u;
+  }
+  __syncthreads();
+  if (lane == 0) {
+    atomicAnd(&sel[0], ka);
+    atomicOr(&sel[1], ko);
+  }
+  __syncthreads();
+  const uint32_t diff = sel[0] ^ sel[1];
+  int top = diff ? 31 - __clz(diff) : -1;   // highest bit in which keys differ
+  uint32_t mask = top >= 0 ? ~(0xFFFFFFFFu >> (31 - top)) : 0xFFFFFFFFu;
+  uint32_t prefix = sel[0] & mask;
+  unsigned kk = (unsigned)k, count = (unsigned)N;
+  __syncthreads();
+  while (count > 32u && top >= 0) {
+    const int width = top + 1 < 11 ? top + 1 : 11, shift = top + 1 - width;
+    const uint32_t dmask = (1u << width) - 1u;
     for (int b = threadIdx.x; b < 2048; b += blockDim.x) hist[b] = 0u;
     __syncthreads();
 #pragma unroll
@@ -231,32 +290,36 @@ static __device__ double kth_largest_prefix(const double* q, int N, int k, const
       if (excl + h0 >= kk) {
         sel[0] = 2047u - 2u * threadIdx.x;
         sel[1] = kk - excl;
+        sel[66] = h0;
       } else {
         sel[0] = 2046u - 2u * threadIdx.x;
         sel[1] = kk - excl - h0;
+        sel[66] = h1;
       }
     }
     __syncthreads();
     prefix |= sel[0] << shift;
     mask |= dmask << shift;
     kk = sel[1];
+    count = sel[66];
+    top = shift - 1;
     __syncthreads();
   }
-  // samples whose top 32 key bits equal the selected prefix; the answer is the kk-th largest of them
+  *ok = count <= 32u;
+  if (count > 32u) return 0.0;
+  // the samples under the selected prefix; the answer is the kk-th largest of them
   if (threadIdx.x == 0) *ncand = 0;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < KPT; ++j) {
     const int i = j * blockDim.x + threadIdx.x;
-    if (i < N && kr[j] == prefix) {
+    if (i < N && (kr[j] & mask) == prefix) {
       const int slot = atomicAdd(ncand, 1);
       if (slot < 32) cand[slot] = q[i];
     }
   }
   __syncthreads();
   const int nc = *ncand;
-  *ok = nc <= 32;
-  if (!*ok) return 0.0;
   if (warp == 0) {
     const uint64_t mine = lane < nc ? dkey(cand[lane]) : 0ull;
     unsigned rank = 0;
@@ -287,12 +350,12 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
                               const RiskDev* __restrict__ risks, int n_risks, double* __restrict__ params,
                               double* __restrict__ zero_out, int n_zero) {
   __shared__ unsigned hist[2048];
-  __shared__ unsigned sel[2 + 64];
+  __shared__ unsigned sel[2 + 64 + 1];
   __shared__ double cand[32];
   __shared__ int ncand;
   __shared__ double win[RISK_WINDOW_MAX];
   __shared__ float winf[RISK_WINDOW_MAX];
-  __shared__ int nwin;
+  __shared__ int nwin, s_above;
   __shared__ double s_par[6];   // qbar, var, -, v + eps, v - eps, t
   __shared__ bool s_ok;
   __shared__ double red[40];
@@ -300,10 +363,9 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
   pdl_wait();
   if (zero_out)   // the weighted-gradient sums of the next pass start from 0
     for (int i = threadIdx.x; i < n_zero; i += blockDim.x) zero_out[i] = 0.0;
-  // key prefixes first: their loads are in flight while warp 0 combines the moments
-  bool need_select = false;
-  for (int r = 0; r < n_risks; ++r) need_select |= risks[r].kind == OUU_RISK_CVAR_SMOOTH && risks[r].t_optimal;
-  const bool prefix_path = need_select && N <= KEYS_PER_THREAD * (int)blockDim.x;
+  // key prefixes first (whether or not a t* is asked for): their loads are in flight while
+  // the risk descriptors are read and warp 0 combines the moments
+  const bool prefix_path = N <= KEYS_PER_THREAD * (int)blockDim.x;
   uint32_t kr[KEYS_PER_THREAD];
   if (prefix_path) load_key_prefixes(q, N, kr);
   if (warp == 0) {   // moments from the per-block partial sums
@@ -342,23 +404,54 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
         s_par[3] = v + eps;
         s_par[4] = v - eps;
         nwin = 0;
+        s_above = 0;
       }
       __syncthreads();
       const uint64_t khi = dkey(s_par[3]), klo = dkey(s_par[4]);
       int C = 0;   // samples at or above v + eps (each contributes exactly 1)
-      for (int i0 = 0; i0 < N; i0 += blockDim.x) {   // uniform trip count for __syncthreads_count
-        const int i = i0 + threadIdx.x;
-        bool above = false;
-        if (i < N) {
-          const double qi = q[i];
-          const uint64_t k = dkey(qi);
-          above = k >= khi;
-          if (!above && k > klo) {
-            const int slot = atomicAdd(&nwin, 1);
-            if (slot < RISK_WINDOW_MAX) win[slot] = qi;
+      if (prefix_path) {
+        // from the register-held prefixes: a prefix above that of v + eps is above it, one
+        // below that of v - eps is below the window; the rest (the window and the two
+        // boundary prefixes) are tested on their full keys
+        const uint32_t hp = (uint32_t)(khi >> 32), lp = (uint32_t)(klo >> 32);
+        unsigned above = 0;
+#pragma unroll
+        for (int j = 0; j < KEYS_PER_THREAD; ++j) {
+          const int i = j * blockDim.x + threadIdx.x;
+          if (i < N) {
+            if (kr[j] > hp) {
+              ++above;
+            } else if (kr[j] >= lp) {
+              const double qi = q[i];
+              const uint64_t kf = dkey(qi);
+              if (kf >= khi) {
+                ++above;
+              } else if (kf > klo) {
+                const int slot = atomicAdd(&nwin, 1);
+                if (slot < RISK_WINDOW_MAX) win[slot] = qi;
+              }
+            }
           }
         }
-        C += __syncthreads_count(above);
+        above = __reduce_add_sync(0xffffffffu, above);
+        if (lane == 0) atomicAdd(&s_above, (int)above);
+        __syncthreads();
+        C = s_above;
+      } else {
+        for (int i0 = 0; i0 < N; i0 += blockDim.x) {   // uniform trip count for __syncthreads_count
+          const int i = i0 + threadIdx.x;
+          bool above = false;
+          if (i < N) {
+            const double qi = q[i];
+            const uint64_t k = dkey(qi);
+            above = k >= khi;
+            if (!above && k > klo) {
+              const int slot = atomicAdd(&nwin, 1);
+              if (slot < RISK_WINDOW_MAX) win[slot] = qi;
+            }
+          }
+          C += __syncthreads_count(above);
+        }
       }
       const int W = nwin;
       const double K = R.K;
@@ -419,7 +512,13 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
               hi = t;
             }
             if (hi - lo <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) break;
-            const double step = dg > 0.0 ? g / dg : INFINITY;
+            // the Newton step needs a few correct bits only: an FP32 reciprocal of G' (an
+            // FP64 division is a long sequence on the narrow FP64 pipe)
+            double step = INFINITY;
+            if (dg > 0.0) {
+              const float df = (float)dg;
+              step = (df > 1e-30f && df < 1e30f) ? g * (double)(1.0f / df) : g / dg;
+            }
             double nt;
             if (fabs(step) <= 2.220446049250313e-16 * fabs(t)) {   // converged: bracket t tightly
               const double a = nextafter(t, -INFINITY), b = nextafter(t, INFINITY);
@@ -473,21 +572,33 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
 // Pass 3 (many CTAs, each a contiguous range of samples): weights w[r][i] and per-block
 // partial sums of s_eps and s'_eps; with per-sample gradients gq [N][ldg] (FP32), also
 // grad_out[r][j] += sum_i w[r][i] gq[i][j] (per-block FP64 sums added atomically; the
-// select pass zeroed grad_out).  The last block to finish (an arrival counter, reset for the
-// next call) combines the partial sums into the risk values and d rho / dt.
-// out[3r..3r+2] = value, dt, t.
+// select pass zeroed grad_out).  The products and the per-thread sums run in float-float
+// arithmetic: w = wh + wl (two FP32), wh g split exactly by an FMA, sums by the error-free
+// two-sum, so each thread's total carries about 44 bits and only the totals are FP64.
+// The last block to finish (an arrival counter, reset for the next call) combines the
+// partial sums into the risk values and d rho / dt.  out[3r..3r+2] = value, dt, t.
 #define APPLY_SUB 128
+static __device__ __forceinline__ void ff_add_prod(float& sh, float& sl, float wh, float wl, float g) {
+  const float p = wh * g;
+  float e = fmaf(wh, g, -p);   // wh g = p + e exactly
+  e = fmaf(wl, g, e);
+  const float t = sh + p;      // two-sum: sh + p = t + err exactly
+  const float bp = t - sh;
+  const float err = (sh - (t - bp)) + (p - bp);
+  sh = t;
+  sl += err + e;
+}
+
 __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q, int N,
                                                     const RiskDev* __restrict__ risks, int n_risks,
                                                     const double* __restrict__ params, double* __restrict__ w,
                                                     double* __restrict__ part, unsigned* __restrict__ arrivals,
                                                     double* __restrict__ out, const float* __restrict__ gq, int ldg,
                                                     int dz, double* __restrict__ grad_out) {
-  __shared__ double red[40];
   __shared__ bool last;
-  __shared__ double ws[OUU_MAX_RISKS][APPLY_SUB];
+  __shared__ float wsh[OUU_MAX_RISKS][APPLY_SUB], wsl[OUU_MAX_RISKS][APPLY_SUB];
   __shared__ double gsum[OUU_MAX_RISKS][128];
-  BlockRed br{red};
+  __shared__ double buf[2 * 256 + 2];
   pdl_wait();
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int i0 = min(N, (int)blockIdx.x * chunk), i1 = min(N, i0 + chunk);
@@ -514,7 +625,11 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
           sd[r] += d1;
         }
         w[(int64_t)r * N + i] = wi;
-        ws[r][i - s0] = wi;
+        if (gq) {
+          const float wh = (float)wi;
+          wsh[r][i - s0] = wh;
+          wsl[r][i - s0] = (float)(wi - (double)wh);
+        }
       }
     }
     if (gq) {
@@ -522,38 +637,41 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
       const int g = threadIdx.x >> 7, jl = threadIdx.x & 127;   // two sample halves x 128 columns
       for (int jb = 0; jb < dz; jb += 128) {
         const int j = jb + jl;
-        double acc[OUU_MAX_RISKS];
+        float sh[OUU_MAX_RISKS], sl[OUU_MAX_RISKS];
 #pragma unroll
-        for (int r = 0; r < OUU_MAX_RISKS; ++r) acc[r] = 0.0;
+        for (int r = 0; r < OUU_MAX_RISKS; ++r) sh[r] = sl[r] = 0.f;
         if (j < dz && g < 2)
           for (int i = s0 + g; i < s1; i += 2) {
-            const double gv = (double)gq[(int64_t)i * ldg + j];
+            const float gv = gq[(int64_t)i * ldg + j];
 #pragma unroll
             for (int r = 0; r < OUU_MAX_RISKS; ++r)
-              if (r < n_risks) acc[r] += ws[r][i - s0] * gv;
+              if (r < n_risks) ff_add_prod(sh[r], sl[r], wsh[r][i - s0], wsl[r][i - s0], gv);
           }
         if (g == 1)
 #pragma unroll
-          for (int r = 0; r < OUU_MAX_RISKS; ++r) gsum[r][jl] = acc[r];
+          for (int r = 0; r < OUU_MAX_RISKS; ++r)
+            if (r < n_risks) gsum[r][jl] = (double)sh[r] + (double)sl[r];
         __syncthreads();
         if (g == 0 && j < dz)
 #pragma unroll
           for (int r = 0; r < OUU_MAX_RISKS; ++r)
-            if (r < n_risks) atomicAdd(&grad_out[r * dz + j], acc[r] + gsum[r][jl]);
+            if (r < n_risks) atomicAdd(&grad_out[r * dz + j], ((double)sh[r] + (double)sl[r]) + gsum[r][jl]);
         __syncthreads();
       }
     }
     __syncthreads();
   }
+  // threads that held samples: [0, min(range, APPLY_SUB))
+  const int nact = min(i1 - i0, APPLY_SUB);
 #pragma unroll
   for (int r = 0; r < OUU_MAX_RISKS; ++r) {
     if (r >= n_risks) break;
     if (risks[r].kind == OUU_RISK_MEAN_VAR) continue;
-    const double tv = br.sum(sv[r]);
-    const double td = br.sum(sd[r]);
+    double tv = sv[r], td = sd[r];
+    if (nact > 0) block_sum2(tv, td, buf, nact);
     if (threadIdx.x == 0) {
-      part[(2 * r) * gridDim.x + blockIdx.x] = tv;
-      part[(2 * r + 1) * gridDim.x + blockIdx.x] = td;
+      part[(2 * r) * gridDim.x + blockIdx.x] = nact > 0 ? tv : 0.0;
+      part[(2 * r + 1) * gridDim.x + blockIdx.x] = nact > 0 ? td : 0.0;
     }
   }
   __threadfence();
