@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--pde-steps", type=int, default=3)
     ap.add_argument("--train", type=int, default=32768, help="training pairs for the surrogate")
     ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--network-mode", type=int, default=None, choices=[0, 1, 2],
+                    help="evaluation network (default: the library's, 2): 0 per-layer GEMM kernels, "
+                         "1 one kernel per tile, 2 4-CTA clusters")
     ap.add_argument("--lr-final", type=float, default=1e-5,
                     help="geometric decay of the second half's rate down to this (0: keep 2.5e-4)")
     ap.add_argument("--batch", action="store_true",
@@ -352,6 +355,9 @@ def run_ours(args):
                 "adjoint_solves": float(np.mean([s.adjoint_solves for s in st]))}
 
     if use_dino:
+        net_mode = 2 if args.network_mode is None else args.network_mode   # the library default is 2
+        D.ouu_dino_set_fused_network(net_mode)
+
         def step():
             return P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)
         for _ in range(max(3, args.warmup)):
@@ -378,17 +384,20 @@ def run_ours(args):
                "risks": ["cvar0.95", "mean+var"], "reference": "plain GPU path (matches the FP64 oracle to 1e-8)"}
         nnp = (n * n + 63) // 64 * 64
         in0 = R_M + dz
+        net_kernel = {0: "k_build_x0 + k_gemm_bf16 x 8 (MLP forward + reverse-mode gradient)",
+                      1: "k_mlp_eval (whole MLP per 128-sample tile)",
+                      2: "k_mlp_cluster (whole MLP, 4-CTA clusters per 128-sample tile)"}[net_mode]
         flops_net = 2 * N * (in0 * WIDTH + 2 * WIDTH * WIDTH + WIDTH * R_U) + 2 * N * (R_U * WIDTH + 2 * WIDTH * WIDTH + WIDTH * dz)
         # algorithmic bytes of the fused projection: the FP64 fields once, the BF16 KL basis,
         # the FP32 coordinates written (the atomic partial sums of the K split come on top)
         kern = {
             "project": ("k_kl_project (fused FP64 read + BF16 tcgen05 KL projection)", "hbm",
                         N * n * n * 8 + R_M * nnp * 2 + N * R_M * 4, ph["ms_project"]),
-            "network": ("k_gemm_bf16 x 8 (MLP forward + reverse-mode gradient)", "tensor", flops_net, ph["ms_network"]),
+            "network": (net_kernel, "tensor", flops_net, ph["ms_network"]),
         }
         # DRAM bytes per launch from the committed ncu capture of the same kernel
         # (profiles/kl_project_129x129_N1024_ncu.md: N = 1024, scaled by the 4x samples)
-        traffic = {"project": 4 * (148.111872e6 + 3.392512e6)}
+        traffic = {"project": 4 * (148.096e6 + 3.491072e6)}
         key = max(kern, key=lambda k: kern[k][3])
         name, bound, work, kms = kern[key]
         achieved = work / (kms / 1000.0) / (1e9 if bound == "hbm" else 1e12)
@@ -400,9 +409,10 @@ def run_ours(args):
                 "phases": {k: {"kernel": v[0], "bound": v[1], "ms": v[3],
                                "achieved": v[2] / (v[3] / 1000.0) / (1e9 if v[1] == "hbm" else 1e12)}
                            for k, v in kern.items()}}
-        # per step: k_kl_project, k_build_x0, 4 forward GEMMs (the last with the reduced-QoI
-        # epilogue), 4 reverse GEMMs, k_risk_moments, k_risk_select, k_risk_apply
-        launches = 13 * args.steps
+        # per step: k_kl_project; the network (mode 0: k_build_x0, 4 forward GEMMs, the last with
+        # the reduced-QoI epilogue, and 4 reverse GEMMs; modes 1 and 2: one kernel);
+        # k_risk_moments, k_risk_select, k_risk_apply
+        launches = (13 if net_mode == 0 else 5) * args.steps
         e2e = None
         if not args.no_e2e:
             m_host = m.cpu().pin_memory()
@@ -470,7 +480,9 @@ def run_ours(args):
                        "risks": ["cvar_smooth beta=0.95 eps=1e-4 t=t*", "mean+var kappa=1"],
                        "backend": args.backend, "sample_evals_per_s": value * N,
                        "l2": "inputs larger than L2 (545 MB of FP64 fields per step)",
-                       "surrogate": recipe},
+                       "surrogate": recipe,
+                       "network_mode": {0: "per-layer kernels", 1: "one kernel per tile",
+                                        2: "4-CTA clusters"}[net_mode] if use_dino else None},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "pde": pde_info, "speedup_vs_pde": value / pde_rate if use_dino else 1.0,
             "accuracy": acc, "phases_ms": ph,

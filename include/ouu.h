@@ -277,12 +277,17 @@ ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_samples, const
  * enqueues its kernels eagerly and reports per-phase times in ouu_eval_stats). */
 ouu_status ouu_dino_set_graphs(ouu_dino_t d, int enable);
 
-/* The evaluation network with a gradient (projection output -> forward layers -> reduced QoI
- * -> reverse-mode z-gradient) runs as one fused tensor-core kernel per 128-sample tile when
- * the network fits it (width, r_U, d_Z <= 416, r_M + d_Z <= 448); enable = 0 selects the
- * per-layer GEMM kernels instead (same arithmetic).  Default 0: one CTA per 128 samples
- * leaves the GELU epilogues of a layer to one SM, which at thousands of samples is slower
- * than the per-layer kernels; ouu_batch_create with autotune picks per network by timing. */
+/* How the evaluation network with a gradient (projection output -> forward layers -> reduced
+ * QoI -> reverse-mode z-gradient) runs; every mode has the same arithmetic.
+ *   mode 0: one tensor-core GEMM kernel per layer, fused epilogues;
+ *   mode 1: one kernel, one CTA per 128-sample tile holding the activations in shared memory
+ *           (width, r_U, d_Z <= 416, r_M + d_Z <= 448); the GELU epilogues of a layer then run
+ *           on one SM per tile, slower than mode 0 at thousands of samples;
+ *   mode 2 (default): one kernel, each 128-sample tile on a cluster of 4 CTAs, each computing a quarter of
+ *           every layer's columns, activations passed through L2 (width, r_U, r_M + d_Z <= 448,
+ *           d_Z <= 512, r_M % 4 == 0, width % 8 == 0).
+ * A mode whose size limits the network exceeds falls back to mode 0.  ouu_batch_create with
+ * autotune picks per network by timing.  Returns OUU_ERR_INVALID_ARG for another mode. */
 ouu_status ouu_dino_set_fused_network(ouu_dino_t d, int enable);
 
 /* Thread-local message of the last failed call ("" if none).  Copies at most
@@ -306,7 +311,7 @@ int ouu_problem_slots(ouu_problem_t p);
  *   - each MR-DINO problem's evaluation on a concurrent branch of the graph.
  * With autotune != 0, ouu_batch_create times every MR-DINO problem's evaluation with the
  * per-layer GEMM kernels (their N tiles tuned per layer shape by measurement) and with the
- * one-kernel network, and keeps the faster for that network (ouu_dino_set_fused_network).
+ * one-kernel networks, and keeps the fastest for that network (ouu_dino_set_fused_network).
  *
  * Each item names its own problem handle and, for MR-DINO, its own network (items must
  * not share either: the handle's arena holds the item's results, the network's buffers

@@ -35,7 +35,17 @@
  * w = (1 + 2 kappa (Q_i - Qbar)) / N; smoothed CVaR: w = s'_eps(Q_i - t) / (N (1 - beta)).
  * With gq_dev (device FP32 per-sample gradients [N][ldg], dz columns used), also
  * grad_host[r][j] = sum_i w[r][i] gq[i][j] (FP64 sums), the SAA gradient of the risk.
- * Synchronises `stream`; allocates its own scratch (test entry only). */
+ * Synchronises `stream`; allocates its own scratch (test entry only).
+ *
+ * ouu_kernel_dino_network: the MR-DINO evaluation network of Sec. 3.3 (layer-0 input
+ * [xi; z] in BF16, three GELU layers, output layer phi with the reduced QoI
+ * Q = 1/2 ||phi + c||^2 + const and, when gradq_dev is given, the reverse-mode
+ * grad_z Q) from given projection coordinates xi_dev (device FP32 [n_samples][r_M]) instead
+ * of from fields, in network mode `mode` (0 per-layer kernels, 1 one kernel per 128-sample
+ * tile, 2 4-CTA clusters; see ouu_dino_set_fused_network), so that the modes can be
+ * compared on identical inputs.  z_host: d_Z controls.  Outputs (device, each may be NULL):
+ * q_dev [n_samples] FP64, phi_dev [n_samples][r_U] FP32, gradq_dev [n_samples][d_Z] FP64.
+ * The handle's own network mode is restored; synchronises the handle's stream. */
 #ifndef OUU_KERNELS_H
 #define OUU_KERNELS_H
 
@@ -65,6 +75,9 @@ int ouu_kernel_gemm_tuned_shapes(void);
 
 ouu_status ouu_kernel_kl_project(const double* m, int N, int nn, const void* W, int ldw, int rm, const float* bias,
                                  float* xi, int* err_dev, void* stream);
+
+ouu_status ouu_kernel_dino_network(ouu_dino_t d, const float* xi_dev, int n_samples, const double* z_host, int mode,
+                                   double* q_dev, float* phi_dev, double* gradq_dev);
 
 #ifdef __cplusplus
 }

@@ -109,6 +109,7 @@ SIGNATURES = {
     "ouu_batch_run": (_i, [_vp, ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                            ctypes.POINTER(_dp), _dp, _dp]),
     "ouu_kernel_gemm_tuned_shapes": (_i, []),
+    "ouu_kernel_dino_network": (_i, [_vp, _vp, _i, _dp, _i, _vp, _vp, _vp]),
     "ouu_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "ouu_problem_slots": (_i, [_vp]),
 }
@@ -371,8 +372,20 @@ class Dino:
         check(load().ouu_dino_get_output_scale(self.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
         return s
 
-    def ouu_dino_set_fused_network(self, enable):
-        check(load().ouu_dino_set_fused_network(self.handle, 1 if enable else 0))
+    def ouu_kernel_dino_network(self, xi, n_samples, z, mode, q=None, phi=None, gradq=None):
+        """The evaluation network alone from device FP32 projection coordinates xi [N][r_M], in
+        network mode `mode` (kernel-level test entry)."""
+        import numpy as np
+        import torch
+        zz = np.ascontiguousarray(z, dtype=np.float64)
+        check(load().ouu_kernel_dino_network(self.handle, dev_ptr(xi, torch.float32), n_samples,
+                                             zz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(mode),
+                                             dev_ptr(q, torch.float64), dev_ptr(phi, torch.float32),
+                                             dev_ptr(gradq, torch.float64)))
+
+    def ouu_dino_set_fused_network(self, mode):
+        """0: per-layer GEMM kernels, 1: one kernel per 128-sample tile, 2: 4-CTA clusters."""
+        check(load().ouu_dino_set_fused_network(self.handle, int(mode)))
 
     def ouu_dino_set_graphs(self, enable):
         check(load().ouu_dino_set_graphs(self.handle, int(enable)))

@@ -215,8 +215,8 @@ extern "C" ouu_status ouu_batch_create(const ouu_batch_item* items, int n_items,
   BATCH_CUDA(cudaMalloc((void**)&b->d_cycles, 2 * np * 8));
   BATCH_CUDA(cudaMallocHost((void**)&b->h_cycles, 2 * np * 8));
   // Autotuning of every MR-DINO problem's evaluation: the per-layer GEMM path with its N tiles
-  // timed per layer shape, against the one-kernel network; the faster one is kept (the fused
-  // kernel runs one CTA per 128 samples, so small sample counts can favour the layer kernels).
+  // timed per layer shape, against the one-kernel networks (one CTA per 128 samples, and 4-CTA
+  // clusters per 128 samples); the fastest is kept.
   if (autotune && !b->dino.empty()) {
     ouu_status st = OUU_OK;
     cudaEvent_t t0, t1;
@@ -226,21 +226,25 @@ extern "C" ouu_status ouu_batch_create(const ouu_batch_item* items, int n_items,
       BatchEntry& e = b->items[k];
       ouu_dino* d = e.it.dino;
       std::vector<double> z0(e.it.problem->dz, 0.0);
-      float ms[2] = {1e30f, 1e30f};
-      const int fits = mlp_fused_fits(d) ? 1 : 0;
-      for (int fused = 0; fused <= fits && st == OUU_OK; ++fused) {
-        d->fused_mlp = fused;
-        if (!fused) ouu_gemm_set_autotune(1);
+      float ms[3] = {1e30f, 1e30f, 1e30f};
+      const int fits[3] = {1, mlp_fused_fits(d) ? 1 : 0, mlp_cluster_fits(d) ? 1 : 0};
+      for (int mode = 0; mode < 3 && st == OUU_OK; ++mode) {
+        if (!fits[mode]) continue;
+        d->fused_mlp = mode;
+        if (mode == 0) ouu_gemm_set_autotune(1);
         for (int rep = 0; rep < 2 && st == OUU_OK; ++rep) {   // the second run is timed
           cudaEventRecord(t0, d->stream);
           st = dino_enqueue_risk(e.it.problem, d, e.it.m_dev, e.it.n_samples, e.it.n_risks, z0.data());
           cudaEventRecord(t1, d->stream);
           if (st == OUU_OK && cudaEventSynchronize(t1) != cudaSuccess) st = OUU_ERR_CUDA;
-          if (st == OUU_OK && rep == 1) cudaEventElapsedTime(&ms[fused], t0, t1);
+          if (st == OUU_OK && rep == 1) cudaEventElapsedTime(&ms[mode], t0, t1);
         }
         ouu_gemm_set_autotune(0);
       }
-      d->fused_mlp = (fits && ms[1] <= ms[0]) ? 1 : 0;
+      int best = 0;
+      for (int mode = 1; mode < 3; ++mode)
+        if (fits[mode] && ms[mode] < ms[best]) best = mode;
+      d->fused_mlp = best;
       if (d->gexec) {   // the network's own captured evaluation may hold the other path
         cudaGraphExecDestroy(d->gexec);
         d->gexec = nullptr;

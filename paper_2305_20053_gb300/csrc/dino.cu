@@ -14,16 +14,12 @@
 #include <vector>
 
 #include "dino.cuh"
+#include "gelu.cuh"
+#include "ouu_kernels.h"
 
 static int pad8(int x) { return (x + 7) / 8 * 8; }
 static int pad64(int x) { return (x + 63) / 64 * 64; }
 
-static __device__ __forceinline__ float gelu_d1(float x) {
-  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
-}
-static __device__ __forceinline__ float gelu_d2(float x) {
-  return 0.3989422804014327f * expf(-0.5f * x * x) * (2.f - x * x);
-}
 
 #define GRID_STRIDE(e, total) \
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (total); e += (int64_t)gridDim.x * blockDim.x)
@@ -320,7 +316,7 @@ static void free_dino(ouu_dino* d) {
   void* ptrs[] = {d->d_params, d->d_grad, d->d_adam_m, d->d_adam_v, d->d_phi, d->d_phi64, d->d_ubar, d->d_ut,
                   d->d_c, d->d_cf, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
                   d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
-                  d->Ge, d->GQe, d->Qe, d->d_zf, d->d_err, d->d_gov, d->d_oscale, d->d_klbias};
+                  d->Ge, d->GQe, d->Qe, d->Qpart, d->d_zf, d->d_err, d->d_gov, d->d_oscale, d->d_klbias};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < 4; ++l) {
     cudaFree(d->A[l]);
@@ -446,6 +442,7 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   al((void**)&d->Ge, E * rup * 2);
   al((void**)&d->GQe, E * dzp * 4);
   al((void**)&d->Qe, E * 8);
+  al((void**)&d->Qpart, E * 4 * 4);
   al((void**)&d->d_zf, std::max<size_t>(maxB, 1) * d->dz * 4 + 64);
   al((void**)&d->d_err, 16);
   if (ok && cudaMallocHost((void**)&d->h_pin, (size_t)(4 * 3 + 4 * d->dz + 64) * 8 + 4096) != cudaSuccess) ok = false;
@@ -780,14 +777,22 @@ extern "C" ouu_status ouu_dino_loss_grad(ouu_dino_t d, const float* xi_dev, cons
 // ------------------------------------------------------------------ evaluation
 // Projection, forward values, reduced QoI (Qe) and, with want_grad, per-sample
 // grad_z Q in GQe by reverse mode: seed phi + c through W3^T, GELU', ... , W0z^T.
+static ouu_status dino_network(ouu_dino* d, int N, bool want_grad);
+
 ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad) {
-  const int wd = d->wd, wdp = d->wd, rup = pad8(d->ru), in0p = d->inp_l[0], dz = d->dz, dzp = pad8(d->dz);
   float* zh = (float*)d->h_pin;
-  for (int j = 0; j < dz; ++j) zh[j] = (float)z_host[j];
-  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)dz * 4, cudaMemcpyHostToDevice, d->stream));
+  for (int j = 0; j < d->dz; ++j) zh[j] = (float)z_host[j];
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)d->dz * 4, cudaMemcpyHostToDevice, d->stream));
   DINO_TRY(project_fields(d, m_dev, N, d->XIe, true));
-  if (want_grad && d->fused_mlp && mlp_fused_fits(d)) {   // the whole network in one kernel
-    DINO_TRY(mlp_fused_eval(d, N));
+  return dino_network(d, N, want_grad);
+}
+
+// The network from the projection coordinates in XIe and the controls in d_zf.
+static ouu_status dino_network(ouu_dino* d, int N, bool want_grad) {
+  const int wd = d->wd, wdp = d->wd, rup = pad8(d->ru), in0p = d->inp_l[0], dz = d->dz, dzp = pad8(d->dz);
+  if (want_grad && ((d->fused_mlp == 1 && mlp_fused_fits(d)) || (d->fused_mlp == 2 && mlp_cluster_fits(d)))) {
+    // the whole network in one kernel
+    DINO_TRY(d->fused_mlp == 2 ? mlp_cluster_eval(d, N) : mlp_fused_eval(d, N));
     if (!d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[3], d->stream));
     OUU_CUDA_TRY(cudaGetLastError());
     return OUU_OK;
@@ -874,6 +879,33 @@ extern "C" ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_sam
   return check_err(d);
 }
 
+extern "C" ouu_status ouu_kernel_dino_network(ouu_dino_t d, const float* xi_dev, int n_samples, const double* z_host,
+                                              int mode, double* q_dev, float* phi_dev, double* gradq_dev) {
+  OUU_CHECK_ARG(d && xi_dev && z_host, "null argument");
+  OUU_CHECK_ARG(d->bases_ready, "bases not built");
+  OUU_CHECK_ARG(n_samples >= 1 && n_samples <= d->maxE, "n_samples outside [1, max_eval]");
+  OUU_CHECK_ARG(mode >= 0 && mode <= 2, "network mode: 0, 1 or 2");
+  const int rup = pad8(d->ru), dz = d->dz, dzp = pad8(d->dz);
+  float* zh = (float*)d->h_pin;
+  for (int j = 0; j < dz; ++j) zh[j] = (float)z_host[j];
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)dz * 4, cudaMemcpyHostToDevice, d->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->XIe, xi_dev, (size_t)n_samples * d->rm * 4, cudaMemcpyDeviceToDevice, d->stream));
+  const int saved = d->fused_mlp;
+  d->fused_mlp = mode;
+  const ouu_status st = dino_network(d, n_samples, gradq_dev != nullptr);
+  d->fused_mlp = saved;
+  DINO_TRY(st);
+  if (phi_dev)
+    k_copy_rows_f32<<<grid_for((int64_t)n_samples * d->ru), 256, 0, d->stream>>>(d->OUTe, rup, n_samples, d->ru,
+                                                                                 phi_dev, d->ru);
+  if (q_dev) OUU_CUDA_TRY(cudaMemcpyAsync(q_dev, d->Qe, (size_t)n_samples * 8, cudaMemcpyDeviceToDevice, d->stream));
+  if (gradq_dev)
+    k_f32_to_f64<<<grid_for((int64_t)n_samples * dz), 256, 0, d->stream>>>(d->GQe, dzp, n_samples, dz, gradq_dev);
+  OUU_CUDA_TRY(cudaGetLastError());
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return check_err(d);
+}
+
 extern "C" ouu_status ouu_dino_set_output_scale(ouu_dino_t d, const float* s_host) {
   OUU_CHECK_ARG(d && s_host, "null argument");
   for (int r = 0; r < d->ru; ++r) OUU_CHECK_ARG(s_host[r] > 0 && std::isfinite(s_host[r]), "scales must be positive");
@@ -891,7 +923,8 @@ extern "C" ouu_status ouu_dino_get_output_scale(ouu_dino_t d, float* s_host) {
 
 extern "C" ouu_status ouu_dino_set_fused_network(ouu_dino_t d, int enable) {
   OUU_CHECK_ARG(d != nullptr, "null argument");
-  d->fused_mlp = enable ? 1 : 0;
+  OUU_CHECK_ARG(enable >= 0 && enable <= 2, "network mode: 0 per-layer kernels, 1 one kernel, 2 clusters");
+  d->fused_mlp = enable;
   if (d->gexec) {   // a captured evaluation holds the other path's kernels
     cudaGraphExecDestroy(d->gexec);
     d->gexec = nullptr;

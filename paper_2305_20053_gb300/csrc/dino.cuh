@@ -57,6 +57,7 @@ struct ouu_dino {
   __nv_bfloat16* Ge = nullptr;     // [maxE][ru] seed phi + c
   float* GQe = nullptr;            // [maxE][dz]
   double* Qe = nullptr;            // [maxE]
+  float* Qpart = nullptr;          // [maxE][4] per-CTA partial QoI sums of the cluster network
   float* d_zf = nullptr;           // [max(maxB, 1) * dz] FP32 controls of the current call
   double* h_pin = nullptr;         // pinned host scratch
   int* d_err = nullptr;
@@ -68,7 +69,9 @@ struct ouu_dino {
   const double* gkey_m = nullptr;
   int gkey_N = 0, gkey_nr = 0;
   int use_graphs = 1;
-  int fused_mlp = 0;               // evaluation network in one kernel (mlp_fused.cu) when it fits
+  int fused_mlp = 2;               // evaluation network: 0 per-layer kernels, 1 one kernel per
+                                   // 128-sample tile (mlp_fused.cu), 2 one kernel over 4-CTA
+                                   // clusters (mlp_cluster.cu); 1 and 2 when the sizes fit
   bool capturing = false;
 };
 
@@ -80,6 +83,12 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
 // mode to GQe.  mlp_fused_fits: the handle's sizes fit the kernel (width, r_u, d_Z <= 416).
 bool mlp_fused_fits(const ouu_dino* d);
 ouu_status mlp_fused_eval(ouu_dino* d, int N);
+// The same network with each 128-sample tile on a cluster of 4 CTAs, each CTA computing a
+// quarter of every layer's columns; the layers' activations pass through the handle's
+// evaluation buffers in L2 (mlp_cluster.cu).  mlp_cluster_fits: width, r_U, r_M + d_Z <= 448,
+// d_Z <= 512, r_M % 4 == 0, width % 8 == 0.
+bool mlp_cluster_fits(const ouu_dino* d);
+ouu_status mlp_cluster_eval(ouu_dino* d, int N);
 
 // The whole MR-DINO risk evaluation enqueued on d->stream (capi.cu); the problem's risk
 // descriptors must be in p->d_risks.

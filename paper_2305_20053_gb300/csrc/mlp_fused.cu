@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "dino.cuh"
+#include "gelu.cuh"
 #include "tc_gemm.cuh"
 #include "tc_ptx.cuh"
 
@@ -55,7 +56,6 @@ struct MlpParams {
   int* err;
 };
 
-static __device__ __forceinline__ float mlp_gelu_cdf(float a) { return 0.5f * (1.f + erff(a * 0.70710678118654752f)); }
 
 // Epilogue column group of this warp: [c_begin, c_end) of the layer's N columns.
 static __device__ __forceinline__ void mlp_group(int N, int g, int& cb, int& ce) {
@@ -233,10 +233,7 @@ __global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_eval(const __grid_consta
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int c = c0 + j;
-            const float a = __uint_as_float(u[j]) + (c < L.N ? L.bias[c] : 0.f);
-            const float cdf = mlp_gelu_cdf(a);
-            v[j] = a * cdf;
-            dv[j] = cdf + a * 0.3989422804014327f * expf(-0.5f * a * a);
+            gelu_and_d1(__uint_as_float(u[j]) + (c < L.N ? L.bias[c] : 0.f), v[j], dv[j]);
           }
           if (in) {
             float* o = L.out_f32 + (size_t)row * L.ld_out + c0;

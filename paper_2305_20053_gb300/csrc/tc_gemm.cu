@@ -16,6 +16,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "gelu.cuh"
 #include "tc_gemm.cuh"
 #include "tc_ptx.cuh"
 
@@ -23,10 +24,8 @@
 #define GEMM_BK 64
 #define GEMM_THREADS 384
 
-static __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
-static __device__ __forceinline__ float gelu_d1f(float x) {
-  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
-}
+static __device__ __forceinline__ float gelu_f(float x) { return gelu_fwd(x); }
+static __device__ __forceinline__ float gelu_d1f(float x) { return gelu_d1(x); }
 
 // Pipeline depth: four stages; five for the wide tiles of long-K projections (one CTA per
 // SM) where five still fit in 227 KB of shared memory (BN = 208: 210 KB; BN = 256 would need 240).
@@ -117,12 +116,7 @@ static __device__ __forceinline__ void epi_quads(float* stage, const float* sbia
       }
     } else if (MODE == EPI_GELU_D) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {   // one erf and one exp give both gelu(a) and gelu'(a)
-        const float a = acc[j] + sbias[cc + j];
-        const float cdf = 0.5f * (1.f + erff(a * 0.70710678118654752f));
-        o[j] = a * cdf;
-        y[j] = cdf + a * 0.3989422804014327f * expf(-0.5f * a * a);
-      }
+      for (int j = 0; j < 4; ++j) gelu_and_d1(acc[j] + sbias[cc + j], o[j], y[j]);   // one exp for both
     } else if (MODE == EPI_GELU) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {

@@ -262,16 +262,19 @@ def test_graph_replay_matches_eager(setup):
         np.testing.assert_allclose(g1, g0, rtol=1e-12, atol=1e-15 * np.abs(g0).max())
 
 
-def test_fused_network_matches_layer_kernels(setup):
-    """The one-kernel evaluation network gives the per-layer GEMM path's results (the same BF16
-    roundings and K order; only FP32 sums of the QoI and the FP64 risk reductions may differ)."""
+@pytest.mark.parametrize("mode", [1, 2])
+def test_fused_network_matches_layer_kernels(setup, mode):
+    """The one-kernel evaluation networks (mode 1: one CTA per tile; mode 2: 4-CTA clusters, here
+    with two of the four column quarters past the width) give the per-layer GEMM path's results
+    (the same BF16 roundings and K order; only FP32 sums of the QoI and the FP64 risk reductions
+    may differ)."""
     from paper_2305_20053_gb300 import capi
     D, P, n, N = setup["D"], setup["P"], N_GRID, 40
     m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
     P.ouu_sample_fields(SEED_SAA, 0, N, m)
     z = controls(SEED_EVAL_Z, 1, DZ)[0]
     out = {}
-    for fused in (1, 0):
+    for fused in (mode, 0):
         D.ouu_dino_set_fused_network(fused)
         q = torch.empty(N, dtype=torch.float64, device="cuda")
         gq = torch.empty(N, DZ, dtype=torch.float64, device="cuda")
@@ -282,9 +285,48 @@ def test_fused_network_matches_layer_kernels(setup):
         v, g, _, _, _ = P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)
         out[fused] = (q.cpu().numpy(), gq.cpu().numpy(), phi.cpu().numpy(), v, g)
     D.ouu_dino_set_fused_network(0)
-    (q1, g1, p1, v1, r1), (q0, g0, p0, v0, r0) = out[1], out[0]
+    (q1, g1, p1, v1, r1), (q0, g0, p0, v0, r0) = out[mode], out[0]
     np.testing.assert_allclose(p1, p0, rtol=1e-5, atol=1e-6 * np.abs(p0).max())
     np.testing.assert_allclose(q1, q0, rtol=1e-5)
     assert rel(g1, g0) <= 1e-5
     np.testing.assert_allclose(v1, v0, rtol=1e-5)
     assert rel(r1, r0) <= 1e-5
+
+
+def test_cluster_network_bench_shape():
+    """The one-kernel networks (modes 1 and 2) at the widths of the 129 x 129 workload's network
+    (r_M 200, width 400, r_U 200, d_Z 100), random weights and an M-orthonormal random basis,
+    over three 128-sample tiles (the last ragged), against the per-layer path on IDENTICAL
+    projection coordinates (the network alone, so that the projection's atomically added
+    partial sums cannot differ between the runs): phi and grad_z Q to 1e-6 (the same
+    arithmetic), Q to 1e-6 (its FP32 row sums run in another order)."""
+    from paper_2305_20053_gb300 import capi
+    n, L, RMb, RUb, Wb, N = 33, 10, 200, 200, 400, 300
+    dz, h = L * L, 1.0 / (n - 1)
+    Ws, bs = glorot_uniform_mlp([RMb + dz, Wb, Wb, Wb, RUb], seed=91)
+    bs = [0.1 * random_state_like(92 + l, b.shape) for l, b in enumerate(bs)]
+    D = capi.Dino(n=n, lattice_L=L, r_m=RMb, r_u=RUb, width=Wb, max_batch=16, max_eval=N)
+    D.ouu_dino_set_params(capi.flatten_params(Ws, bs))
+    D.ouu_dino_set_output_scale(np.linspace(0.05, 0.01, RUb).astype(np.float32))
+    Q, _ = np.linalg.qr(random_state_like(97, ((n - 2) ** 2, RUb)))
+    phi = np.zeros((RUb, n, n))
+    phi[:, 1:-1, 1:-1] = (Q / h).T.reshape(RUb, n - 2, n - 2)
+    ub = np.zeros((n, n))
+    ub[1:-1, 1:-1] = 0.05 * random_state_like(98, (n - 2, n - 2))
+    D.ouu_dino_set_bases(torch.tensor(phi, device="cuda"), torch.tensor(ub, device="cuda"))
+    xi = torch.tensor(random_state_like(99, (N, RMb)).astype(np.float32), device="cuda")
+    z = controls(SEED_EVAL_Z, 1, dz)[0]
+    out = {}
+    for mode in (0, 1, 2):
+        q = torch.empty(N, dtype=torch.float64, device="cuda")
+        gq = torch.empty(N, dz, dtype=torch.float64, device="cuda")
+        ph = torch.empty(N, RUb, dtype=torch.float32, device="cuda")
+        D.ouu_kernel_dino_network(xi, N, z, mode, q, ph, gq)
+        out[mode] = (q.cpu().numpy(), gq.cpu().numpy(), ph.cpu().numpy())
+    q0, g0, p0 = out[0]
+    assert np.all(np.isfinite(q0)) and np.all(np.isfinite(g0)) and np.abs(g0).max() > 0
+    for mode in (1, 2):
+        qm, gm, pm = out[mode]
+        np.testing.assert_allclose(pm, p0, rtol=1e-6, atol=1e-7 * np.abs(p0).max())
+        np.testing.assert_allclose(qm, q0, rtol=1e-6)
+        assert rel(gm, g0) <= 1e-6, (mode, rel(gm, g0))
