@@ -153,6 +153,7 @@ extern "C" ouu_status ouu_batch_create(const ouu_batch_item* items, int n_items,
       risk_dev_finish(rd[r], e.it.n_samples);
     }
     BATCH_CUDA(cudaMemcpy(e.it.problem->d_risks, rd, sizeof(RiskDev) * e.it.n_risks, cudaMemcpyHostToDevice));
+    e.it.problem->rd_n = -1;   // ouu_risk_and_grad's record of the uploaded descriptors is stale
     if (e.it.backend == OUU_BACKEND_DINO) e.dino_pos = (int)b->dino.size() - 1;
   }
   for (int s = 0; s < BATCH_SIDE_STREAMS; ++s) {

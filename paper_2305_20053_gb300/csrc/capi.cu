@@ -400,6 +400,7 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
   if (ouu_status st = check_risks(risks, n_risks)) return st;
   for (int j = 0; j < p->dz; ++j) OUU_CHECK_ARG(std::isfinite(z_host[j]), "z has a non-finite entry");
   RiskDev rd[OUU_MAX_RISKS];
+  std::memset(rd, 0, sizeof(rd));   // padding too: the descriptors are compared bytewise below
   for (int r = 0; r < n_risks; ++r) {
     rd[r].kind = risks[r].kind;
     rd[r].kappa = risks[r].kappa;
@@ -413,10 +414,6 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
   double* d_res = p->d_out;                         // [n_risks][3]
   double* d_grad = p->d_out + 3 * OUU_MAX_RISKS;    // [n_risks][dz]
   int* d_solved = (int*)(p->d_out + OUU_MAX_RISKS * (3 + dz));
-  std::memcpy(p->h_out, z_host, (size_t)dz * 8);
-  OUU_CUDA_TRY(cudaMemcpyAsync(p->d_z, p->h_out, (size_t)dz * 8, cudaMemcpyHostToDevice, p->stream));
-  OUU_CUDA_TRY(cudaMemcpyAsync(p->d_risks, rd, sizeof(RiskDev) * n_risks, cudaMemcpyHostToDevice, p->stream));
-  OUU_CUDA_TRY(cudaStreamSynchronize(p->stream));   // h_out / rd are reused below
   if (backend == OUU_BACKEND_DINO) {
     OUU_CHECK_ARG(dino != nullptr, "DINO backend needs a trained network");
     OUU_CHECK_ARG(dino->n == p->n && dino->dz == p->dz, "problem and network grids differ");
@@ -425,6 +422,25 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
       ouu_set_error("network bases not built");
       return OUU_ERR_STATE;
     }
+  }
+  // The risk descriptors go up on the stream that reads them, and only when they differ from
+  // the last ones sent there (every call ends synchronised, so an upload on the same stream
+  // has been performed).  z: the plain path reads it from d_z (staged in the pinned h_out,
+  // which the results overwrite only later in the same stream); the MR-DINO evaluation copies
+  // it itself.  No synchronisation before the work is enqueued.
+  cudaStream_t us = backend == OUU_BACKEND_DINO ? dino->stream : p->stream;
+  if (n_risks != p->rd_n || us != p->rd_stream || std::memcmp(rd, p->rd_last, sizeof(RiskDev) * n_risks) != 0) {
+    p->rd_n = -1;   // stays invalid if the upload fails
+    OUU_CUDA_TRY(cudaMemcpyAsync(p->d_risks, rd, sizeof(RiskDev) * n_risks, cudaMemcpyHostToDevice, us));
+    std::memcpy(p->rd_last, rd, sizeof(RiskDev) * n_risks);
+    p->rd_n = n_risks;
+    p->rd_stream = us;
+  }
+  if (backend != OUU_BACKEND_DINO) {
+    std::memcpy(p->h_out, z_host, (size_t)dz * 8);
+    OUU_CUDA_TRY(cudaMemcpyAsync(p->d_z, p->h_out, (size_t)dz * 8, cudaMemcpyHostToDevice, p->stream));
+  }
+  if (backend == OUU_BACKEND_DINO) {
     cudaStream_t ds = dino->stream;
     auto enqueue = [&]() -> ouu_status { return dino_enqueue_risk(p, dino, m_dev, n_samples, n_risks, z_host); };
     const bool replay = dino->use_graphs && dino->gexec && dino->gkey_p == p && dino->gkey_m == m_dev &&

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
     fence_async_smem();
   }
   if (warp == KLP_MMA_WARP) tmem_alloc(tslot, 512);
+  if (warp == KLP_PROD_WARP && lane < 2) tmap_prefetch(lane == 0 ? &tm : &tw);
   pdl_wait();
   tc_fence_before();
   __syncthreads();

@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
     fence_async_smem();
   }
   if (warp == MLC_MMA_WARP) tmem_alloc(tslot, MLC_NCMAX);
+  if (warp == MLC_PROD_WARP && lane < 2 * MLC_LAYERS)   // every layer's descriptors, off the critical path
+    tmap_prefetch(lane < MLC_LAYERS ? &P.a[lane] : &P.w[lane - MLC_LAYERS]);
   pdl_wait();
   tc_fence_before();
   __syncthreads();

@@ -214,6 +214,9 @@ struct ouu_problem {
   double* d_s = nullptr;      // [OUU_MAX_RISKS][n*n]
   double* d_out = nullptr;    // results: [OUU_MAX_RISKS][3] + grads [OUU_MAX_RISKS][dz] + misc
   RiskDev* d_risks = nullptr;
+  RiskDev rd_last[OUU_MAX_RISKS];   // host copy of what d_risks holds, uploaded on rd_stream
+  int rd_n = -1;
+  cudaStream_t rd_stream = nullptr;
   double* d_z = nullptr;      // [dz] shared control of the current evaluation
   double* d_rscr = nullptr;   // [OUU_RISK_SCRATCH] risk-weight scratch
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // evaluation phase timers

@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tslot, TMEM_COLS);
+  if (warp == 0 && lane < 2) tmap_prefetch(lane == 0 ? &ta : &tb);
   pdl_wait();   // everything below reads or writes what earlier kernels produce or consume
   for (int i = threadIdx.x; i < BN; i += GEMM_THREADS) {   // per-column epilogue constants
     const int c = n0 + i;

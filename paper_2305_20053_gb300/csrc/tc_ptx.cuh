@@ -127,3 +127,9 @@ static __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, i
   asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x), "r"(y)
                : "memory");
 }
+
+// Fetch a tensor map's descriptor ahead of its first TMA copy (the map lives in kernel
+// parameter space; its generic address is given).
+static __device__ __forceinline__ void tmap_prefetch(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
