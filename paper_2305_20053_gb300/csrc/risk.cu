@@ -486,7 +486,11 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
             th = nt;
           }
           const double KC = K - (double)C;
-          double lo = v - eps, hi = v, t = v - eps * (double)th;
+          // the bracket [lo, hi] and the iterate in order-preserving keys: the bookkeeping (bracket
+          // width in ulps, membership, neighbours, bisection) is integer arithmetic, and the FP64
+          // instructions (each holding the narrow FP64 pipe) are those of G and of the step
+          uint64_t klo = dkey(v - eps), khi = dkey(v);
+          double t = v - eps * (double)th;
           bool lo_neg = false;   // G(lo) < 0 was evaluated
           auto G = [&](double tt, double* dG) {
             double S = 0.0, Sp = 0.0;
@@ -505,13 +509,14 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
           for (int it = 0; it < 64; ++it) {
             double dg;
             const double g = G(t, &dg);
+            const uint64_t kt = dkey(t);
             if (g < 0.0) {
-              lo = t;
+              klo = kt;
               lo_neg = true;
             } else {
-              hi = t;
+              khi = kt;
             }
-            if (hi - lo <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) break;
+            if ((int64_t)(khi - klo) <= 4) break;   // a few ulps wide (or crossed by rounding noise)
             // the Newton step needs a few correct bits only: an FP32 reciprocal of G' (an
             // FP64 division is a long sequence on the narrow FP64 pipe)
             double step = INFINITY;
@@ -519,29 +524,32 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
               const float df = (float)dg;
               step = (df > 1e-30f && df < 1e30f) ? g * (double)(1.0f / df) : g / dg;
             }
-            double nt;
-            if (fabs(step) <= 2.220446049250313e-16 * fabs(t)) {   // converged: bracket t tightly
-              const double a = nextafter(t, -INFINITY), b = nextafter(t, INFINITY);
-              if (G(a, nullptr) < 0.0) {
-                lo = fmax(lo, a);
+            // converged when |step| < 2^-52 |t|: from the exponent fields
+            const int es = (__double2hiint(step) >> 20) & 0x7FF, et = (__double2hiint(t) >> 20) & 0x7FF;
+            uint64_t kn;
+            if (((uint64_t)__double_as_longlong(step) << 1) == 0 || es + 53 <= et) {   // bracket t tightly
+              const uint64_t ka = kt - 1, kb = kt + 1;
+              if (G(dval(ka), nullptr) < 0.0) {
+                klo = ka > klo ? ka : klo;
                 lo_neg = true;
               } else {
-                hi = fmin(hi, a);
+                khi = ka < khi ? ka : khi;
               }
-              if (G(b, nullptr) < 0.0) {
-                lo = fmax(lo, b);
+              if (G(dval(kb), nullptr) < 0.0) {
+                klo = kb > klo ? kb : klo;
                 lo_neg = true;
               } else {
-                hi = fmin(hi, b);
+                khi = kb < khi ? kb : khi;
               }
-              if (hi - lo <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) break;
-              nt = 0.5 * (lo + hi);
+              if ((int64_t)(khi - klo) <= 4) break;
+              kn = klo + (khi - klo) / 2;
             } else {
-              nt = t - step;
-              if (!(nt > lo && nt < hi) || (it >= 8 && it % 2 == 0)) nt = 0.5 * (lo + hi);   // bisect when slow
+              const uint64_t k1 = dkey(t - step);
+              kn = (k1 > klo && k1 < khi && !(it >= 8 && it % 2 == 0)) ? k1 : klo + (khi - klo) / 2;   // bisect when slow
             }
-            t = nt;
+            t = dval(kn);
           }
+          const double lo = dval(klo), hi = dval(khi);
           // bisection end rule: lo if G(lo) >= 0 (possible only for the unevaluated v - eps), else hi
           const bool take_lo = !lo_neg && G(lo, nullptr) >= 0.0;
           if (lane == 0) s_par[5] = take_lo ? lo : hi;
@@ -577,7 +585,7 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
 // two-sum, so each thread's total carries about 44 bits and only the totals are FP64.
 // The last block to finish (an arrival counter, reset for the next call) combines the
 // partial sums into the risk values and d rho / dt.  out[3r..3r+2] = value, dt, t.
-#define APPLY_SUB 128
+#define APPLY_W 256   // samples of a block whose weights sit in shared memory at a time
 static __device__ __forceinline__ void ff_add_prod(float& sh, float& sl, float wh, float wl, float g) {
   const float p = wh * g;
   float e = fmaf(wh, g, -p);   // wh g = p + e exactly
@@ -589,6 +597,17 @@ static __device__ __forceinline__ void ff_add_prod(float& sh, float& sl, float w
   sl += err + e;
 }
 
+// Thread (g, jl) of the gradient sum: column j of samples s0 + kg + g + 2k, k < 16 (one batch of
+// loads in flight instead of one round trip per sample).
+static __device__ __forceinline__ void load_grad_group(float (&gv)[16], const float* __restrict__ gq, int ldg, int dz,
+                                                       int s0, int s1, int kg, int g, int j) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int i = s0 + kg + g + 2 * k;
+    gv[k] = (i < s1 && j < dz) ? __ldg(gq + (int64_t)i * ldg + j) : 0.f;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q, int N,
                                                     const RiskDev* __restrict__ risks, int n_risks,
                                                     const double* __restrict__ params, double* __restrict__ w,
@@ -596,18 +615,22 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
                                                     double* __restrict__ out, const float* __restrict__ gq, int ldg,
                                                     int dz, double* __restrict__ grad_out) {
   __shared__ bool last;
-  __shared__ float wsh[OUU_MAX_RISKS][APPLY_SUB], wsl[OUU_MAX_RISKS][APPLY_SUB];
+  __shared__ float wsh[OUU_MAX_RISKS][APPLY_W], wsl[OUU_MAX_RISKS][APPLY_W];
   __shared__ double gsum[OUU_MAX_RISKS][128];
   __shared__ double buf[2 * 256 + 2];
   pdl_wait();
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int i0 = min(N, (int)blockIdx.x * chunk), i1 = min(N, i0 + chunk);
+  const int g = threadIdx.x >> 7, jl = threadIdx.x & 127;   // two sample parities x 128 columns
   double sv[OUU_MAX_RISKS], sd[OUU_MAX_RISKS];
 #pragma unroll
   for (int r = 0; r < OUU_MAX_RISKS; ++r) sv[r] = sd[r] = 0.0;
-  for (int s0 = i0; s0 < i1; s0 += APPLY_SUB) {
-    const int s1 = min(i1, s0 + APPLY_SUB);
-    for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+  for (int s0 = i0; s0 < i1; s0 += APPLY_W) {
+    const int s1 = min(i1, s0 + APPLY_W), ns = s1 - s0;
+    float gv[16];
+    if (gq) load_grad_group(gv, gq, ldg, dz, s0, s1, 0, g, jl);   // in flight during the weights
+    const int i = s0 + threadIdx.x;
+    if (i < s1) {
       const double qi = q[i];
 #pragma unroll
       for (int r = 0; r < OUU_MAX_RISKS; ++r) {
@@ -627,26 +650,29 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
         w[(int64_t)r * N + i] = wi;
         if (gq) {
           const float wh = (float)wi;
-          wsh[r][i - s0] = wh;
-          wsl[r][i - s0] = (float)(wi - (double)wh);
+          wsh[r][threadIdx.x] = wh;
+          wsl[r][threadIdx.x] = (float)(wi - (double)wh);
         }
       }
     }
     if (gq) {
-      __syncthreads();
-      const int g = threadIdx.x >> 7, jl = threadIdx.x & 127;   // two sample halves x 128 columns
+      __syncthreads();   // the weights of the sub-range are in shared memory
       for (int jb = 0; jb < dz; jb += 128) {
         const int j = jb + jl;
         float sh[OUU_MAX_RISKS], sl[OUU_MAX_RISKS];
 #pragma unroll
         for (int r = 0; r < OUU_MAX_RISKS; ++r) sh[r] = sl[r] = 0.f;
-        if (j < dz && g < 2)
-          for (int i = s0 + g; i < s1; i += 2) {
-            const float gv = gq[(int64_t)i * ldg + j];
+        for (int kg = 0; kg < ns; kg += 32) {
+          if (jb > 0 || kg > 0) load_grad_group(gv, gq, ldg, dz, s0, s1, kg, g, j);
 #pragma unroll
-            for (int r = 0; r < OUU_MAX_RISKS; ++r)
-              if (r < n_risks) ff_add_prod(sh[r], sl[r], wsh[r][i - s0], wsl[r][i - s0], gv);
+          for (int k = 0; k < 16; ++k) {
+            const int ii = kg + g + 2 * k;
+            if (ii < ns)
+#pragma unroll
+              for (int r = 0; r < OUU_MAX_RISKS; ++r)
+                if (r < n_risks) ff_add_prod(sh[r], sl[r], wsh[r][ii], wsl[r][ii], gv[k]);
           }
+        }
         if (g == 1)
 #pragma unroll
           for (int r = 0; r < OUU_MAX_RISKS; ++r)
@@ -659,10 +685,9 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
         __syncthreads();
       }
     }
-    __syncthreads();
   }
-  // threads that held samples: [0, min(range, APPLY_SUB))
-  const int nact = min(i1 - i0, APPLY_SUB);
+  // threads that held samples: [0, min(range, APPLY_W))
+  const int nact = min(i1 - i0, APPLY_W);
 #pragma unroll
   for (int r = 0; r < OUU_MAX_RISKS; ++r) {
     if (r >= n_risks) break;
