@@ -316,7 +316,8 @@ static void free_dino(ouu_dino* d) {
   void* ptrs[] = {d->d_params, d->d_grad, d->d_adam_m, d->d_adam_v, d->d_phi, d->d_phi64, d->d_ubar, d->d_ut,
                   d->d_c, d->d_cf, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
                   d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
-                  d->Ge, d->GQe, d->Qe, d->Qpart, d->d_zf, d->d_err, d->d_gov, d->d_oscale, d->d_klbias};
+                  d->Ge, d->GQe, d->Qe, d->Qpart, d->d_zf, d->d_err, d->d_klp_ctr, d->d_gov, d->d_oscale,
+                  d->d_klbias};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < 4; ++l) {
     cudaFree(d->A[l]);
@@ -445,6 +446,7 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   al((void**)&d->Qpart, E * 4 * 4);
   al((void**)&d->d_zf, std::max<size_t>(maxB, 1) * d->dz * 4 + 64);
   al((void**)&d->d_err, 16);
+  al((void**)&d->d_klp_ctr, (OUU_KLP_MAX_TILES + 1) * sizeof(int));   // zeroed by al()
   if (ok && cudaMallocHost((void**)&d->h_pin, (size_t)(4 * 3 + 4 * d->dz + 64) * 8 + 4096) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();
@@ -587,7 +589,8 @@ static ouu_status check_err(ouu_dino* d) {
 static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi, bool mark = false) {
   // one fused pass over the FP64 fields (kl_project.cu); the bias -W mbar carries the prior mean
   if (mark && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
-  DINO_TRY(ouu_kl_project(m, count, d->nn, d->d_wkl, d->nnp, d->rm, d->d_klbias, xi, d->d_err, d->num_sms, d->stream));
+  DINO_TRY(ouu_kl_project(m, count, d->nn, d->d_wkl, d->nnp, d->rm, d->d_klbias, xi, d->d_err, d->d_klp_ctr,
+                          d->num_sms, d->stream));
   if (mark && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
   return OUU_OK;
 }

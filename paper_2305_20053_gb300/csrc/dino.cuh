@@ -61,6 +61,7 @@ struct ouu_dino {
   float* d_zf = nullptr;           // [max(maxB, 1) * dz] FP32 controls of the current call
   double* h_pin = nullptr;         // pinned host scratch
   int* d_err = nullptr;
+  int* d_klp_ctr = nullptr;        // [OUU_KLP_MAX_TILES] tile counters of the KL projection
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // cast | projection | network phase marks
   // CUDA graph of the risk evaluation (captured on a private stream, replayed on `stream`)
   cudaStream_t cap = nullptr;
@@ -100,7 +101,11 @@ ouu_status dino_install_bases(ouu_dino* d);
 // Jacobian-data solves (pde.cu): jy[i][j][r] = h^2 Phi_r . J(u_i)^-1 g_j.
 // Fused KL projection of FP64 fields (kl_project.cu): xi[N][rm] = bf16(m) W^T + bias with
 // W = [rm][ldw] BF16 (K = nn contiguous); xi is zeroed here.  m 8-byte aligned, rm <= 240.
+// ctr: device scratch of OUU_KLP_MAX_TILES + 1 ints, zero before the first call (the per-tile
+// unit counters and an arrival count; each launch leaves them zero); N above
+// OUU_KLP_MAX_TILES * 128 runs as several launches.
+#define OUU_KLP_MAX_TILES 512
 ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W, int ldw, int rm, const float* bias,
-                          float* xi, int* err, int num_sms, cudaStream_t s);
+                          float* xi, int* err, int* ctr, int num_sms, cudaStream_t s);
 
 void launch_pde_jacobian_data(const PdeArgs& a, int nslots, const float* phi, int ru, float* jy, cudaStream_t s);

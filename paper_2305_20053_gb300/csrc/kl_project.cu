@@ -1,30 +1,35 @@
 // Fused KL projection (Sec. 3.3, the input reduction of the reduced-basis network):
 //   xi[s][c] = bias[c] + sum_k bf16(m[s][k]) * W[c][k],   s < N, c < r_m,
-// reading the FP64 fields once.  One persistent CTA per SM; the (128-sample tile, 64-wide
-// K block) units are dealt to the CTAs in equal contiguous ranges ("stream-K"), so every
-// SM streams the same number of bytes whatever N and n^2 are.  Per CTA:
-//   warp 16      : field producer.  Per K block, TMA loads of the FP64 slice
-//                  m[tile rows][k0, k0+64).  With n^2 odd the row stride n^2 * 8 bytes is
-//                  not a multiple of 16, which a tensor map needs; the fields are then read
-//                  as rows of sample PAIRS (stride 2 n^2 * 8 bytes), even samples from
-//                  x = k0 and odd samples from x = n^2 + k0 - 1 (one element early, so that
-//                  x stays 16-byte aligned), 66 elements each: two copies per K block.  A
-//                  last unpaired sample (N odd), and every sample when the base is not
-//                  16-byte aligned, is read with plain loads.
-//   warp 22      : basis producer.  TMA loads of the BF16 basis block W[0, BN) x [k0, k0+64)
-//                  (128-byte swizzle), paced by the MMA instead of by the field copies.
+// reading the FP64 fields once.  One persistent CTA per SM over the units (128-sample tile,
+// 64-wide K block).  The units are claimed at run time, one at a time, from a counter per
+// tile: a CTA keeps claiming K blocks of its tile (accumulating them in one TMEM accumulator,
+// flushed once per tile visit) and, when the tile runs out, moves to the tile with the most K
+// blocks left; the CTAs start spread evenly over the tiles.  So every SM streams for as long
+// as there is work, whatever its share of DRAM bandwidth, and all finish within about one
+// unit of each other.  Per CTA:
+//   warp 16      : field producer.  Claims the units (one ahead, to know where a tile visit
+//                  ends), publishes each in a shared ring, and TMA-loads the FP64 slice
+//                  m[tile rows][k0, k0+64).  With n^2 odd the row stride n^2 * 8 bytes is not a
+//                  multiple of 16, which a tensor map needs; the fields are then read as rows
+//                  of sample PAIRS (stride 2 n^2 * 8 bytes), even samples from x = k0 and odd
+//                  samples from x = n^2 + k0 - 1 (one element early, so that x stays 16-byte
+//                  aligned), 66 elements each: two copies per K block.  A last unpaired sample
+//                  (N odd), and every sample when the base is not 16-byte aligned, is read with
+//                  plain loads.
 //   warps 0..15  : converters.  Each copies its 8 rows of the FP64 stage into registers and
 //                  releases the stage at once (the next field copy then overlaps the
 //                  arithmetic), then converts FP64 -> BF16 (round to FP32, then to BF16,
 //                  both to nearest even; the first step in integer arithmetic, as the FP64
 //                  pipe is narrow) straight into the swizzled K-major A tile that
-//                  tcgen05.mma reads.
+//                  tcgen05.mma reads.  Warp 0 also loads the unit's BF16 basis block
+//                  W[0, BN) x [k0, k0 + 64) (128-byte swizzle) once its stage is free.
 //   warp 17      : tcgen05.mma issuer (M = 128, N = BN, K = 16 per instruction) into one of
-//                  two TMEM accumulators; allocates and frees the tensor memory.
-//   warps 18..21 : epilogue.  TMEM -> registers, + bias on the unit range that holds K block
-//                  0 of its tile, 16-byte atomic adds into xi (zeroed beforehand).
-// Every mbarrier wait is bounded; on a timeout the CTA stops, drains its own copies and
-// raises *err.
+//                  two TMEM accumulators (one per tile visit); allocates and frees the tensor
+//                  memory; hands each visit's (tile, holds K block 0) to the epilogue.
+//   warps 18..21 : epilogue.  TMEM -> registers, + bias on the visit that holds K block 0 of
+//                  its tile, 16-byte atomic adds into xi (zeroed beforehand).
+// Every mbarrier wait is bounded; on a timeout the CTA publishes the end of its units, stops,
+// drains its own copies and raises *err.
 #include <cuda_bf16.h>
 
 #include "dino.cuh"
@@ -36,8 +41,8 @@
 #define KLP_PROD_WARP 16
 #define KLP_MMA_WARP 17
 #define KLP_EPI_WARP0 18
-#define KLP_BPROD_WARP 22
-#define KLP_THREADS (23 * 32)
+#define KLP_THREADS (22 * 32)
+#define KLP_RING 16                          // published units (the MMA lags the producer by < 8)
 #define KLP_ROWS_PER_WARP (128 / KLP_CONV_WARPS)
 #define KLP_ROW_BYTES 528                    // pair mode: 66 doubles per sample row
 #define KLP_F64_STAGE (128 * KLP_ROW_BYTES)
@@ -49,7 +54,9 @@ struct KlpArgs {
   int N, nn, KBt, BN, rm;
   int pair;        // 1: fields read as sample pairs (n^2 odd); 0: as rows (n^2 even)
   int n_tma;       // samples [0, n_tma) come by TMA, the rest (at most one) by plain loads
-  long long U;
+  int T;           // 128-sample tiles
+  int* ctr;        // [T] next unclaimed K block of each tile, [T] CTAs finished; zero at launch and
+                   // left zero by the last CTA
   const float* bias;
   float* xi;
   int* err;
@@ -120,6 +127,8 @@ static __device__ __forceinline__ float f64_to_f32_rne(double x) {
   return __uint_as_float(f);
 }
 
+// A published unit: x = tile (< 0: no more units), y = K block | first << 16 | last << 17
+// (first / last unit of a tile visit).
 __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_constant__ CUtensorMap tw,
                                                                 const __grid_constant__ CUtensorMap tm, KlpArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -129,25 +138,22 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
   uint8_t* sB = sA + 2 * KLP_A_STAGE;
   uint8_t* sF = sB + 2 * B_BYTES;
   uint64_t* bars = (uint64_t*)(sF + 2 * KLP_F64_STAGE);
-  uint64_t* f64_full = bars + 0;    // producer: field copies landed
-  uint64_t* f64_empty = bars + 2;   // converters: FP64 stage consumed
-  uint64_t* b_full = bars + 4;      // producer: basis block landed
+  uint64_t* f64_full = bars + 0;    // producer: unit published (and its field copies landed)
+  uint64_t* f64_empty = bars + 2;   // converters: FP64 stage in registers
+  uint64_t* b_full = bars + 4;      // converter warp 0: basis block landed
   uint64_t* a_full = bars + 6;      // converters: BF16 A tile written
   uint64_t* ab_empty = bars + 8;    // MMA: A and B stages consumed
   uint64_t* acc_full = bars + 10;   // MMA: accumulator complete
   uint64_t* acc_empty = bars + 12;  // epilogue: accumulator drained
-  uint64_t* mma_done = bars + 14;
-  uint32_t* tslot = (uint32_t*)(bars + 16);
+  uint64_t* seg_full = bars + 14;   // MMA: tile-visit descriptor written
+  uint64_t* mma_done = bars + 16;
+  uint32_t* tslot = (uint32_t*)(bars + 17);
+  __shared__ int2 s_unit[KLP_RING];
+  __shared__ int2 s_seg[2];         // (tile, holds K block 0); tile < 0: no more visits
   __shared__ volatile int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long u0 = (long long)blockIdx.x * a.U / gridDim.x;
-  const long long u1 = (long long)(blockIdx.x + 1) * a.U / gridDim.x;
-  const int nj = (int)(u1 - u0);
   const int nn = a.nn, KBt = a.KBt, N = a.N;
-  // unit u0 + j is (tile t, K block kb); every role steps (t, kb) along with j instead of
-  // dividing
-  const int t_first = (int)(u0 / KBt), kb_first = (int)(u0 % KBt);
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -159,6 +165,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
       mbar_init(&ab_empty[i], 1);
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], 4);
+      mbar_init(&seg_full[i], 1);
     }
     mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -174,67 +181,127 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
 
   if (warp == KLP_PROD_WARP) {
     // ---------------------------------------------------------------- field producer
-    if (lane == 0) {
-      int issued = 0;
-      bool ok = true;
-      const uint32_t fbytes = a.pair ? 2u * KLP_HALF : 128u * 512u;
-      for (int j = 0, t = t_first, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1, t += kb == 0) {
-        const int k0 = kb * 64, s = j & 1;
-        const uint32_t ph = (uint32_t)(j >> 1) & 1u;
-        if (j >= 2 && !mbar_wait(&f64_empty[s], ph ^ 1u)) {
-          ok = false;
-          break;
+    int cur = (int)(((long long)blockIdx.x * a.T) / gridDim.x);   // the tile claimed from
+    // The tile with the most K blocks left (the warp's lanes scan the counters; the lowest
+    // index among equals); false when every tile is done.
+    auto next_tile = [&]() -> bool {
+      int best = 0x7FFFFFFF, left = 0;
+      for (int t0 = 0; t0 < a.T; t0 += 32) {
+        const int t = t0 + lane;
+        const int l = t < a.T ? KBt - *(volatile int*)(a.ctr + t) : 0;
+        if (l > left) {
+          left = l;
+          best = t;
         }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const int ol = __shfl_xor_sync(0xffffffffu, left, o), ob = __shfl_xor_sync(0xffffffffu, best, o);
+        if (ol > left || (ol == left && ob < best)) {
+          left = ol;
+          best = ob;
+        }
+      }
+      if (left <= 0) return false;
+      cur = best;
+      return true;
+    };
+    // A claimed K block kb of tile cur (kb from the counter, possibly past the end): true with
+    // the unit if valid, else moves to another tile and claims there, synchronously.
+    auto settle = [&](int kb, int& t_out, int& kb_out) -> bool {
+      for (int tries = 0; tries < 4 * a.T + 8; ++tries) {
+        if (kb < KBt) {
+          t_out = cur;
+          kb_out = kb;
+          return true;
+        }
+        if (!next_tile()) return false;
+        kb = 0;
+        if (lane == 0) kb = atomicAdd(&a.ctr[cur], 1);
+        kb = __shfl_sync(0xffffffffu, kb, 0);
+      }
+      return false;
+    };
+    // Claim pipeline: unit j (t_cur, kb_cur) and unit j + 1 (t_nxt, kb_nxt) resolved, the
+    // counter increment for the one after in flight, so that its latency overlaps the wait
+    // for a free stage.  The first claim takes two K blocks at once.
+    int t_cur = 0, kb_cur = 0, t_nxt = -1, kb_nxt = 0, pend = 0, prev_t = -1, j = 0;
+    bool have, have_nxt;
+    {
+      int k2 = 0;
+      if (lane == 0) k2 = atomicAdd(&a.ctr[cur], 2);
+      k2 = __shfl_sync(0xffffffffu, k2, 0);
+      have = settle(k2, t_cur, kb_cur);
+      if (have && t_cur == cur && k2 + 1 < KBt && kb_cur == k2) {
+        t_nxt = cur;
+        kb_nxt = k2 + 1;
+        have_nxt = true;
+      } else {
+        int k1 = 0;
+        if (have && lane == 0) k1 = atomicAdd(&a.ctr[cur], 1);
+        k1 = __shfl_sync(0xffffffffu, k1, 0);
+        have_nxt = have && settle(k1, t_nxt, kb_nxt);
+      }
+    }
+    if (have_nxt && lane == 0) pend = atomicAdd(&a.ctr[cur], 1);
+    bool ok = true;
+    const uint32_t fbytes = a.pair ? 2u * KLP_HALF : 128u * 512u;
+    for (;; ++j) {
+      const int s = j & 1;
+      if (j >= 2 && !__all_sync(0xffffffffu, mbar_wait(&f64_empty[s], (((uint32_t)j >> 1) & 1u) ^ 1u) ? 1 : 0))
+        ok = false;
+      const bool pub = have && ok;   // on a timeout the end is published instead
+      if (lane == 0) {
+        s_unit[j & (KLP_RING - 1)] =
+            pub ? make_int2(t_cur, kb_cur | ((t_cur != prev_t) << 16) | ((!have_nxt || t_nxt != t_cur) << 17))
+                : make_int2(-1, 0);
         uint8_t* dst = sF + s * KLP_F64_STAGE;
-        if (a.n_tma == 0) {
-          mbar_arrive(&f64_full[s]);   // plain loads only
+        if (!pub || a.n_tma == 0) {
+          mbar_arrive(&f64_full[s]);   // the end, or plain loads only
         } else if (a.pair) {
           mbar_expect_tx(&f64_full[s], fbytes);
-          tma_load_2d(dst, &tm, k0, t * 64, &f64_full[s]);
-          tma_load_2d(dst + KLP_HALF, &tm, nn + k0 - 1, t * 64, &f64_full[s]);
+          tma_load_2d(dst, &tm, kb_cur * 64, t_cur * 64, &f64_full[s]);
+          tma_load_2d(dst + KLP_HALF, &tm, nn + kb_cur * 64 - 1, t_cur * 64, &f64_full[s]);
         } else {
           mbar_expect_tx(&f64_full[s], fbytes);
-          tma_load_2d(dst, &tm, k0, t * 128, &f64_full[s]);
+          tma_load_2d(dst, &tm, kb_cur * 64, t_cur * 128, &f64_full[s]);
         }
-        issued = j + 1;
       }
-      if (!ok) s_fail = 1;
-      // drain: the copies into both stages must have landed before the CTA exits
-      for (int j = max(0, issued - 2); j < issued; ++j)
-        if (!mbar_wait(&f64_full[j & 1], (uint32_t)(j >> 1) & 1u)) s_fail = 1;
+      if (!pub) break;
+      prev_t = t_cur;
+      t_cur = t_nxt;
+      kb_cur = kb_nxt;
+      have = have_nxt;
+      if (have_nxt) {   // resolve the claim in flight, start the next
+        have_nxt = settle(__shfl_sync(0xffffffffu, pend, 0), t_nxt, kb_nxt);
+        if (have_nxt && lane == 0) pend = atomicAdd(&a.ctr[cur], 1);
+      }
     }
-  } else if (warp == KLP_BPROD_WARP) {
-    // ---------------------------------------------------------------- basis producer
+    // drain: the copies of the last published units have landed before the CTA exits
     if (lane == 0) {
-      int issued = 0;
-      bool ok = true;
-      for (int j = 0, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1) {
-        const int k0 = kb * 64, s = j & 1;
-        const uint32_t ph = (uint32_t)(j >> 1) & 1u;
-        if (j >= 2 && !mbar_wait(&ab_empty[s], ph ^ 1u)) {
-          ok = false;
-          break;
-        }
-        mbar_expect_tx(&b_full[s], B_BYTES);
-        tma_load_2d(sB + s * B_BYTES, &tw, k0, 0, &b_full[s]);
-        issued = j + 1;
-      }
       if (!ok) s_fail = 1;
-      for (int j = max(0, issued - 2); j < issued; ++j)
-        if (!mbar_wait(&b_full[j & 1], (uint32_t)(j >> 1) & 1u)) s_fail = 1;
+      for (int u = max(0, j - 1); u <= j; ++u)
+        if (!mbar_wait(&f64_full[u & 1], ((uint32_t)u >> 1) & 1u)) s_fail = 1;
     }
   } else if (warp < KLP_CONV_WARPS) {
     // ---------------------------------------------------------------- converters
     // Lane l owns columns 2l and 2l + 1 of the warp's 8 rows: one 16-byte shared load per
     // row, and its two BF16 values form one 32-bit word of the A tile.
     const int r0 = warp * KLP_ROWS_PER_WARP;
-    for (int j = 0, t = t_first, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1, t += kb == 0) {
-      const int k0 = kb * 64, s = j & 1;
+    for (int j = 0;; ++j) {
+      const int s = j & 1;
       const uint32_t ph = (uint32_t)(j >> 1) & 1u;
       if (!__all_sync(0xffffffffu, mbar_wait(&f64_full[s], ph) ? 1 : 0)) {
         if (lane == 0) s_fail = 1;
         break;
       }
+      const int2 e = s_unit[j & (KLP_RING - 1)];
+      if (e.x < 0) {   // no more units: the MMA issuer learns it through a_full
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_full[s]);
+        break;
+      }
+      const int t = e.x, k0 = (e.y & 0xFFFF) * 64;
       const uint8_t* fst = sF + s * KLP_F64_STAGE;
       const int rb = t * 128 + r0;   // the warp's first sample
       double x0[KLP_ROWS_PER_WARP], x1[KLP_ROWS_PER_WARP];
@@ -261,6 +328,10 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
       if (j >= 2 && !__all_sync(0xffffffffu, mbar_wait(&ab_empty[s], ph ^ 1u) ? 1 : 0)) {
         if (lane == 0) s_fail = 1;
         break;
+      }
+      if (warp == 0 && lane == 0) {   // the unit's basis block into the freed stage
+        mbar_expect_tx(&b_full[s], B_BYTES);
+        tma_load_2d(sB + s * B_BYTES, &tw, k0, 0, &b_full[s]);
       }
       uint8_t* ast = sA + s * KLP_A_STAGE;
       // 128-byte swizzle: 16-byte chunk index XOR (row mod 8) within the 8-row atom;
@@ -295,17 +366,31 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.BN >> 3) << 17) | ((128u >> 4) << 24);
-      int seg = 0, issued_any = 0;
-      for (int j = 0, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1) {
+      int seg = 0, seg_t = -1, has0 = 0;
+      bool ok = true, any = false;
+      for (int j = 0;; ++j) {
         const int s = j & 1;
         const uint32_t ph = (uint32_t)(j >> 1) & 1u;
-        const bool first = j == 0 || kb == 0, last = j == nj - 1 || kb == KBt - 1;
+        if (!mbar_wait(&a_full[s], ph)) {
+          ok = false;
+          break;
+        }
+        const int2 e = s_unit[j & (KLP_RING - 1)];
+        if (e.x < 0) break;
+        const int kb = e.y & 0xFFFF;
+        const bool first = (e.y >> 16) & 1, last = (e.y >> 17) & 1;
         const int acc = seg & 1;
-        bool ok = true;
-        if (first && seg >= 2) ok = mbar_wait(&acc_empty[acc], (uint32_t)((seg >> 1) - 1) & 1u);
-        ok = ok && mbar_wait(&a_full[s], ph) && mbar_wait(&b_full[s], ph);
-        if (!ok) {
-          s_fail = 1;
+        if (first) {
+          if (seg >= 2 && !mbar_wait(&acc_empty[acc], (uint32_t)((seg >> 1) - 1) & 1u)) {
+            ok = false;
+            break;
+          }
+          seg_t = e.x;
+          has0 = 0;
+        }
+        has0 |= kb == 0;
+        if (!mbar_wait(&b_full[s], ph)) {
+          ok = false;
           break;
         }
         tc_fence_after();
@@ -315,14 +400,22 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
           tc_mma(tmem + (uint32_t)acc * 256u, smem_desc_sw128(a0 + k * 32), smem_desc_sw128(b0 + k * 32), idesc,
                  (!first || k > 0) ? 1u : 0u);
         tc_commit(&ab_empty[s]);
-        issued_any = 1;
+        any = true;
         if (last) {
           tc_commit(&acc_full[acc]);
+          s_seg[acc] = make_int2(seg_t, has0);
+          mbar_arrive(&seg_full[acc]);
           ++seg;
         }
       }
+      if (!ok) s_fail = 1;
+      // the end of the visits, in the slot whose last descriptor the epilogue has read
+      const int acc = seg & 1;
+      if (seg >= 2 && !mbar_wait(&acc_empty[acc], (uint32_t)((seg >> 1) - 1) & 1u)) s_fail = 1;
+      s_seg[acc] = make_int2(-1, 0);
+      mbar_arrive(&seg_full[acc]);
       // every MMA issued above has completed before the tensor memory is freed
-      if (issued_any) {
+      if (any) {
         tc_commit(mma_done);
         if (!mbar_wait(mma_done, 0)) s_fail = 1;
       }
@@ -330,17 +423,21 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
   } else {
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;
-    int seg = 0, first_kb = 0;
-    for (int j = 0, t = t_first, kb = kb_first; j < nj; ++j, kb = kb + 1 == KBt ? 0 : kb + 1, t += kb == 0) {
-      if (j == 0 || kb == 0) first_kb = kb;
-      if (!(j == nj - 1 || kb == KBt - 1)) continue;
-      const int acc = seg & 1;
-      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[acc], (uint32_t)(seg >> 1) & 1u) ? 1 : 0)) {
+    for (int k = 0;; ++k) {
+      const int acc = k & 1;
+      const uint32_t ph = (uint32_t)(k >> 1) & 1u;
+      if (!__all_sync(0xffffffffu, mbar_wait(&seg_full[acc], ph) ? 1 : 0)) {
+        if (lane == 0) s_fail = 1;
+        break;
+      }
+      const int2 d = s_seg[acc];
+      if (d.x < 0) break;
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[acc], ph) ? 1 : 0)) {
         if (lane == 0) s_fail = 1;
         break;
       }
       tc_fence_after();
-      const int r = t * 128 + q * 32 + lane;
+      const int r = d.x * 128 + q * 32 + lane;
       float* orow = a.xi + (size_t)r * a.rm;
       const bool vec4 = (a.rm & 3) == 0;
       for (int c0 = 0; c0 < a.BN; c0 += 16) {
@@ -354,7 +451,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
             float y[4];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
-              y[jj] = __uint_as_float(v[i + jj]) + ((first_kb == 0 && c + jj < a.rm) ? a.bias[c + jj] : 0.f);
+              y[jj] = __uint_as_float(v[i + jj]) + ((d.y && c + jj < a.rm) ? a.bias[c + jj] : 0.f);
             if (vec4) {
               atomicAdd(reinterpret_cast<float4*>(orow + c), make_float4(y[0], y[1], y[2], y[3]));
             } else {
@@ -366,7 +463,6 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[acc]);
-      ++seg;
     }
   }
   tc_fence_before();
@@ -375,20 +471,18 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
-  if (threadIdx.x == 0 && s_fail) atomicExch(a.err, 1);
+  if (threadIdx.x == 0) {
+    if (s_fail) atomicExch(a.err, 1);
+    // the last CTA to finish (nobody claims any more) leaves the counters zero for the next launch
+    if (atomicAdd(a.ctr + a.T, 1) == (int)gridDim.x - 1) {
+      for (int t = 0; t <= a.T; ++t) *(volatile int*)(a.ctr + t) = 0;
+    }
+  }
 }
 
-ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W, int ldw, int rm, const float* bias,
-                          float* xi, int* err, int num_sms, cudaStream_t s) {
-  OUU_CHECK_ARG(m && W && bias && xi && err, "null argument");
-  OUU_CHECK_ARG(N >= 1 && nn >= 1 && rm >= 1 && rm <= 240, "KL projection sizes: N, n^2 >= 1, 1 <= r_m <= 240");
-  OUU_CHECK_ARG(((uintptr_t)m & 7) == 0, "fields must be 8-byte aligned");
-  const int BN = (rm + 15) / 16 * 16;
-  CUtensorMap tw;
-  if (!ouu_tmap_bf16(&tw, W, (uint64_t)nn, (uint64_t)rm, (uint64_t)ldw, (uint32_t)BN)) {
-    ouu_set_error("tensor map for the KL basis failed (alignment or driver entry point)");
-    return OUU_ERR_INVALID_ARG;
-  }
+// One launch over N <= OUU_KLP_MAX_TILES * 128 samples.
+static ouu_status kl_project_launch(const double* m, int N, int nn, const CUtensorMap& tw, int BN, int rm,
+                                    const float* bias, float* xi, int* err, int* ctr, int num_sms, cudaStream_t s) {
   // fields tensor map: sample rows (n^2 even) or sample pairs (n^2 odd)
   // A base that is not 16-byte aligned (a slice starting at an odd sample) cannot be a
   // tensor map's base: every row then goes by plain loads.
@@ -416,19 +510,44 @@ ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W
   a.KBt = (nn + 63) / 64;
   a.BN = BN;
   a.rm = rm;
-  a.U = (long long)((N + 127) / 128) * a.KBt;
+  a.T = (N + 127) / 128;
+  a.ctr = ctr;
   a.bias = bias;
   a.xi = xi;
   a.err = err;
-  const size_t smem = 1024 + 2 * KLP_A_STAGE + 2 * (size_t)BN * 128 + 2 * KLP_F64_STAGE + 16 * 8 + 16;
+  const size_t smem = 1024 + 2 * KLP_A_STAGE + 2 * (size_t)BN * 128 + 2 * KLP_F64_STAGE + 17 * 8 + 16;
   static size_t attr = 0;   // one device per process is the supported set-up
   if (attr < smem) {
     OUU_CUDA_TRY(cudaFuncSetAttribute((const void*)k_kl_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
-  const int grid = (int)std::min<long long>(a.U, (long long)std::max(1, num_sms));
+  const long long U = (long long)a.T * a.KBt;
+  const int grid = (int)std::min<long long>(U, (long long)std::max(1, num_sms));
   OUU_CUDA_TRY(cudaMemsetAsync(xi, 0, (size_t)N * rm * 4, s));
   OUU_CUDA_TRY(launch_pdl(k_kl_project, dim3(grid), dim3(KLP_THREADS), smem, s, tw, tm, a));
+  return OUU_OK;
+}
+
+ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W, int ldw, int rm, const float* bias,
+                          float* xi, int* err, int* ctr, int num_sms, cudaStream_t s) {
+  OUU_CHECK_ARG(m && W && bias && xi && err && ctr, "null argument");
+  OUU_CHECK_ARG(N >= 1 && nn >= 1 && rm >= 1 && rm <= 240, "KL projection sizes: N, n^2 >= 1, 1 <= r_m <= 240");
+  OUU_CHECK_ARG(((uintptr_t)m & 7) == 0, "fields must be 8-byte aligned");
+  const int BN = (rm + 15) / 16 * 16;
+  CUtensorMap tw;
+  if (!ouu_tmap_bf16(&tw, W, (uint64_t)nn, (uint64_t)rm, (uint64_t)ldw, (uint32_t)BN)) {
+    ouu_set_error("tensor map for the KL basis failed (alignment or driver entry point)");
+    return OUU_ERR_INVALID_ARG;
+  }
+  // chunks of at most OUU_KLP_MAX_TILES tiles (one tile counter each); a chunk's first sample
+  // is a multiple of 128, so its base keeps the fields' 16-byte alignment
+  const int chunk = OUU_KLP_MAX_TILES * 128;
+  for (int n0 = 0; n0 < N; n0 += chunk) {
+    const int nc = std::min(chunk, N - n0);
+    if (ouu_status st = kl_project_launch(m + (size_t)n0 * nn, nc, nn, tw, BN, rm, bias, xi + (size_t)n0 * rm, err,
+                                          ctr, num_sms, s))
+      return st;
+  }
   return OUU_OK;
 }
 
@@ -438,5 +557,10 @@ extern "C" ouu_status ouu_kernel_kl_project(const double* m, int N, int nn, cons
   int dev = 0, sms = 0;
   OUU_CUDA_TRY(cudaGetDevice(&dev));
   OUU_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  return ouu_kl_project(m, N, nn, (const __nv_bfloat16*)W, ldw, rm, bias, xi, err_dev, sms, (cudaStream_t)stream);
+  static int* ctr = nullptr;   // tile counters of this entry (one device per process)
+  if (!ctr) {
+    OUU_CUDA_TRY(cudaMalloc((void**)&ctr, (OUU_KLP_MAX_TILES + 1) * sizeof(int)));
+    OUU_CUDA_TRY(cudaMemset(ctr, 0, (OUU_KLP_MAX_TILES + 1) * sizeof(int)));
+  }
+  return ouu_kl_project(m, N, nn, (const __nv_bfloat16*)W, ldw, rm, bias, xi, err_dev, ctr, sms, (cudaStream_t)stream);
 }
