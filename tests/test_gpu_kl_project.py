@@ -71,3 +71,35 @@ def test_kl_project_offset_base():
     ref = round_bf16(m_d.cpu().numpy()) @ W[:, :nn].T
     scale = np.abs(ref).max(axis=1, keepdims=True)
     assert np.all(np.abs(xi.cpu().numpy() - ref) <= (1e-5 + 5e-7 * math.sqrt(nn)) * scale)
+
+
+def test_kl_project_several_launches_and_repeat():
+    """More than 512 tiles (65,536 samples) run as several launches, each over its own slice
+    with the tile counters left zero for the next: 65,536 + 301 samples (the second launch
+    ragged, N odd: its last sample by plain loads), checked on rows around the boundary and
+    spread over both launches; a second call on the same inputs gives the same rows (the
+    counters were reset)."""
+    from paper_2305_20053_gb300 import capi
+    N, nn, rm = 65536 + 301, 289, 24
+    rng = np.random.default_rng(4242)
+    m_d = torch.randn(N, nn, device="cuda", dtype=torch.float64, generator=torch.Generator(device="cuda").manual_seed(5))
+    W = np.zeros((rm, 320))
+    W[:, :nn] = round_bf16(rng.standard_normal((rm, nn)) / 17.0)
+    W_d = torch.tensor(W, device="cuda").to(torch.bfloat16)
+    bias = rng.standard_normal(rm).astype(np.float32)
+    b_d = torch.tensor(bias, device="cuda")
+    rows = np.unique(np.concatenate([np.arange(65530, 65542), rng.integers(0, N, 40), [0, N - 2, N - 1]]))
+    out = []
+    for _ in range(2):
+        xi = torch.full((N, rm), float("nan"), device="cuda", dtype=torch.float32)
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        capi.ouu_kernel_kl_project(m_d, N, nn, W_d, rm, b_d, xi, err)
+        torch.cuda.synchronize()
+        assert err.item() == 0
+        assert not torch.isnan(xi).any().item()
+        out.append(xi[torch.tensor(rows, device="cuda")].cpu().numpy().astype(np.float64))
+    ref = round_bf16(m_d[torch.tensor(rows, device="cuda")].cpu().numpy()) @ W[:, :nn].T + bias.astype(np.float64)
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    for got in out:
+        assert np.all(np.abs(got - ref) <= (1e-5 + 5e-7 * math.sqrt(nn)) * scale)
+    np.testing.assert_allclose(out[1], out[0], rtol=0, atol=(1e-5 + 5e-7 * math.sqrt(nn)) * scale.max())
