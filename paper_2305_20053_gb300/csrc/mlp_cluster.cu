@@ -14,9 +14,9 @@
 //                 activations and FP32 side outputs (gelu'(a), phi, grad_z Q) to global
 //   warp 16     : TMA producer: the CTA's rows of the weights through a 7-stage ring (a whole
 //                 layer ahead, during the previous epilogue), and, once the layer's input is
-//                 complete, a quarter of the tile's input K blocks, multicast to the four CTAs
-//                 (up to 7 x 64 columns stay resident; the staging tile of the epilogue reuses
-//                 their space once the MMAs are done)
+//                 complete, all of the tile's input K blocks at once (up to 7 x 64 columns
+//                 stay resident; the staging tile of the epilogue reuses their space once the
+//                 MMAs are done)
 //   warp 17     : tcgen05.mma issuer (M = 128, N = the CTA's columns); allocates and frees
 //                 the tensor memory
 // Every mbarrier wait is bounded; on a timeout the CTA skips the remaining work (still
@@ -110,17 +110,6 @@ static __device__ __forceinline__ bool mlc_wait_cluster(uint64_t* bar, uint32_t 
     if (ok) return true;
     if (clock64() - t0 > TC_WAIT_CYCLES) return false;
   }
-}
-
-// TMA load of a 2-D box into the same shared offset of every CTA in cta_mask, completing its
-// bytes on the barrier at the same offset in each of them.
-static __device__ __forceinline__ void mlc_tma_load_mc(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
-                                                       uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(cta_mask)
-      : "memory");
 }
 
 // Named barrier of the 16 epilogue warps.
@@ -226,13 +215,11 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
         // still loaded, so that every barrier armed here completes before the CTA exits
         if (!mlc_wait_cluster(&layer_in[l & 1], (uint32_t)(l >> 1) & 1u)) ok = false;
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        // every CTA of the cluster needs the same input rows: each loads the blocks kb = rank
-        // (mod 4) once from L2 and multicasts them to all four (each arms its own barriers; a
-        // peer's copy may land first, the transaction count then passes through negative)
+        // all of the layer's input blocks at once (multicasting each block from one CTA of the
+        // cluster to all four measured slower: each CTA then waits for its slowest peer)
         for (int kb = 0; kb < KB; ++kb) {
           mbar_expect_tx(&a_full[kb], MLC_A_BYTES);
-          if (kb % MLC_CS == (int)rank)
-            mlc_tma_load_mc(sA + kb * MLC_A_BYTES, &P.a[l], kb * 64, m0, &a_full[kb], (uint16_t)((1u << MLC_CS) - 1u));
+          tma_load_2d(sA + kb * MLC_A_BYTES, &P.a[l], kb * 64, m0, &a_full[kb]);
           ++a_uses[kb];
         }
         for (int kb = pre; kb < KB && ok; ++kb) ok = load_w(kb);
