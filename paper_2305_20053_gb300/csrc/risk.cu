@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
       s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
     if (lane == 0) {
-      const double invN = 1.0 / N;
+      const double invN = risks[0].inv_N;   // 1/N from the host (an FP64 division is long on the narrow pipe)
       s_par[0] = s * invN;
       s_par[1] = fmax(s2 * invN - s_par[0] * s_par[0], 0.0);
     }
@@ -527,19 +527,21 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
             // converged when |step| < 2^-52 |t|: from the exponent fields
             const int es = (__double2hiint(step) >> 20) & 0x7FF, et = (__double2hiint(t) >> 20) & 0x7FF;
             uint64_t kn;
-            if (((uint64_t)__double_as_longlong(step) << 1) == 0 || es + 53 <= et) {   // bracket t tightly
-              const uint64_t ka = kt - 1, kb = kt + 1;
-              if (G(dval(ka), nullptr) < 0.0) {
-                klo = ka > klo ? ka : klo;
-                lo_neg = true;
-              } else {
-                khi = ka < khi ? ka : khi;
-              }
-              if (G(dval(kb), nullptr) < 0.0) {
-                klo = kb > klo ? kb : klo;
-                lo_neg = true;
-              } else {
-                khi = kb < khi ? kb : khi;
+            if (((uint64_t)__double_as_longlong(step) << 1) == 0 || es + 53 <= et) {
+              // converged: t bounds the root on the side its sign says; walk to adjacent doubles
+              // on the other side until the sign changes (usually the first one)
+              const bool tneg = g < 0.0;
+              uint64_t kx = kt;
+              for (int w = 0; w < 8; ++w) {
+                kx = tneg ? kx + 1 : kx - 1;
+                const bool neg = G(dval(kx), nullptr) < 0.0;
+                if (neg) {
+                  klo = kx > klo ? kx : klo;
+                  lo_neg = true;
+                } else {
+                  khi = kx < khi ? kx : khi;
+                }
+                if (neg != tneg) break;
               }
               if ((int64_t)(khi - klo) <= 4) break;
               kn = klo + (khi - klo) / 2;
