@@ -66,6 +66,7 @@ def parse():
                          "aggregate evals/s")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clocks-log", default=None, help="file for the nvidia-smi clock samples of the timed region")
     return ap.parse_args()
 
 
@@ -113,10 +114,12 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, path=None):
+        import tempfile
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples (the JSON line carries their summary); --clocks-log keeps them
+        self.path = path or os.path.join(tempfile.gettempdir(), f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -338,7 +341,7 @@ def run_ours(args):
         pde_step()
     torch.cuda.synchronize()
     pde_k = args.pde_steps if use_dino else args.steps
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_log)
     if not use_dino:
         clocks.start()
     barrier(dist)
