@@ -487,6 +487,8 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
     OUU_CUDA_TRY(cudaStreamSynchronize(ds));
     if (p->h_stat[0]) {
       cudaMemsetAsync(dino->d_err, 0, 4, ds);
+      // an interrupted projection may have left its tile counters non-zero
+      cudaMemsetAsync(dino->d_klp_ctr, 0, (OUU_KLP_MAX_TILES + 1) * sizeof(int), ds);
       ouu_set_error("tensor-core GEMM pipeline wait timed out");
       return OUU_ERR_CUDA;
     }

@@ -578,6 +578,8 @@ static ouu_status check_err(ouu_dino* d) {
   OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
   if (e) {
     cudaMemsetAsync(d->d_err, 0, 4, d->stream);
+    // an interrupted projection may have left its tile counters non-zero
+    cudaMemsetAsync(d->d_klp_ctr, 0, (OUU_KLP_MAX_TILES + 1) * sizeof(int), d->stream);
     ouu_set_error("tensor-core GEMM pipeline wait timed out");
     return OUU_ERR_CUDA;
   }
