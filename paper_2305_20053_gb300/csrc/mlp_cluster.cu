@@ -331,6 +331,26 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
         if (L.scale) cb1 = __ldg(L.scale + c0 + et);
         if (L.add) cb2 = __ldg(L.add + c0 + et);
       }
+      // quad e = et + i NT of the slice: row tr_i, quad cq_i, stepped without dividing
+      const int tr_s = NT / QPR, cq_s = NT - tr_s * QPR, tr0 = et / QPR, cq0 = et - tr0 * QPR;
+      float4 ax[MLC_QMAX];   // SCALE: the forward layer's gelu'(a), loaded before the accumulator is ready
+      if (L.mode == MLC_SCALE) {
+#pragma unroll
+        for (int i = 0, tr = tr0, cq = cq0; i < MLC_QMAX; ++i, tr += tr_s + (cq + cq_s >= QPR), cq += cq_s - (cq + cq_s >= QPR ? QPR : 0)) {
+          const int e = et + i * NT, c = c0 + 4 * cq, row = m0 + tr;
+          ax[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (e < NQ && row < P.M && c < L.N) {
+            const float* ap = L.aux + (size_t)row * L.ld_aux + c;
+            if (c + 3 < L.N) {
+              ax[i] = __ldcg(reinterpret_cast<const float4*>(ap));
+            } else {
+              float x[4] = {0.f, 0.f, 0.f, 0.f};
+              for (int j = 0; j < L.N - c; ++j) x[j] = __ldcg(ap + j);
+              ax[i] = make_float4(x[0], x[1], x[2], x[3]);
+            }
+          }
+        }
+      }
       if (live) live = __all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)l & 1u) ? 1 : 0) != 0;
       if (!live && lane == 0) s_fail = 1;
       tc_fence_after();
@@ -355,7 +375,9 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
       }
       mlc_epi_sync();   // the staging tile and the constants are complete
       if (live && L.mode == MLC_QOI) {
-        // whole rows per warp, lanes over the row's quads; the row's partial (phi + c)^2 sum
+        // whole rows per warp, lanes over the row's quads; the row's partial (phi + c)^2 sum (the
+        // 8 rows of a warp unrolled, so that their loads and reductions overlap)
+#pragma unroll
         for (int tr = warp; tr < 128; tr += MLC_EPI_WARPS) {
           const int row = m0 + tr, cq = 4 * lane, c = c0 + cq;
           float sq = 0.f;
@@ -382,24 +404,6 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
           if (lane == 0 && row < P.M) P.qpart[(size_t)row * MLC_CS + rank] = sq;
         }
       } else if (live && L.mode == MLC_SCALE) {
-        // quad e = et + i NT of the slice: row tr_i, quad cq_i, stepped without dividing
-        const int tr_s = NT / QPR, cq_s = NT - tr_s * QPR, tr0 = et / QPR, cq0 = et - tr0 * QPR;
-        float4 ax[MLC_QMAX];
-#pragma unroll
-        for (int i = 0, tr = tr0, cq = cq0; i < MLC_QMAX; ++i, tr += tr_s + (cq + cq_s >= QPR), cq += cq_s - (cq + cq_s >= QPR ? QPR : 0)) {   // all aux loads first: one round trip
-          const int e = et + i * NT, c = c0 + 4 * cq, row = m0 + tr;
-          ax[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (e < NQ && row < P.M && c < L.N) {
-            const float* ap = L.aux + (size_t)row * L.ld_aux + c;
-            if (c + 3 < L.N) {
-              ax[i] = __ldcg(reinterpret_cast<const float4*>(ap));
-            } else {
-              float x[4] = {0.f, 0.f, 0.f, 0.f};
-              for (int j = 0; j < L.N - c; ++j) x[j] = __ldcg(ap + j);
-              ax[i] = make_float4(x[0], x[1], x[2], x[3]);
-            }
-          }
-        }
 #pragma unroll
         for (int i = 0, tr = tr0, cq = cq0; i < MLC_QMAX; ++i, tr += tr_s + (cq + cq_s >= QPR), cq += cq_s - (cq + cq_s >= QPR ? QPR : 0)) {
           const int e = et + i * NT, c = c0 + 4 * cq, row = m0 + tr;
@@ -410,12 +414,10 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
           }
         }
       } else if (live) {
-        const int tr_s = NT / QPR, q_s = NT - tr_s * QPR;
-        int tr = et / QPR, qq = et - tr * QPR;
-#pragma unroll 2
-        for (int e = et; e < NQ; e += NT, tr += tr_s + (qq + q_s >= QPR), qq += q_s - (qq + q_s >= QPR ? QPR : 0)) {
-          const int cq = 4 * qq, c = c0 + cq, row = m0 + tr;
-          if (row >= P.M || c >= L.N) continue;
+#pragma unroll
+        for (int i = 0, tr = tr0, qq = cq0; i < MLC_QMAX; ++i, tr += tr_s + (qq + cq_s >= QPR), qq += cq_s - (qq + cq_s >= QPR ? QPR : 0)) {
+          const int e = et + i * NT, cq = 4 * qq, c = c0 + cq, row = m0 + tr;
+          if (e >= NQ || row >= P.M || c >= L.N) continue;
           const int nv = min(4, L.N - c);
           const float4 a4 = *reinterpret_cast<const float4*>(stg + tr * MLC_SROW + cq);
           const float acc[4] = {a4.x, a4.y, a4.z, a4.w};
