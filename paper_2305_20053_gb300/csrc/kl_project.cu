@@ -55,6 +55,7 @@ struct KlpArgs {
   int pair;        // 1: fields read as sample pairs (n^2 odd); 0: as rows (n^2 even)
   int n_tma;       // samples [0, n_tma) come by TMA, the rest (at most one) by plain loads
   int T;           // 128-sample tiles
+  int bulk;        // 1: the final visit's rows are added by TMA bulk reductions (r_m % 4 == 0, xi 16-byte aligned)
   int* ctr;        // [T] next unclaimed K block of each tile, [T] CTAs finished; zero at launch and
                    // left zero by the last CTA
   const float* bias;
@@ -127,8 +128,8 @@ static __device__ __forceinline__ float f64_to_f32_rne(double x) {
   return __uint_as_float(f);
 }
 
-// A published unit: x = tile (< 0: no more units), y = K block | first << 16 | last << 17
-// (first / last unit of a tile visit).
+// A published unit: x = tile (< 0: no more units), y = K block | first << 16 | last << 17 |
+// final << 18 (first / last unit of a tile visit; the last unit of the CTA).
 __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_constant__ CUtensorMap tw,
                                                                 const __grid_constant__ CUtensorMap tm, KlpArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
   uint64_t* mma_done = bars + 16;
   uint32_t* tslot = (uint32_t*)(bars + 17);
   __shared__ int2 s_unit[KLP_RING];
-  __shared__ int2 s_seg[2];         // (tile, holds K block 0); tile < 0: no more visits
+  __shared__ int2 s_seg[2];         // (tile, holds K block 0 | final visit << 1); tile < 0: no more visits
   __shared__ volatile int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -253,7 +254,8 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
       const bool pub = have && ok;   // on a timeout the end is published instead
       if (lane == 0) {
         s_unit[j & (KLP_RING - 1)] =
-            pub ? make_int2(t_cur, kb_cur | ((t_cur != prev_t) << 16) | ((!have_nxt || t_nxt != t_cur) << 17))
+            pub ? make_int2(t_cur, kb_cur | ((t_cur != prev_t) << 16) | ((!have_nxt || t_nxt != t_cur) << 17) |
+                                       ((!have_nxt) << 18))
                 : make_int2(-1, 0);
         uint8_t* dst = sF + s * KLP_F64_STAGE;
         if (!pub || a.n_tma == 0) {
@@ -378,7 +380,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
         const int2 e = s_unit[j & (KLP_RING - 1)];
         if (e.x < 0) break;
         const int kb = e.y & 0xFFFF;
-        const bool first = (e.y >> 16) & 1, last = (e.y >> 17) & 1;
+        const bool first = (e.y >> 16) & 1, last = (e.y >> 17) & 1, fin = (e.y >> 18) & 1;
         const int acc = seg & 1;
         if (first) {
           if (seg >= 2 && !mbar_wait(&acc_empty[acc], (uint32_t)((seg >> 1) - 1) & 1u)) {
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
         any = true;
         if (last) {
           tc_commit(&acc_full[acc]);
-          s_seg[acc] = make_int2(seg_t, has0);
+          s_seg[acc] = make_int2(seg_t, has0 | (fin ? 2 : 0));
           mbar_arrive(&seg_full[acc]);
           ++seg;
         }
@@ -440,6 +442,44 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
       const int r = d.x * 128 + q * 32 + lane;
       float* orow = a.xi + (size_t)r * a.rm;
       const bool vec4 = (a.rm & 3) == 0;
+      if ((d.y & 2) && a.bulk) {
+        // The CTA's final visit, when every CTA flushes at once: the rows go through the
+        // (now idle) FP64 stages and are added into xi by the TMA engine, one bulk reduction
+        // of r_m floats per row, in whole lines instead of 16-byte atomics.
+        float* srow = reinterpret_cast<float*>(sF) + (size_t)(q * 32 + lane) * a.rm;
+        for (int c0 = 0; c0 < a.BN; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * 256u + (uint32_t)c0, v);
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) {
+            const int c = c0 + i;
+            if (c < a.rm) {   // r_m % 4 == 0
+              float4 y = make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]), __uint_as_float(v[i + 2]),
+                                     __uint_as_float(v[i + 3]));
+              if (d.y & 1) {
+                y.x += a.bias[c];
+                y.y += a.bias[c + 1];
+                y.z += a.bias[c + 2];
+                y.w += a.bias[c + 3];
+              }
+              *reinterpret_cast<float4*>(srow + c) = y;
+            }
+          }
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          const int rw0 = d.x * 128 + q * 32;
+          for (int i = 0; i < 32 && rw0 + i < N; ++i)
+            asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                             a.xi + (size_t)(rw0 + i) * a.rm),
+                         "r"(smem_u32(reinterpret_cast<float*>(sF) + (size_t)(q * 32 + i) * a.rm)), "r"(a.rm * 4)
+                         : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // done before the CTA exits
+        }
+        __syncwarp();
+      } else
       for (int c0 = 0; c0 < a.BN; c0 += 16) {
         uint32_t v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * 256u + (uint32_t)c0, v);
@@ -512,6 +552,7 @@ static ouu_status kl_project_launch(const double* m, int N, int nn, const CUtens
   a.rm = rm;
   a.T = (N + 127) / 128;
   a.ctr = ctr;
+  a.bulk = (rm % 4 == 0 && ((uintptr_t)xi & 15) == 0 && (size_t)128 * rm * 4 <= 2 * (size_t)KLP_F64_STAGE) ? 1 : 0;
   a.bias = bias;
   a.xi = xi;
   a.err = err;
