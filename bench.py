@@ -400,7 +400,7 @@ def run_ours(args):
         }
         # DRAM bytes per launch from the committed ncu capture of the same kernel
         # (profiles/kl_project_129x129_N1024_ncu.md: N = 1024, scaled by the 4x samples)
-        traffic = {"project": 4 * (144.39936e6 + 3.25376e6)}
+        traffic = {"project": 4 * (144.396544e6 + 3.240448e6)}
         key = max(kern, key=lambda k: kern[k][3])
         name, bound, work, kms = kern[key]
         achieved = work / (kms / 1000.0) / (1e9 if bound == "hbm" else 1e12)
