@@ -25,9 +25,11 @@
 //                  W[0, BN) x [k0, k0 + 64) (128-byte swizzle) once its stage is free.
 //   warp 17      : tcgen05.mma issuer (M = 128, N = BN, K = 16 per instruction) into one of
 //                  two TMEM accumulators (one per tile visit); allocates and frees the tensor
-//                  memory; hands each visit's (tile, holds K block 0) to the epilogue.
+//                  memory; hands each visit's (tile, holds K block 0, final) to the epilogue.
 //   warps 18..21 : epilogue.  TMEM -> registers, + bias on the visit that holds K block 0 of
-//                  its tile, 16-byte atomic adds into xi (zeroed beforehand).
+//                  its tile, 16-byte atomic adds into xi (zeroed beforehand); the CTA's final
+//                  visit (when every CTA flushes at once) goes through the idle FP64 stages
+//                  and TMA bulk reductions of whole rows instead.
 // Every mbarrier wait is bounded; on a timeout the CTA publishes the end of its units, stops,
 // drains its own copies and raises *err.
 #include <cuda_bf16.h>
