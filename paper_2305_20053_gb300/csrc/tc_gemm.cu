@@ -1,7 +1,7 @@
 // tcgen05 + TMA BF16 GEMM with fused epilogues (see tc_gemm.cuh).
 //
-// CTA = 6 warps, one 128 x BN output tile:
-//   warp 0 (one lane): TMA producer, 4-stage ring of 64-wide K blocks (SWIZZLE_128B)
+// CTA = 12 warps (384 threads), one 128 x BN output tile:
+//   warp 0 (one lane): TMA producer, 4- or 5-stage ring of 64-wide K blocks (SWIZZLE_128B)
 //   warp 1 (one lane): tcgen05.mma issuer (kind::f16, BF16 x BF16 -> FP32 in TMEM);
 //                      warp 1 also allocates / frees the tensor memory
 //   warps 2..5       : TMEM -> shared staging tile, one accumulator row (TMEM lane) per thread
