@@ -281,14 +281,14 @@ ouu_status ouu_dino_set_graphs(ouu_dino_t d, int enable);
  * QoI -> reverse-mode z-gradient) runs; every mode has the same arithmetic.
  *   mode 0: one tensor-core GEMM kernel per layer, fused epilogues;
  *   mode 1: one kernel, one CTA per 128-sample tile holding the activations in shared memory
- *           (width, r_U, d_Z <= 416, r_M + d_Z <= 448); the GELU epilogues of a layer then run
- *           on one SM per tile, slower than mode 0 at thousands of samples;
+ *           (width, r_U, d_Z <= 416, r_M + d_Z <= 448, r_M % 4 == 0); the GELU epilogues of a
+ *           layer then run on one SM per tile, slower than mode 0 at thousands of samples;
  *   mode 2 (default): one kernel, each 128-sample tile on a cluster of 4 CTAs, each computing a quarter of
  *           every layer's columns, activations passed through L2 (width, r_U, r_M + d_Z <= 448,
  *           d_Z <= 512, r_M % 4 == 0, width % 8 == 0).
  * A mode whose size limits the network exceeds falls back to mode 0.  ouu_batch_create with
  * autotune picks per network by timing.  Returns OUU_ERR_INVALID_ARG for another mode. */
-ouu_status ouu_dino_set_fused_network(ouu_dino_t d, int enable);
+ouu_status ouu_dino_set_fused_network(ouu_dino_t d, int mode);
 
 /* Thread-local message of the last failed call ("" if none).  Copies at most
  * len-1 bytes plus a terminating zero into buf; returns the full length. */

@@ -926,10 +926,10 @@ extern "C" ouu_status ouu_dino_get_output_scale(ouu_dino_t d, float* s_host) {
   return OUU_OK;
 }
 
-extern "C" ouu_status ouu_dino_set_fused_network(ouu_dino_t d, int enable) {
+extern "C" ouu_status ouu_dino_set_fused_network(ouu_dino_t d, int mode) {
   OUU_CHECK_ARG(d != nullptr, "null argument");
-  OUU_CHECK_ARG(enable >= 0 && enable <= 2, "network mode: 0 per-layer kernels, 1 one kernel, 2 clusters");
-  d->fused_mlp = enable;
+  OUU_CHECK_ARG(mode >= 0 && mode <= 2, "network mode: 0 per-layer kernels, 1 one kernel, 2 clusters");
+  d->fused_mlp = mode;
   if (d->gexec) {   // a captured evaluation holds the other path's kernels
     cudaGraphExecDestroy(d->gexec);
     d->gexec = nullptr;

@@ -1,5 +1,6 @@
 // The whole evaluation network of the reduced-basis neural operator (Sec. 3.3) in one kernel:
-// for a tile of 128 samples, the forward pass [xi; z] -> 400 -> 400 -> 400 -> phi with exact
+// for a tile of 128 samples, the forward pass [xi; z] -> width -> width -> width -> phi (width,
+// r_U and d_Z at most 416, r_M + d_Z at most 448) with exact
 // GELU, the reduced QoI Q = 1/2 ||phi + c||^2 + const and its seed s (phi + c), and the
 // reverse-mode gradient grad_z Q = W0z^T (s'(a1) * W1^T (s'(a2) * W2^T (s'(a3) * W3^T seed))).
 // The activations never leave shared memory: each layer's BF16 output is written, in the
@@ -12,7 +13,7 @@
 //   warp 16     : TMA producer of the weight blocks of all layers, in order, through a two-stage
 //                 ring (it runs ahead into the next layer while the epilogue works)
 //   warp 17     : tcgen05.mma issuer (one or two N pieces of 208 columns per K step);
-//                 allocates and frees the tensor memory (512 columns: the 400-wide accumulator)
+//                 allocates and frees the tensor memory (512 columns: two 208-column pieces)
 // Every mbarrier wait is bounded; on a timeout the CTA stops and raises *err.
 #include <cuda_bf16.h>
 
