@@ -5,6 +5,8 @@
 * Stratified Gaussian QoIs: mean -> mu, variance -> sigma^2 and
   CVaR_0.95 -> mu + sigma phi(Phi^-1(0.95)) / 0.05 (closed form of the normal).
 * Brute-force Rockafellar-Uryasev minimum on tiny N against the smoothed t*.
+* t* is the minimiser of the smoothed objective: no point of a dense grid of t does
+  better, also with ties, a constant sample and N (1 - beta) < 1 (CVaR = max Q).
 * Risk gradients against finite differences through per-sample linear QoIs.
 """
 import numpy as np
@@ -97,3 +99,22 @@ def test_risk_gradients_finite_difference():
     dt = risk.cvar_dt(Q, t, 0.9, 1e-2)
     fd_t = (risk.cvar_value(Q, t + 1e-7, 0.9, 1e-2) - risk.cvar_value(Q, t - 1e-7, 0.9, 1e-2)) / 2e-7
     np.testing.assert_allclose(dt, fd_t, rtol=1e-6)
+
+
+@pytest.mark.parametrize("case", ["random", "ties", "constant", "single_tail"])
+def test_tstar_is_the_minimiser(case):
+    rng = np.random.default_rng(11)
+    beta, eps = 0.9, 1e-3
+    Q = {"random": rng.standard_normal(37),
+         "ties": np.repeat(rng.standard_normal(5), 7),
+         "constant": np.full(9, 0.3),
+         "single_tail": rng.standard_normal(6)}[case]   # N (1 - beta) = 0.6 < 1
+    t = risk.cvar_tstar(Q, beta, eps)
+    v = risk.cvar_value(Q, t, beta, eps)
+    grid = np.linspace(Q.min() - 2 * eps, Q.max() + 2 * eps, 20001)
+    vals = grid + risk.splus(Q[None, :] - grid[:, None], eps).sum(axis=1) / (Q.size * (1 - beta))
+    assert v <= vals.min() + 1e-12
+    bf = risk.cvar_bruteforce(Q, beta)
+    assert bf - 0.5 * eps / (1 - beta) - 1e-12 <= v <= bf + 1e-12
+    if case == "single_tail":
+        assert bf == Q.max()
