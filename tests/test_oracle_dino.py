@@ -1,6 +1,8 @@
 """Pins of the oracle's reduced-basis neural operator (Sec. 3.3-3.4), CPU only.
 
-* KL projection returns exactly the whitened normals of a synthesised field.
+* KL projection returns exactly the whitened normals of a synthesised field (also with
+  a nonzero mean field); its BF16 form rounds the centred field and the basis, each to
+  the nearest bfloat16 (hand-computed values of the format), and sums in FP64.
 * POD: M-orthonormal basis, reconstruction error = tail eigenvalue sum,
   rank-one data gives one mode.
 * MLP: forward-mode control Jacobian against finite differences in z; the
@@ -30,6 +32,26 @@ def test_kl_projection_returns_normals():
     lam = field.kl_eigenvalues(n, 0.1, 1.0).ravel()[order]
     assert np.all(np.diff(lam) >= 0)
     assert order[0] == 0 and set(order[1:3]) == {1, n}
+    m1 = field.synthesize(xi.reshape(3, n, n), n, 0.1, 1.0, -1.5)
+    np.testing.assert_allclose(dino.project_fields(m1.reshape(3, -1), W, m_mean=-1.5), xi[:, order[:r_m]],
+                               atol=1e-12)
+
+
+def test_kl_projection_bf16_operands():
+    # 1 + 2^-8 + 2^-12 lies above the midpoint of the bfloat16 neighbours 1 and 1 + 2^-7
+    x = 1.0 + 2.0 ** -8 + 2.0 ** -12
+    up = 1.0 + 2.0 ** -7
+    m = np.array([[3.0 + x, 3.0 + 2.0, 3.0 - 0.5]])
+    W = np.array([[x], [0.25], [-3.0]])
+    got = dino.project_fields(m, W, m_mean=3.0, bf16=True)
+    assert got[0, 0] == up * up + 2.0 * 0.25 + (-0.5) * (-3.0)
+    exact = dino.project_fields(m, W, m_mean=3.0)
+    np.testing.assert_allclose(exact[0, 0], x * x + 0.5 + 1.5, rtol=1e-15)
+    # operands already in bfloat16: the sum is exact
+    rng = np.random.default_rng(5)
+    a = rng.integers(-64, 64, (4, 50)) * 2.0 ** -6
+    B = rng.integers(-64, 64, (50, 3)) * 2.0 ** -4
+    assert np.array_equal(dino.project_fields(a, B, bf16=True), a @ B)
 
 
 def test_pod_properties():
