@@ -480,7 +480,7 @@ static bool mlc_layer(MlcParams& P, int l, const __nv_bfloat16* a, int lda, cons
 }
 
 ouu_status mlp_cluster_eval(ouu_dino* d, int N) {
-  static MlcParams P;   // host staging of the kernel parameters (one device per process)
+  MlcParams P;   // kernel parameters: the launch copies them, so concurrent handles share nothing
   std::memset(&P, 0, sizeof(P));
   P.M = N;
   const int wd = d->wd, rup = (d->ru + 7) / 8 * 8, dzp = (d->dz + 7) / 8 * 8, in0p = d->inp_l[0];

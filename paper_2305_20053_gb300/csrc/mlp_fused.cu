@@ -321,7 +321,7 @@ static bool mlp_layer(MlpParams& P, int l, const __nv_bfloat16* base, int ld, in
 }
 
 ouu_status mlp_fused_eval(ouu_dino* d, int N) {
-  static MlpParams P;   // host staging of the kernel parameters (one device per process)
+  MlpParams P;   // kernel parameters: the launch copies them, so concurrent handles share nothing
   std::memset(&P, 0, sizeof(P));
   const int wd = d->wd, rup = (d->ru + 7) / 8 * 8, dzp = (d->dz + 7) / 8 * 8;
   bool ok = mlp_layer(P, 0, d->Wb[0], d->inp_l[0], d->in0, wd, MLP_GELU_D);
