@@ -2,6 +2,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "dino.cuh"
@@ -10,6 +12,19 @@
 static thread_local std::string g_last_error;
 
 void ouu_set_error(const std::string& msg) { g_last_error = msg; }
+
+cudaError_t ouu_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;   // (device, kernel) -> limit set so far
+  int dev = 0;
+  if (const cudaError_t e = cudaGetDevice(&dev)) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{dev, fn}];
+  if (cur >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 extern "C" size_t ouu_last_error(char* buf, size_t len) {
   if (buf && len > 0) {

@@ -90,10 +90,8 @@ void launch_sample_fields(int n, uint64_t seed, int64_t first, int count, const 
   if (count <= 0) return;
   const size_t sm1 = (size_t)OUU_FIELD_ROWS * n * sizeof(double);
   const size_t sm2 = (size_t)n * 32 * sizeof(double);
-  if (sm2 > 48 * 1024)
-    cudaFuncSetAttribute((const void*)k_fields_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-  if (sm1 > 48 * 1024)
-    cudaFuncSetAttribute((const void*)k_fields_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  if (sm2 > 48 * 1024) ouu_smem_limit((const void*)k_fields_cols, sm2);
+  if (sm1 > 48 * 1024) ouu_smem_limit((const void*)k_fields_rows, sm1);
   dim3 g1((n + OUU_FIELD_ROWS - 1) / OUU_FIELD_ROWS, count);
   k_fields_rows<<<g1, 256, sm1, s>>>(n, seed, first, invlam, V, m);
   dim3 g2((n + 31) / 32, count);

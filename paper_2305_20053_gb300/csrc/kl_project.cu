@@ -559,11 +559,7 @@ static ouu_status kl_project_launch(const double* m, int N, int nn, const CUtens
   a.xi = xi;
   a.err = err;
   const size_t smem = 1024 + 2 * KLP_A_STAGE + 2 * (size_t)BN * 128 + 2 * KLP_F64_STAGE + 17 * 8 + 16;
-  static size_t attr = 0;   // one device per process is the supported set-up
-  if (attr < smem) {
-    OUU_CUDA_TRY(cudaFuncSetAttribute((const void*)k_kl_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  OUU_CUDA_TRY(ouu_smem_limit((const void*)k_kl_project, smem));
   const long long U = (long long)a.T * a.KBt;
   const int grid = (int)std::min<long long>(U, (long long)std::max(1, num_sms));
   OUU_CUDA_TRY(cudaMemsetAsync(xi, 0, (size_t)N * rm * 4, s));

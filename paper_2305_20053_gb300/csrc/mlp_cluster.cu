@@ -532,12 +532,7 @@ ouu_status mlp_cluster_eval(ouu_dino* d, int N) {
   P.qconst = d->qconst;
   P.err = d->d_err;
   const size_t smem = MLC_SMEM;
-  static bool attr = false;
-  if (!attr) {
-    OUU_CUDA_TRY(cudaFuncSetAttribute((const void*)k_mlp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    attr = true;
-  }
+  OUU_CUDA_TRY(ouu_smem_limit((const void*)k_mlp_cluster, smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(MLC_CS * ((N + 127) / 128));
   cfg.blockDim = dim3(MLC_THREADS);

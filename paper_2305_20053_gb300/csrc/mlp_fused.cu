@@ -362,11 +362,7 @@ ouu_status mlp_fused_eval(ouu_dino* d, int N) {
   P.qconst = d->qconst;
   P.err = d->d_err;
   const size_t smem = 1024 + MLP_ABLOCKS * MLP_ABLOCK + 2 * MLP_BSTAGE + 16 * 8;
-  static bool attr = false;
-  if (!attr) {
-    OUU_CUDA_TRY(cudaFuncSetAttribute((const void*)k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  OUU_CUDA_TRY(ouu_smem_limit((const void*)k_mlp_eval, smem));
   OUU_CUDA_TRY(launch_pdl(k_mlp_eval, dim3((N + 127) / 128), dim3(MLP_THREADS), smem, d->stream, P));
   return OUU_OK;
 }

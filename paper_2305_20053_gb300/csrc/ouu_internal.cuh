@@ -10,6 +10,11 @@
 // ------------------------------------------------------------------ errors
 void ouu_set_error(const std::string& msg);
 
+// Raises kernel fn's dynamic shared memory limit to at least `bytes` (never lowers it), under
+// one lock, so that launches of the same kernel with different sizes from concurrent handles
+// cannot undo each other's limit.  Kept per device (the current one).
+cudaError_t ouu_smem_limit(const void* fn, size_t bytes);
+
 // ------------------------------------------------------------------ programmatic dependent launch
 // Kernels launched with launch_pdl may start while the previous kernel in the stream drains
 // (their set-up overlaps its tail); each calls pdl_wait() before it reads or writes global

@@ -245,19 +245,17 @@ void launch_pde_batch(const PdeArgs* probs_dev, const int2* tasks_dev, int n_tas
                       int64_t smem_bytes, int nslots, int* counter, unsigned long long* cycles, bool adjoint,
                       cudaStream_t s) {
   if (adjoint) {
-    cudaFuncSetAttribute((const void*)k_pde_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    ouu_smem_limit((const void*)k_pde_batch<true>, (size_t)smem_bytes);
     k_pde_batch<true><<<nslots, OUU_SOLVER_THREADS, (size_t)smem_bytes, s>>>(probs_dev, tasks_dev, n_tasks, slots,
                                                                               slot_bytes, counter, cycles);
   } else {
-    cudaFuncSetAttribute((const void*)k_pde_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    ouu_smem_limit((const void*)k_pde_batch<false>, (size_t)smem_bytes);
     k_pde_batch<false><<<nslots, OUU_SOLVER_THREADS, (size_t)smem_bytes, s>>>(probs_dev, tasks_dev, n_tasks, slots,
                                                                                slot_bytes, counter, cycles);
   }
 }
 
-static void set_smem(const void* fn, int64_t bytes) {
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+static void set_smem(const void* fn, int64_t bytes) { ouu_smem_limit(fn, (size_t)bytes); }
 
 void launch_pde_state(const PdeArgs& a, int nslots, cudaStream_t s) {
   set_smem((const void*)k_pde_state, a.lay.smem_bytes);
@@ -302,9 +300,7 @@ __global__ void k_sources_transpose_apply(int n, int L, const double* gx, const 
 void launch_sources_transpose(int n, int L, int n_w, const double* gx, const double* gy, double gscale,
                               const double* s, double* grad, cudaStream_t st) {
   const size_t sm = (size_t)L * n * sizeof(double);
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute((const void*)k_sources_transpose_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
+  if (sm > 48 * 1024) ouu_smem_limit((const void*)k_sources_transpose_apply, sm);
   k_sources_transpose_apply<<<n_w, 256, sm, st>>>(n, L, gx, gy, gscale, s, grad);
 }
 
@@ -314,9 +310,7 @@ void launch_reduce_slots_and_gradient(const char* slots, const SlotLayout& lay, 
   const int64_t count = (int64_t)n_w * n * n;
   k_reduce_slots<<<(int)((count + 255) / 256), 256, 0, st>>>(slots, lay.bytes, lay.acc, nslots, count, s_out);
   const size_t sm = (size_t)L * n * sizeof(double);
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute((const void*)k_sources_transpose_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
+  if (sm > 48 * 1024) ouu_smem_limit((const void*)k_sources_transpose_apply, sm);
   k_sources_transpose_apply<<<n_w, 256, sm, st>>>(n, L, gx, gy, gscale, s_out, grad);
 }
 

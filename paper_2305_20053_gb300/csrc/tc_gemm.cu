@@ -391,11 +391,7 @@ static ouu_status launch_bn(const CUtensorMap& ta, const __nv_bfloat16* B, int l
   }
   const size_t smem = 1024 + (size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) +
                       (2 * GEMM_STAGES + 1) * 8 + 16;
-  static bool attr_set = false;   // one device per process is the supported set-up
-  if (!attr_set) {
-    cudaFuncSetAttribute((const void*)k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
-  }
+  OUU_CUDA_TRY(ouu_smem_limit((const void*)k_gemm_bf16<BN>, smem));
   dim3 grid((N + BN - 1) / BN, (M + GEMM_BM - 1) / GEMM_BM, splits);
   OUU_CUDA_TRY(launch_pdl(k_gemm_bf16<BN>, grid, dim3(GEMM_THREADS), smem, s, ta, tb, M, N, K, ep, err));
   return OUU_OK;
