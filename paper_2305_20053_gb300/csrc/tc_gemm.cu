@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -418,7 +419,7 @@ struct GemmKey {
 };
 static std::map<GemmKey, int> g_tuned;
 static std::mutex g_tune_mu;
-static int g_autotune = 0;
+static std::atomic<int> g_autotune{0};
 
 ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                          const EpiParams& ep, int* err, cudaStream_t s, int splits) {
@@ -487,13 +488,12 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   // N tile: a CTA's time is mostly fixed latency (TMA round trips, MMA commit, epilogue)
   // plus a part that grows with BN, and tiles beyond one per SM run in a further wave;
   // pick the tile that minimises waves x (BN + 64) (ties: the wider tile).
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {   // initialised once, thread-safe (one device per process)
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   static const int cands[] = {256, 208, 128, 112, 80, 64};
   int best = 64;
   long best_cost = 1L << 60;
