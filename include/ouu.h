@@ -183,7 +183,8 @@ ouu_status ouu_pde_solve_batch_noalloc(const ouu_problem_desc* desc, const doubl
  * the prior (Sec. 3.3, KLE; mode order: decreasing prior variance, ties by
  * (k1 + k2, k1)), Phi the r_u leading modes of the mass-weighted POD of training
  * states (Sec. 3.3, M = h^2 I on interior nodes, Phi^T M Phi = I), phi_w a dense
- * net [m_r; z] -> width -> width -> width -> r_u with exact-erf GELU and a linear
+ * net [m_r; z] -> width -> width -> width -> r_u with GELU x Phi(x) (Phi by Abramowitz &
+ * Stegun 26.2.17, within 5e-7 of the exact function) and a linear
  * output layer.  The control Jacobian d_z phi_w is carried in forward mode
  * (Sec. 3.2); training minimises the reduced-space DINO loss of Sec. 3.4,
  *   (1/B) sum_i ||phi_i - y_i||^2 + jac_weight ||d_z phi_i - Y_i||_F^2,

@@ -5,7 +5,7 @@
  * cores (TMA-fed, BF16 operands, FP32 accumulation in tensor memory), with the
  * fused epilogue `mode` applied to the accumulator acc at row r, column c:
  *   0 LINEAR     : y = alpha * acc + bias[c]
- *   1 GELU       : a = acc + bias[c]; out_f32 = a; BF16 outputs = gelu(a)   (exact erf GELU)
+ *   1 GELU       : a = acc + bias[c]; out_f32 = a; BF16 outputs = gelu(a)   (GELU x Phi(x), Phi by A&S 26.2.17)
  *   2 DGELU_SCALE: y = acc * gelu'(aux[(r / aux_rdiv) * ld_aux + c]); out2 = bf16(acc)
  *   3 GELU_D     : a = acc + bias[c]; out_f32 = gelu'(a); BF16 outputs = gelu(a)
  *   4 SCALE      : y = acc * aux[(r / aux_rdiv) * ld_aux + c]

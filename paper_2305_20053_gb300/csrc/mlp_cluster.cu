@@ -1,6 +1,6 @@
 // The evaluation network of the reduced-basis neural operator (Sec. 3.3) in one kernel, each
 // 128-sample tile on a cluster of 4 CTAs, each CTA computing a quarter of the columns of
-// every layer: forward [xi; z] -> width -> width -> width -> phi with exact GELU, the reduced
+// every layer: forward [xi; z] -> width -> width -> width -> phi with GELU (gelu.cuh), the reduced
 // QoI Q = 1/2 ||phi + c||^2 + const with its seed s (phi + c), and the reverse-mode gradient
 // grad_z Q = W0z^T (s'(a1) * W1^T (s'(a2) * W2^T (s'(a3) * W3^T seed))).
 // The layers' BF16 activations pass through the handle's evaluation buffers (L2-resident,

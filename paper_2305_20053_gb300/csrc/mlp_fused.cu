@@ -1,7 +1,7 @@
 // The whole evaluation network of the reduced-basis neural operator (Sec. 3.3) in one kernel:
 // for a tile of 128 samples, the forward pass [xi; z] -> width -> width -> width -> phi (width,
-// r_U and d_Z at most 416, r_M + d_Z at most 448) with exact
-// GELU, the reduced QoI Q = 1/2 ||phi + c||^2 + const and its seed s (phi + c), and the
+// r_U and d_Z at most 416, r_M + d_Z at most 448) with GELU
+// (gelu.cuh), the reduced QoI Q = 1/2 ||phi + c||^2 + const and its seed s (phi + c), and the
 // reverse-mode gradient grad_z Q = W0z^T (s'(a1) * W1^T (s'(a2) * W2^T (s'(a3) * W3^T seed))).
 // The activations never leave shared memory: each layer's BF16 output is written, in the
 // 128-byte swizzled K-major layout tcgen05.mma reads, over the layer's own input (its MMAs

@@ -4,7 +4,10 @@ batched solver, POD basis, and training by the library's own kernels.
 Host-side orchestration only (epoch loop, learning-rate schedule, minibatch
 index arrays); every computation is a call into libouu.so.
 
-  python -m paper_2305_20053_gb300.train [--n 129] [--train 1024] [--epochs 200] [--eval]
+  python -m paper_2305_20053_gb300.train [--n 129] [--train 1024] [--epochs 200] [--save net.npz]
+
+A trained surrogate is kept with save_surrogate / load_surrogate (an .npz archive of the
+parameters, output scale and POD basis, checked against the handle's sizes and prior).
 """
 from __future__ import annotations
 
@@ -173,6 +176,68 @@ def risk_errors(P, D, n_samples, zs, risks):
     return worst_r, worst_g, rows
 
 
+# ----------------------------------------------------------------------------- persistence
+# What defines a surrogate besides its arrays: the sizes and the prior (the KL projection rows
+# follow from n, r_m and the prior, and are rebuilt when a handle is created).
+SURROGATE_KEYS = ("n", "lattice_L", "r_m", "r_u", "width", "gamma", "delta", "m_mean")
+
+
+def _surrogate_meta(desc):
+    return np.array([float(getattr(desc, k)) for k in SURROGATE_KEYS])
+
+
+def write_surrogate(path, desc, params, out_scale, phi, ubar):
+    """Stores a trained surrogate as an .npz archive at `path` (written as given, no suffix
+    added): the sizes and prior of `desc`, the flat FP32 parameter vector, the FP32 output
+    scale [r_u] and the FP64 POD basis [r_u][n][n] with its mean state [n][n]."""
+    n, r_u = int(desc.n), int(desc.r_u)
+    params = np.ascontiguousarray(params, dtype=np.float32).ravel()
+    out_scale = np.ascontiguousarray(out_scale, dtype=np.float32)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ubar = np.ascontiguousarray(ubar, dtype=np.float64)
+    if out_scale.shape != (r_u,) or phi.shape != (r_u, n, n) or ubar.shape != (n, n):
+        raise ValueError("surrogate arrays do not match the descriptor's n and r_u")
+    with open(path, "wb") as fh:
+        np.savez(fh, meta=_surrogate_meta(desc), params=params, out_scale=out_scale, phi=phi, ubar=ubar)
+
+
+def read_surrogate(path, desc):
+    """The arrays of write_surrogate, after checking that the archive holds a surrogate of the
+    sizes and prior of `desc` (ValueError otherwise)."""
+    with np.load(path) as f:
+        meta, want = f["meta"], _surrogate_meta(desc)
+        if meta.shape != want.shape or not np.array_equal(meta, want):
+            bad = [k for k, a, b in zip(SURROGATE_KEYS, meta, want) if a != b] if meta.shape == want.shape else []
+            raise ValueError(f"surrogate archive {path} was written for other sizes or prior {bad}")
+        return {k: f[k] for k in ("params", "out_scale", "phi", "ubar")}
+
+
+def save_surrogate(D, path):
+    """Writes the trained state of the handle D (parameters, output scale, POD basis)."""
+    import torch
+    d = D.desc
+    phi = torch.empty(d.r_u, d.n, d.n, dtype=torch.float64, device="cuda")
+    ubar = torch.empty(d.n, d.n, dtype=torch.float64, device="cuda")
+    D.ouu_dino_get_bases(phi, ubar)   # synchronises
+    write_surrogate(path, d, D.ouu_dino_get_params(), D.ouu_dino_get_output_scale(), phi.cpu().numpy(),
+                    ubar.cpu().numpy())
+
+
+def load_surrogate(D, path):
+    """Installs a surrogate written by save_surrogate into the handle D, created with the same
+    sizes and prior (the Adam state starts afresh)."""
+    import torch
+    a = read_surrogate(path, D.desc)
+    if a["params"].size != D.n_params:
+        raise ValueError(f"surrogate archive {path}: {a['params'].size} parameters, the handle has {D.n_params}")
+    D.ouu_dino_set_params(a["params"])
+    phi = torch.tensor(a["phi"], device="cuda")
+    ubar = torch.tensor(a["ubar"], device="cuda")
+    D.ouu_dino_set_bases(phi, ubar)
+    D.ouu_dino_set_output_scale(a["out_scale"])
+    torch.cuda.synchronize()   # the basis copies have read phi and ubar before they are freed
+
+
 def build_surrogate(n=129, L=10, n_train=1024, epochs=200, batch=256, jac_weight=1.0, max_eval=4096, log_every=0):
     """Problem + trained network; returns (P, D, report)."""
     P = make_problem(n, L, max(n_train, max_eval, 256))
@@ -196,11 +261,14 @@ def main():
     ap.add_argument("--samples", type=int, default=4096)
     ap.add_argument("--jac-weight", type=float, default=1.0)
     ap.add_argument("--out", default="")
+    ap.add_argument("--save", default="", help="write the trained surrogate to this .npz file")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
     P, D, rep = build_surrogate(args.n, args.L, args.train, args.epochs, jac_weight=args.jac_weight,
                                 max_eval=args.samples, log_every=20)
+    if args.save:
+        save_surrogate(D, args.save)
     es, ej = heldout_errors(P, D)
     rep["heldout_state_rel"] = es
     rep["heldout_jacobian_rel"] = ej
