@@ -1,0 +1,59 @@
+"""The JSON line of bench.py's reference arm (the FP64 oracle on the host cores), CPU only,
+with the timed oracle replaced by a stub of known rate: one line from rank 0 with the
+contract's keys, a value that is the mean of the steps' rates, ms_per_step = 1000 / value,
+cpu_baseline and e2e describing the same run; other ranks print nothing."""
+import json
+from types import SimpleNamespace
+
+import pytest
+
+import bench
+
+
+def _args(**kw):
+    a = dict(steps=3, warmup=2, backend="dino", impl="reference", batch=False)
+    a.update(kw)
+    return SimpleNamespace(**a)
+
+
+@pytest.fixture
+def stub(monkeypatch):
+    calls = []
+    rates = iter([9.0, 9.0, 2.0, 4.0, 6.0])   # two warm-up steps, then three timed
+
+    def fake(per_core=1, cores=None):
+        calls.append(per_core)
+        return next(rates), 8 * per_core, 8, 0.01
+
+    monkeypatch.setattr(bench, "cpu_oracle_dino_rate", fake)
+    monkeypatch.setattr(bench, "cpu_oracle_pde_rate", fake)
+    return calls
+
+
+def test_reference_line(stub, capsys, monkeypatch):
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_reference(_args())
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["higher_is_better"] is True
+    assert len(stub) == 5 and d["steps"] == 3 and d["warmup"] == 2
+    assert d["value"] == pytest.approx(4.0) and d["ms_per_step"] == pytest.approx(250.0)
+    assert d["unit"] == d["cpu_baseline"]["unit"] == d["e2e"]["unit"]
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] == 8 and "sample" in d["cpu_baseline"]
+    assert d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert "workload" in d["config"] and "model" not in d["config"]
+    assert d["vs_baseline"] is None and d["dtype"] == "f64"
+
+
+def test_other_ranks_print_nothing(stub, capsys, monkeypatch):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.run_reference(_args())
+    assert capsys.readouterr().out.strip() == "" and stub == []
