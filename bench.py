@@ -142,9 +142,15 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
+        with open(self.path) as fh:
+            return self.summarize(fh)
+
+    @staticmethod
+    def summarize(lines):
+        """Median and maximum SM clock and the throttle reasons seen, from CSV lines of QUERY."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue

@@ -1,7 +1,8 @@
 """The JSON line of bench.py's reference arm (the FP64 oracle on the host cores), CPU only,
 with the timed oracle replaced by a stub of known rate: one line from rank 0 with the
 contract's keys, a value that is the mean of the steps' rates, ms_per_step = 1000 / value,
-cpu_baseline and e2e describing the same run; other ranks print nothing."""
+cpu_baseline and e2e describing the same run; other ranks print nothing.  Also the summary of
+the nvidia-smi clock samples (median and maximum SM clock, throttle reasons seen)."""
 import json
 from types import SimpleNamespace
 
@@ -57,3 +58,19 @@ def test_other_ranks_print_nothing(stub, capsys, monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.run_reference(_args())
     assert capsys.readouterr().out.strip() == "" and stub == []
+
+
+def test_clock_summary():
+    lines = [
+        "0, 2070, 2070, 499.88, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 1950, 2070, 1390.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "0, 2010, 2070, 1200.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active\n",   # unreadable sample
+        "garbage\n",
+    ]
+    c = bench.ClockSampler.summarize(lines)
+    assert c["sm_mhz"] == 2010.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = bench.ClockSampler.summarize(["0, 1500, 2070, 1400, 0x8, Not Active, Active, Not Active, Not Active\n"])
+    assert hot["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.ClockSampler.summarize([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
