@@ -16,6 +16,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libouu.so")
 
 OUU_OK = 0
+OUU_ERR_INVALID_ARG = 1
+OUU_ERR_CUDA = 2
+OUU_ERR_OOM = 3
+OUU_ERR_NOT_CONVERGED = 4
+OUU_ERR_NONFINITE = 5
+OUU_ERR_STATE = 6
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE", 6: "STATE"}
 RISK_MEAN_VAR = 0
 RISK_CVAR_SMOOTH = 1

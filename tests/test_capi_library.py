@@ -62,3 +62,60 @@ def test_invalid_problem_is_rejected_on_the_host(lib):
         d = capi.problem_desc(**bad)
         assert L.ouu_create_problem(ctypes.byref(d), None, ctypes.byref(h)) == 1
         assert capi.last_error()
+
+
+def test_invalid_network_is_rejected_on_the_host(lib):
+    """ouu_dino_create checks its descriptor before any device work."""
+    from paper_2305_20053_gb300 import capi
+    L = capi.load()
+    h = ctypes.c_void_p()
+    for bad in (dict(n=6), dict(n=2049), dict(lattice_L=0), dict(r_u=300), dict(r_m=0), dict(width=12),
+                dict(max_batch=4), dict(max_eval=0), dict(gamma=0.0), dict(jac_weight=-1.0)):
+        d = capi.dino_desc(**bad)
+        assert L.ouu_dino_create(ctypes.byref(d), None, ctypes.byref(h)) == capi.OUU_ERR_INVALID_ARG, bad
+        assert capi.last_error() and h.value is None
+
+
+def test_null_handles_are_rejected(lib):
+    from paper_2305_20053_gb300 import capi
+    L = capi.load()
+    bad = capi.OUU_ERR_INVALID_ARG
+    x = ctypes.c_double(0.0)
+    r = capi.risk_desc(capi.RISK_MEAN_VAR)
+    assert L.ouu_sample_fields(None, 1, 0, 4, None) == bad
+    assert L.ouu_pde_solve_batch(None, None, 4, None, 0, None, None, None) == bad
+    assert L.ouu_adjoint_batch(None, None, None, 4, None, None) == bad
+    assert L.ouu_risk_and_grad(None, 0, None, None, 4, ctypes.byref(r), 1, ctypes.byref(x), ctypes.byref(x),
+                               ctypes.byref(x), ctypes.byref(x), None, None) == bad
+    assert L.ouu_dino_set_params(None, None, 0) == bad
+    assert L.ouu_dino_set_fused_network(None, 0) == bad
+    assert L.ouu_dino_set_graphs(None, 1) == bad
+    out = ctypes.c_void_p()
+    assert L.ouu_batch_create(None, 0, 0, ctypes.byref(out)) == bad
+    assert "problem is null" in (L.ouu_sample_fields(None, 1, 0, 4, None) and capi.last_error())
+    # destroying nothing succeeds; queries on nothing give zero
+    assert L.ouu_destroy_problem(None) == capi.OUU_OK and L.ouu_dino_destroy(None) == capi.OUU_OK
+    assert L.ouu_problem_slots(None) == 0 and L.ouu_dino_num_params(None) == 0
+
+
+def test_last_error_is_thread_local_and_truncates(lib):
+    import threading
+    from paper_2305_20053_gb300 import capi
+    L = capi.load()
+    assert L.ouu_dino_set_graphs(None, 1) == capi.OUU_ERR_INVALID_ARG
+    mine = capi.last_error()
+    seen = {}
+
+    def other():
+        seen["before"] = capi.last_error()
+        L.ouu_sample_fields(None, 1, 0, 4, None)
+        seen["after"] = capi.last_error()
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["before"] == "" and "problem is null" in seen["after"]
+    assert capi.last_error() == mine
+    buf = ctypes.create_string_buffer(8)
+    full = L.ouu_last_error(buf, 5)
+    assert full == len(mine.encode()) and buf.value == mine.encode()[:4]
