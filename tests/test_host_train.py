@@ -1,0 +1,25 @@
+"""Host logic of the surrogate construction loop, CPU only: the learning-rate schedule is
+the oracle's Sec. 4.2 schedule (lr0, then a quarter of it from half of the epochs on), and
+its optional geometric tail runs from lr1 at half of the epochs to lr_final at the last one."""
+import numpy as np
+import pytest
+
+from oracle import dino
+from paper_2305_20053_gb300 import train
+
+
+@pytest.mark.parametrize("epochs", [1, 2, 7, 200, 600])
+def test_schedule_is_the_papers(epochs):
+    for ep in range(epochs):
+        assert train.lr_at(ep, epochs) == dino.lr_schedule(ep, epochs)
+
+
+def test_geometric_tail():
+    epochs, lr1, lrf = 600, 2.5e-4, 1e-5
+    r = np.array([train.lr_at(ep, epochs, lr1=lr1, lr_final=lrf) for ep in range(epochs)])
+    half = epochs // 2
+    assert np.all(r[:half] == 1e-3)
+    assert r[half] == pytest.approx(lr1, rel=1e-12) and r[-1] == pytest.approx(lrf, rel=1e-12)
+    ratios = r[half + 1:] / r[half:-1]
+    np.testing.assert_allclose(ratios, ratios[0], rtol=1e-10)
+    assert ratios[0] < 1.0
