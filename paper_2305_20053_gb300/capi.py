@@ -163,6 +163,14 @@ def dev_ptr(t, dtype=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def need(t, count, name):
+    """Raises when the buffer t (tensor or array; None passes) holds fewer than count elements, so
+    that a short buffer is an error here instead of an out-of-bounds access in the library."""
+    size = None if t is None else (t.numel() if hasattr(t, "numel") else np.asarray(t).size)
+    if size is not None and size < count:
+        raise ValueError(f"{name}: {size} elements, the call needs {count}")
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -210,6 +218,7 @@ class Problem:
 
     def ouu_sample_fields(self, seed, first_index, n_samples, m_dev):
         import torch
+        need(m_dev, n_samples * self.n * self.n, "m_dev")
         check(load().ouu_sample_fields(self.handle, seed, first_index, n_samples, dev_ptr(m_dev, torch.float64)))
 
     def ouu_pde_solve_batch(self, m_dev, n_samples, z_dev, z_stride, u_dev, q_dev, status_dev):
@@ -371,6 +380,8 @@ class Dino:
 
     def ouu_dino_set_output_scale(self, s):
         s = np.ascontiguousarray(s, dtype=np.float32)
+        if s.size != self.desc.r_u:
+            raise ValueError(f"output scale: {s.size} entries, r_u = {self.desc.r_u}")
         check(load().ouu_dino_set_output_scale(self.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
 
     def ouu_dino_get_output_scale(self):
@@ -384,6 +395,12 @@ class Dino:
         import numpy as np
         import torch
         zz = np.ascontiguousarray(z, dtype=np.float64)
+        if zz.size != self.d_z:
+            raise ValueError(f"z: {zz.size} entries, d_Z = {self.d_z}")
+        need(xi, n_samples * self.desc.r_m, "xi")
+        need(q, n_samples, "q")
+        need(phi, n_samples * self.desc.r_u, "phi")
+        need(gradq, n_samples * self.d_z, "gradq")
         check(load().ouu_kernel_dino_network(self.handle, dev_ptr(xi, torch.float32), n_samples,
                                              zz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(mode),
                                              dev_ptr(q, torch.float64), dev_ptr(phi, torch.float32),
@@ -437,6 +454,13 @@ class Dino:
     def ouu_dino_eval(self, m_dev, n, z_host, phi_dev=None, jphi_dev=None, q_dev=None, gradq_dev=None):
         import torch
         z = np.ascontiguousarray(z_host, dtype=np.float64)
+        if z.size != self.d_z:
+            raise ValueError(f"z: {z.size} entries, d_Z = {self.d_z}")
+        d, nn = self.desc, self.desc.n * self.desc.n
+        for t, count, name in ((m_dev, n * nn, "m_dev"), (phi_dev, n * d.r_u, "phi_dev"),
+                               (jphi_dev, n * self.d_z * d.r_u, "jphi_dev"), (q_dev, n, "q_dev"),
+                               (gradq_dev, n * self.d_z, "gradq_dev")):
+            need(t, count, name)
         check(load().ouu_dino_eval(self.handle, dev_ptr(m_dev, torch.float64), n, z.ctypes.data_as(_dp),
                                    dev_ptr(phi_dev, torch.float32), dev_ptr(jphi_dev, torch.float32),
                                    dev_ptr(q_dev, torch.float64), dev_ptr(gradq_dev, torch.float64)))

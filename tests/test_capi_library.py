@@ -1,10 +1,12 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function that
-include/*.h declares (CPU only: no compute call is made)."""
+include/*.h declares; the host-side argument checks of the library and of the binding
+reject bad descriptors, null handles and short buffers (CPU only: no compute call is made)."""
 import ctypes
 import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -119,3 +121,29 @@ def test_last_error_is_thread_local_and_truncates(lib):
     buf = ctypes.create_string_buffer(8)
     full = L.ouu_last_error(buf, 5)
     assert full == len(mine.encode()) and buf.value == mine.encode()[:4]
+
+
+def test_binding_refuses_short_buffers():
+    """Sizes are checked in the binding before anything reaches the library (CPU only: the
+    handles below are never created, the checks raise first)."""
+    import torch
+    from paper_2305_20053_gb300 import capi
+    capi.need(None, 10, "x")
+    capi.need(np.zeros(10), 10, "x")
+    with pytest.raises(ValueError, match="x: 9 elements"):
+        capi.need(torch.zeros(3, 3), 10, "x")
+    P = object.__new__(capi.Problem)
+    P.n, P.d_z = 9, 4
+    with pytest.raises(ValueError, match="m_dev"):
+        P.ouu_sample_fields(1, 0, 3, torch.zeros(2, 9, 9, dtype=torch.float64))
+    D = object.__new__(capi.Dino)
+    D.desc, D.d_z = capi.dino_desc(n=9, lattice_L=2, r_m=8, r_u=5, width=16), 4
+    with pytest.raises(ValueError, match="output scale"):
+        D.ouu_dino_set_output_scale(np.ones(4))
+    with pytest.raises(ValueError, match="z: 3 entries"):
+        D.ouu_dino_eval(torch.zeros(2, 9, 9, dtype=torch.float64), 2, np.zeros(3))
+    with pytest.raises(ValueError, match="gradq_dev"):
+        D.ouu_dino_eval(torch.zeros(2, 9, 9, dtype=torch.float64), 2, np.zeros(4), None, None, None,
+                        torch.zeros(2, 3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="xi"):
+        D.ouu_kernel_dino_network(torch.zeros(2, 7), 2, np.zeros(4), 2)
