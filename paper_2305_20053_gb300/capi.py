@@ -223,12 +223,22 @@ class Problem:
 
     def ouu_pde_solve_batch(self, m_dev, n_samples, z_dev, z_stride, u_dev, q_dev, status_dev):
         import torch
+        nn = self.n * self.n
+        for t, count, name in ((m_dev, n_samples * nn, "m_dev"), (u_dev, n_samples * nn, "u_dev"),
+                               (z_dev, z_stride * (n_samples - 1) + self.d_z if n_samples > 0 else 0, "z_dev"),
+                               (q_dev, n_samples, "q_dev"), (status_dev, n_samples, "status_dev")):
+            need(t, count, name)
         check(load().ouu_pde_solve_batch(self.handle, dev_ptr(m_dev, torch.float64), n_samples,
                                          dev_ptr(z_dev, torch.float64), z_stride, dev_ptr(u_dev, torch.float64),
                                          dev_ptr(q_dev, torch.float64), dev_ptr(status_dev, torch.int32)))
 
     def ouu_adjoint_batch(self, m_dev, u_dev, n_samples, lambda_dev, gradq_dev):
         import torch
+        nn = self.n * self.n
+        for t, count, name in ((m_dev, n_samples * nn, "m_dev"), (u_dev, n_samples * nn, "u_dev"),
+                               (lambda_dev, n_samples * nn, "lambda_dev"),
+                               (gradq_dev, n_samples * self.d_z, "gradq_dev")):
+            need(t, count, name)
         check(load().ouu_adjoint_batch(self.handle, dev_ptr(m_dev, torch.float64), dev_ptr(u_dev, torch.float64),
                                        n_samples, dev_ptr(lambda_dev, torch.float64),
                                        dev_ptr(gradq_dev, torch.float64)))
@@ -238,6 +248,7 @@ class Problem:
         The ctypes argument blocks are kept between calls with the same risk descriptors
         (marshalling only; the returned arrays are fresh copies)."""
         import torch
+        need(m_dev, n_samples * self.n * self.n, "m_dev")
         key = tuple(bytes(r) for r in risks)
         c = getattr(self, "_rg_cache", None)
         if c is None or c["key"] != key:

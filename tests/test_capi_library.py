@@ -136,6 +136,18 @@ def test_binding_refuses_short_buffers():
     P.n, P.d_z = 9, 4
     with pytest.raises(ValueError, match="m_dev"):
         P.ouu_sample_fields(1, 0, 3, torch.zeros(2, 9, 9, dtype=torch.float64))
+    m3 = torch.zeros(3, 9, 9, dtype=torch.float64)
+    q3, s3 = torch.zeros(3, dtype=torch.float64), torch.zeros(3, dtype=torch.int32)
+    with pytest.raises(ValueError, match="u_dev"):
+        P.ouu_pde_solve_batch(m3, 3, torch.zeros(4), 0, m3[:2], q3, s3)
+    with pytest.raises(ValueError, match="z_dev: 11 elements, the call needs 12"):   # 4 (3 - 1) + 4
+        P.ouu_pde_solve_batch(m3, 3, torch.zeros(11), 4, None, q3, s3)
+    with pytest.raises(ValueError, match="status_dev"):
+        P.ouu_pde_solve_batch(m3, 3, torch.zeros(4), 0, None, q3, s3[:2])
+    with pytest.raises(ValueError, match="gradq_dev"):
+        P.ouu_adjoint_batch(m3, m3, 3, None, torch.zeros(3, 3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="m_dev"):
+        P.ouu_risk_and_grad(capi.BACKEND_PDE, None, m3, 4, [capi.risk_desc(capi.RISK_MEAN_VAR)], np.zeros(4))
     D = object.__new__(capi.Dino)
     D.desc, D.d_z = capi.dino_desc(n=9, lattice_L=2, r_m=8, r_u=5, width=16), 4
     with pytest.raises(ValueError, match="output scale"):
