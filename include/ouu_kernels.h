@@ -25,8 +25,11 @@
  *   xi[s][c] = bias[c] + sum_k bf16(m[s][k]) W[c][k],   s < N, c < rm, k < nn,
  * reading the FP64 fields m [N][nn] (device, 8-byte aligned, row-major) once; the
  * rounding to BF16 goes through FP32 (both to nearest even).  W: device BF16
- * [rm][ldw] (ldw a multiple of 8, >= nn).  bias: device FP32 [rm].  xi: device FP32
- * [N][rm], overwritten.  rm <= 240.  err_dev as above.
+ * [rm][ldw] (ldw a multiple of 8, >= nn).  bias: device FP32 [rm], added once per row.
+ * xi: device FP32 [N][rm], overwritten; any 4-byte aligned address (partial sums are added
+ * by atomics, 16-byte vector ones and TMA bulk reductions of whole rows when rm % 4 == 0 and
+ * xi is 16-byte aligned).  rm <= 240.
+ * err_dev as above.
  *
  * ouu_kernel_risk_weights: the per-sample risk weights of the SAA gradient (Sec. 2.1-2.2)
  * from the QoIs q_dev [N] (device FP64): for each of the n_risks (1..4) host descriptors,

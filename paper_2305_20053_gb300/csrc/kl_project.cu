@@ -443,7 +443,8 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
       tc_fence_after();
       const int r = d.x * 128 + q * 32 + lane;
       float* orow = a.xi + (size_t)r * a.rm;
-      const bool vec4 = (a.rm & 3) == 0;
+      // 16-byte vector atomics need every row start 16-byte aligned
+      const bool vec4 = (a.rm & 3) == 0 && (reinterpret_cast<uintptr_t>(a.xi) & 15) == 0;
       if ((d.y & 2) && a.bulk) {
         // The CTA's final visit, when every CTA flushes at once: the rows go through the
         // (now idle) FP64 stages and are added into xi by the TMA engine, one bulk reduction
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
             float y[4];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
-              y[jj] = __uint_as_float(v[i + jj]) + ((d.y && c + jj < a.rm) ? a.bias[c + jj] : 0.f);
+              y[jj] = __uint_as_float(v[i + jj]) + (((d.y & 1) && c + jj < a.rm) ? a.bias[c + jj] : 0.f);
             if (vec4) {
               atomicAdd(reinterpret_cast<float4*>(orow + c), make_float4(y[0], y[1], y[2], y[3]));
             } else {
@@ -572,6 +573,7 @@ ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W
   OUU_CHECK_ARG(m && W && bias && xi && err && ctr, "null argument");
   OUU_CHECK_ARG(N >= 1 && nn >= 1 && rm >= 1 && rm <= 240, "KL projection sizes: N, n^2 >= 1, 1 <= r_m <= 240");
   OUU_CHECK_ARG(((uintptr_t)m & 7) == 0, "fields must be 8-byte aligned");
+  OUU_CHECK_ARG(((uintptr_t)xi & 3) == 0, "xi must be 4-byte aligned");
   const int BN = (rm + 15) / 16 * 16;
   CUtensorMap tw;
   if (!ouu_tmap_bf16(&tw, W, (uint64_t)nn, (uint64_t)rm, (uint64_t)ldw, (uint32_t)BN)) {

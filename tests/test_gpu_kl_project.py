@@ -7,7 +7,9 @@ entry of each row, 1e-5 + 5e-7 sqrt(n^2).
 Cases: n^2 odd (sample-pair tensor map) and even (row tensor map); N even, odd (a
 last unpaired sample read with plain loads), one sample (plain loads only), a base
 8 bytes off a 16-byte boundary (plain loads), a ragged last 128-sample tile, a ragged
-last 64-wide K block, r_m not a multiple of 16, and the 129 x 129 width.
+last 64-wide K block, r_m not a multiple of 16, r_m not a multiple of 4 (every partial sum by
+scalar atomics, the bias added once per row whichever visit of a tile a CTA ends on), an
+output 4 bytes off a 16-byte boundary, and the 129 x 129 width.
 """
 import math
 
@@ -28,7 +30,7 @@ def built():
 
 
 @pytest.mark.parametrize("N,nn,rm", [(40, 289, 16), (131, 289, 200), (1, 289, 16), (3, 300, 24), (129, 1024, 52),
-                                     (257, 16641, 200)])
+                                     (300, 289, 30), (257, 16641, 200)])
 def test_kl_project_parity(N, nn, rm):
     from paper_2305_20053_gb300 import capi
     rng = np.random.default_rng(1000 + N + nn + rm)
@@ -71,6 +73,31 @@ def test_kl_project_offset_base():
     ref = round_bf16(m_d.cpu().numpy()) @ W[:, :nn].T
     scale = np.abs(ref).max(axis=1, keepdims=True)
     assert np.all(np.abs(xi.cpu().numpy() - ref) <= (1e-5 + 5e-7 * math.sqrt(nn)) * scale)
+
+
+def test_kl_project_unaligned_output():
+    """xi starting 4 bytes past a 16-byte boundary: no vector atomics, no bulk reductions."""
+    from paper_2305_20053_gb300 import capi
+    N, nn, rm = 300, 289, 16
+    rng = np.random.default_rng(78)
+    m = rng.standard_normal((N, nn))
+    W = np.zeros((rm, 320))
+    W[:, :nn] = round_bf16(rng.standard_normal((rm, nn)) / 17.0)
+    bias = rng.standard_normal(rm).astype(np.float32)
+    m_d = torch.tensor(m, device="cuda")
+    W_d = torch.tensor(W, device="cuda").to(torch.bfloat16)
+    b_d = torch.tensor(bias, device="cuda")
+    buf = torch.full((N * rm + 4,), float("nan"), device="cuda", dtype=torch.float32)
+    xi = buf[1:1 + N * rm].view(N, rm)
+    assert xi.data_ptr() % 16 == 4
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    capi.ouu_kernel_kl_project(m_d, N, nn, W_d, rm, b_d, xi, err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert torch.isnan(buf[0]).item() and torch.isnan(buf[1 + N * rm:]).all().item()
+    ref = round_bf16(m) @ W[:, :nn].T + bias.astype(np.float64)
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(xi.cpu().numpy().astype(np.float64) - ref) <= (1e-5 + 5e-7 * math.sqrt(nn)) * scale)
 
 
 def test_kl_project_several_launches_and_repeat():
