@@ -433,6 +433,10 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   OUU_CHECK_ARG((ep.mode != EPI_DGELU_SCALE && ep.mode != EPI_SCALE) || (ep.aux && ep.aux_rdiv >= 1),
                 "EPI_DGELU_SCALE and EPI_SCALE need aux");
   OUU_CHECK_ARG(splits >= 1 && splits <= 64, "split-K factor in [1, 64]");
+  {   // every K slice must own a K block: an empty slice would add an unwritten accumulator
+    const int kb_all = (K + GEMM_BK - 1) / GEMM_BK, per = (kb_all + splits - 1) / splits;
+    OUU_CHECK_ARG((splits - 1) * per < kb_all, "split-K factor leaves a slice without a K block");
+  }
   OUU_CHECK_ARG(splits == 1 || (ep.mode == EPI_LINEAR && ep.out_f32 && !ep.out_bf16 && !ep.out_t_bf16 &&
                                 !ep.out2_bf16 && !ep.col_scale && !ep.accumulate),
                 "split-K supports one FP32 output of EPI_LINEAR, accumulated into a zeroed buffer");
