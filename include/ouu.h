@@ -103,8 +103,9 @@ void ouu_default_problem_desc(ouu_problem_desc* desc);
 
 /* Creates a problem handle bound to `cuda_stream` (a cudaStream_t, or NULL for the
  * legacy default stream) on the current device and allocates its workspace for
- * up to desc->max_samples samples.  Errors: INVALID_ARG (grid not 2^k+1, L < 1,
- * widths <= 0), OOM, CUDA. */
+ * up to desc->max_samples samples.  Errors: INVALID_ARG (grid not 2^k+1 with
+ * 5 <= n <= 1025, L outside [1, 64], widths <= 0, L * n * 8 bytes above the device's
+ * shared memory per block), OOM, CUDA. */
 ouu_status ouu_create_problem(const ouu_problem_desc* desc, void* cuda_stream, ouu_problem_t* out);
 ouu_status ouu_destroy_problem(ouu_problem_t p);
 

@@ -193,6 +193,11 @@ extern "C" ouu_status ouu_create_problem(const ouu_problem_desc* desc, void* cud
     ouu_set_error("multigrid shared-memory levels exceed the device limit");
     return OUU_ERR_INVALID_ARG;
   }
+  if ((int64_t)L * n * (int64_t)sizeof(double) > smem_optin) {   // the G^T s reduction stages [L][n] in shared memory
+    delete p;
+    ouu_set_error("lattice_L * n too large for the gradient reduction's shared memory");
+    return OUU_ERR_INVALID_ARG;
+  }
   p->nslots = std::min(p->num_sms, desc->max_samples);
   const int64_t nn = (int64_t)n * n;
   const int64_t N = desc->max_samples;
