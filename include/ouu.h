@@ -200,7 +200,7 @@ ouu_status ouu_pde_solve_batch_noalloc(const ouu_problem_desc* desc, const doubl
 typedef struct {
   int n;              /* grid of the states (nodes per side), 2^k + 1 */
   int lattice_L;      /* d_Z = L^2 controls */
-  int r_m, r_u;       /* reduced ranks of m (KL) and u (POD), <= 256 */
+  int r_m, r_u;       /* reduced ranks of m (KL, <= 240) and u (POD, <= 256) */
   int width;          /* hidden width (three hidden layers), multiple of 8 */
   int max_batch;      /* largest training batch (also the Jacobian chunk of ouu_dino_eval) */
   int max_eval;       /* largest n_samples of an evaluation */

@@ -351,7 +351,8 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   const int n = desc->n;
   OUU_CHECK_ARG(n >= 5 && n <= 1025 && (((n - 1) & (n - 2)) == 0), "n must be 2^k + 1");
   OUU_CHECK_ARG(desc->lattice_L >= 1 && desc->lattice_L <= 64, "lattice_L must be in [1, 64]");
-  OUU_CHECK_ARG(desc->r_m >= 1 && desc->r_m <= n * n && desc->r_u >= 1 && desc->r_u <= 256, "bad ranks");
+  OUU_CHECK_ARG(desc->r_m >= 1 && desc->r_m <= n * n && desc->r_m <= 240 && desc->r_u >= 1 && desc->r_u <= 256,
+                "ranks: 1 <= r_m <= min(n^2, 240) (the projection's N tile), 1 <= r_u <= 256");
   OUU_CHECK_ARG(desc->width >= 8 && desc->width % 8 == 0 && desc->width <= 2048, "width: multiple of 8");
   OUU_CHECK_ARG(desc->max_batch >= 8 && desc->max_batch % 8 == 0, "max_batch: positive multiple of 8");
   OUU_CHECK_ARG(desc->max_eval >= 1, "max_eval must be positive");

@@ -71,7 +71,7 @@ def test_invalid_network_is_rejected_on_the_host(lib):
     from paper_2305_20053_gb300 import capi
     L = capi.load()
     h = ctypes.c_void_p()
-    for bad in (dict(n=6), dict(n=2049), dict(lattice_L=0), dict(r_u=300), dict(r_m=0), dict(width=12),
+    for bad in (dict(n=6), dict(n=2049), dict(lattice_L=0), dict(r_u=300), dict(r_m=0), dict(r_m=241), dict(width=12),
                 dict(max_batch=4), dict(max_eval=0), dict(gamma=0.0), dict(jac_weight=-1.0)):
         d = capi.dino_desc(**bad)
         assert L.ouu_dino_create(ctypes.byref(d), None, ctypes.byref(h)) == capi.OUU_ERR_INVALID_ARG, bad
