@@ -77,13 +77,7 @@ static ouu_status check_item(const ouu_batch_item& it) {
   OUU_CHECK_ARG(it.problem && it.m_dev, "batch item: problem and fields are required");
   ouu_problem* p = it.problem;
   OUU_CHECK_ARG(it.n_samples >= 1 && it.n_samples <= p->desc.max_samples, "batch item: n_samples outside [1, max_samples]");
-  OUU_CHECK_ARG(it.risks && it.n_risks >= 1 && it.n_risks <= OUU_MAX_RISKS, "batch item: 1..4 risk descriptors");
-  for (int r = 0; r < it.n_risks; ++r) {
-    const ouu_risk_desc& R = it.risks[r];
-    OUU_CHECK_ARG(R.kind == OUU_RISK_MEAN_VAR ||
-                      (R.kind == OUU_RISK_CVAR_SMOOTH && R.beta >= 0 && R.beta < 1 && R.eps > 0 && std::isfinite(R.t)),
-                  "batch item: bad risk descriptor");
-  }
+  if (ouu_status st = ouu_check_risks(it.risks, it.n_risks)) return st;
   OUU_CHECK_ARG(it.backend == OUU_BACKEND_PDE || it.backend == OUU_BACKEND_DINO, "batch item: unknown backend");
   if (it.backend == OUU_BACKEND_DINO) {
     ouu_dino* d = it.dino;

@@ -373,7 +373,7 @@ extern "C" ouu_status ouu_adjoint_batch(ouu_problem_t p, const double* m_dev, co
   return check_statuses(p, n_samples);
 }
 
-static ouu_status check_risks(const ouu_risk_desc* risks, int n_risks) {
+ouu_status ouu_check_risks(const ouu_risk_desc* risks, int n_risks) {
   OUU_CHECK_ARG(risks != nullptr && n_risks >= 1 && n_risks <= OUU_MAX_RISKS, "need 1..4 risk descriptors");
   for (int r = 0; r < n_risks; ++r) {
     const ouu_risk_desc& R = risks[r];
@@ -417,7 +417,7 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
   OUU_CHECK_ARG(p != nullptr, "problem is null");
   OUU_CHECK_ARG(n_samples >= 1 && n_samples <= p->desc.max_samples, "n_samples outside [1, max_samples]");
   OUU_CHECK_ARG(m_dev && z_host && risk_out && grad_z_out && grad_t_out, "null argument");
-  if (ouu_status st = check_risks(risks, n_risks)) return st;
+  if (ouu_status st = ouu_check_risks(risks, n_risks)) return st;
   for (int j = 0; j < p->dz; ++j) OUU_CHECK_ARG(std::isfinite(z_host[j]), "z has a non-finite entry");
   RiskDev rd[OUU_MAX_RISKS];
   std::memset(rd, 0, sizeof(rd));   // padding too: the descriptors are compared bytewise below

@@ -15,6 +15,10 @@ void ouu_set_error(const std::string& msg);
 // cannot undo each other's limit.  Kept per device (the current one).
 cudaError_t ouu_smem_limit(const void* fn, size_t bytes);
 
+// Checks 1..OUU_MAX_RISKS risk descriptors (known kind; finite kappa; beta in [0, 1), eps > 0
+// and finite t for the smoothed CVaR); INVALID_ARG with a message otherwise.
+ouu_status ouu_check_risks(const ouu_risk_desc* risks, int n_risks);
+
 // ------------------------------------------------------------------ programmatic dependent launch
 // Kernels launched with launch_pdl may start while the previous kernel in the stream drains
 // (their set-up overlaps its tail); each calls pdl_wait() before it reads or writes global
