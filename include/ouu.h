@@ -51,7 +51,9 @@ typedef enum {
 } ouu_status;
 
 typedef enum { OUU_RISK_MEAN_VAR = 0, OUU_RISK_CVAR_SMOOTH = 1 } ouu_risk_kind;
-typedef enum { OUU_BACKEND_PDE = 0, OUU_BACKEND_DINO = 1 } ouu_backend;
+/* OUU_BACKEND_AUTO: the MR-DINO surrogate when it passed its held-out check against the plain
+ * path for this problem (ouu_dino_validate), else the plain path. */
+typedef enum { OUU_BACKEND_PDE = 0, OUU_BACKEND_DINO = 1, OUU_BACKEND_AUTO = 2 } ouu_backend;
 
 /* Per-sample status words written by the solve calls. */
 enum { OUU_SAMPLE_OK = 0, OUU_SAMPLE_NOT_CONVERGED = 1, OUU_SAMPLE_NONFINITE = 2 };
@@ -145,13 +147,34 @@ ouu_status ouu_adjoint_batch(ouu_problem_t p, const double* m_dev, const double*
  * weights, then one adjoint solve per sample whose weight is nonzero in some
  * risk, accumulating sum_i w_i lambda_i and applying G^T once.  Backend DINO:
  * the MR-DINO surrogate (`dino` must be non-NULL and trained), see
- * ouu_dino_eval.  Outputs (host): risk_out[n_risks], grad_z_out[n_risks][d_Z],
+ * ouu_dino_eval.  Backend AUTO: DINO when `dino` passed ouu_dino_validate against this
+ * problem since its last change and can take n_samples, else PDE (ouu_last_backend tells
+ * which ran).  Outputs (host): risk_out[n_risks], grad_z_out[n_risks][d_Z],
  * grad_t_out[n_risks] (d rho / dt for CVaR, 0 for mean+var), t_out[n_risks]
  * (t used; may be NULL), stats (may be NULL).  Synchronises the stream. */
 ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ouu_dino_t dino, const double* m_dev,
                              int n_samples, const ouu_risk_desc* risks, int n_risks, const double* z_host,
                              double* risk_out, double* grad_z_out, double* grad_t_out, double* t_out,
                              ouu_eval_stats* stats);
+
+/* Backend of the last ouu_risk_and_grad on p that returned OUU_OK (OUU_BACKEND_PDE or
+ * OUU_BACKEND_DINO); -1 before any, or for p == NULL. */
+int ouu_last_backend(ouu_problem_t p);
+
+/* Held-out check of the surrogate with the plain path as the judge (the paper's accuracy
+ * study of Sec. 4 as a gate): at each of the n_z controls z_host [n_z][d_Z], both backends
+ * evaluate the n_risks risks over the held-out fields m_dev [n_samples][n][n] (samples not
+ * used for training); the largest relative risk error |rho_DINO - rho_PDE| / |rho_PDE| and
+ * the largest relative gradient error ||g_DINO - g_PDE|| / ||g_PDE|| over controls and risks
+ * go to risk_err_out / grad_err_out (host, nullable).  The network passes when they are
+ * <= risk_tol and <= grad_tol (passed_out, nullable: 1 or 0); OUU_BACKEND_AUTO then uses it
+ * for this problem until its parameters, bases or output scale change or it takes a training
+ * step.  A failed check, or an error part-way, leaves it unused by AUTO.  Errors as
+ * ouu_risk_and_grad; INVALID_ARG for n_z < 1 or a negative or non-finite tolerance. */
+ouu_status ouu_dino_validate(ouu_problem_t p, ouu_dino_t d, const double* m_dev, int n_samples,
+                             const ouu_risk_desc* risks, int n_risks, const double* z_host, int n_z,
+                             double risk_tol, double grad_tol, double* risk_err_out, double* grad_err_out,
+                             int* passed_out);
 
 /* Allocation-free variant of ouu_pde_solve_batch.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory when

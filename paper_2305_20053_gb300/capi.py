@@ -27,6 +27,7 @@ RISK_MEAN_VAR = 0
 RISK_CVAR_SMOOTH = 1
 BACKEND_PDE = 0
 BACKEND_DINO = 1
+BACKEND_AUTO = 2
 
 
 class OuuError(RuntimeError):
@@ -85,6 +86,9 @@ SIGNATURES = {
     "ouu_risk_and_grad": (_i, [_vp, _i, _vp, _vp, _i, ctypes.POINTER(RiskDesc), _i, _dp, _dp, _dp, _dp, _dp,
                                ctypes.POINTER(EvalStats)]),
     "ouu_pde_solve_batch_noalloc": (_i, [ctypes.POINTER(ProblemDesc), _vp, _i, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "ouu_last_backend": (_i, [_vp]),
+    "ouu_dino_validate": (_i, [_vp, _vp, _vp, _i, ctypes.POINTER(RiskDesc), _i, _dp, _i, ctypes.c_double,
+                               ctypes.c_double, _dp, _dp, ctypes.POINTER(ctypes.c_int)]),
     "ouu_default_dino_desc": (None, [ctypes.POINTER(DinoDesc)]),
     "ouu_dino_create": (_i, [ctypes.POINTER(DinoDesc), _vp, ctypes.POINTER(_vp)]),
     "ouu_dino_destroy": (_i, [_vp]),
@@ -215,6 +219,10 @@ class Problem:
 
     def slots(self) -> int:
         return load().ouu_problem_slots(self.handle)
+
+    def ouu_last_backend(self) -> int:
+        """BACKEND_PDE or BACKEND_DINO: what the last successful ouu_risk_and_grad ran (-1: none yet)."""
+        return load().ouu_last_backend(self.handle)
 
     def ouu_sample_fields(self, seed, first_index, n_samples, m_dev):
         import torch
@@ -416,6 +424,22 @@ class Dino:
                                              zz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(mode),
                                              dev_ptr(q, torch.float64), dev_ptr(phi, torch.float32),
                                              dev_ptr(gradq, torch.float64)))
+
+    def ouu_dino_validate(self, problem, m_dev, n_samples, risks, zs, risk_tol=0.01, grad_tol=0.05):
+        """Held-out check against the plain path at the controls zs [n_z][d_Z]; returns
+        (largest relative risk error, largest relative gradient error, passed).  While passed,
+        BACKEND_AUTO evaluations of `problem` use this network."""
+        import torch
+        zz = np.ascontiguousarray(np.atleast_2d(zs), dtype=np.float64)
+        if zz.ndim != 2 or zz.shape[1] != self.d_z:
+            raise ValueError(f"zs: shape {zz.shape}, expected (n_z, {self.d_z})")
+        need(m_dev, n_samples * self.desc.n * self.desc.n, "m_dev")
+        arr = (RiskDesc * len(risks))(*risks)
+        er, eg, ok = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        check(load().ouu_dino_validate(problem.handle, self.handle, dev_ptr(m_dev, torch.float64), n_samples, arr,
+                                       len(risks), zz.ctypes.data_as(_dp), zz.shape[0], float(risk_tol),
+                                       float(grad_tol), ctypes.byref(er), ctypes.byref(eg), ctypes.byref(ok)))
+        return er.value, eg.value, bool(ok.value)
 
     def ouu_dino_set_fused_network(self, mode):
         """0: per-layer GEMM kernels, 1: one kernel per 128-sample tile, 2: 4-CTA clusters."""

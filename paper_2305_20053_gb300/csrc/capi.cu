@@ -1,5 +1,6 @@
 // C ABI: problem handle, argument checks, launches, host results.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -168,6 +169,8 @@ extern "C" ouu_status ouu_create_problem(const ouu_problem_desc* desc, void* cud
   *out = nullptr;
   if (ouu_status st = check_desc(desc)) return st;
   ouu_problem* p = new ouu_problem();
+  static std::atomic<uint64_t> next_serial{1};
+  p->serial = next_serial++;
   p->desc = *desc;
   p->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&p->device) != cudaSuccess ||
@@ -410,10 +413,11 @@ ouu_status dino_enqueue_risk(ouu_problem* p, ouu_dino* dino, const double* m_dev
   return OUU_OK;
 }
 
-extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ouu_dino_t dino, const double* m_dev,
-                                        int n_samples, const ouu_risk_desc* risks, int n_risks, const double* z_host,
-                                        double* risk_out, double* grad_z_out, double* grad_t_out, double* t_out,
-                                        ouu_eval_stats* stats) {
+// One risk evaluation on the given backend (OUU_BACKEND_PDE or OUU_BACKEND_DINO).
+static ouu_status risk_and_grad_on(ouu_problem_t p, ouu_backend backend, ouu_dino_t dino, const double* m_dev,
+                                   int n_samples, const ouu_risk_desc* risks, int n_risks, const double* z_host,
+                                   double* risk_out, double* grad_z_out, double* grad_t_out, double* t_out,
+                                   ouu_eval_stats* stats) {
   OUU_CHECK_ARG(p != nullptr, "problem is null");
   OUU_CHECK_ARG(n_samples >= 1 && n_samples <= p->desc.max_samples, "n_samples outside [1, max_samples]");
   OUU_CHECK_ARG(m_dev && z_host && risk_out && grad_z_out && grad_t_out, "null argument");
@@ -603,6 +607,81 @@ extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ou
     ouu_set_error("non-finite residual in some sample");
     return OUU_ERR_NONFINITE;
   }
+  return OUU_OK;
+}
+
+// The network may stand in for the plain path: it passed its held-out check against this
+// problem and can take this many samples.
+static bool dino_trusted(const ouu_dino* d, const ouu_problem* p, int n_samples) {
+  return d && d->val_ok && d->val_serial == p->serial && d->bases_ready && n_samples <= d->maxE;
+}
+
+extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ouu_dino_t dino, const double* m_dev,
+                                        int n_samples, const ouu_risk_desc* risks, int n_risks, const double* z_host,
+                                        double* risk_out, double* grad_z_out, double* grad_t_out, double* t_out,
+                                        ouu_eval_stats* stats) {
+  OUU_CHECK_ARG(p != nullptr, "problem is null");
+  OUU_CHECK_ARG(backend == OUU_BACKEND_PDE || backend == OUU_BACKEND_DINO || backend == OUU_BACKEND_AUTO,
+                "unknown backend");
+  if (backend == OUU_BACKEND_AUTO)
+    backend = dino_trusted(dino, p, n_samples) ? OUU_BACKEND_DINO : OUU_BACKEND_PDE;
+  const ouu_status st = risk_and_grad_on(p, backend, dino, m_dev, n_samples, risks, n_risks, z_host, risk_out,
+                                         grad_z_out, grad_t_out, t_out, stats);
+  if (st == OUU_OK) p->last_backend = backend;
+  return st;
+}
+
+extern "C" int ouu_last_backend(ouu_problem_t p) { return p ? p->last_backend : -1; }
+
+// Relative error |a - b| / |b| (0 when both are zero; NaN stays NaN).
+static double rel_err(double a, double b) {
+  const double d = std::fabs(a - b), s = std::fabs(b);
+  return s > 0 ? d / s : (d == 0 ? 0.0 : INFINITY);
+}
+
+extern "C" ouu_status ouu_dino_validate(ouu_problem_t p, ouu_dino_t d, const double* m_dev, int n_samples,
+                                        const ouu_risk_desc* risks, int n_risks, const double* z_host, int n_z,
+                                        double risk_tol, double grad_tol, double* risk_err_out, double* grad_err_out,
+                                        int* passed_out) {
+  OUU_CHECK_ARG(p && d && m_dev && z_host, "null argument");
+  OUU_CHECK_ARG(n_z >= 1, "need at least one control");
+  OUU_CHECK_ARG(std::isfinite(risk_tol) && std::isfinite(grad_tol) && risk_tol >= 0 && grad_tol >= 0,
+                "tolerances must be finite and >= 0");
+  OUU_CHECK_ARG(n_risks >= 1 && n_risks <= OUU_MAX_RISKS, "need 1..4 risk descriptors");
+  d->val_ok = 0;   // a check that fails or stops part-way leaves the network untrusted
+  const int dz = p->dz;
+  std::vector<double> r0(n_risks), r1(n_risks), g0((size_t)n_risks * dz), g1((size_t)n_risks * dz),
+      t0(n_risks), t1(n_risks);
+  double er = 0.0, eg = 0.0;
+  for (int k = 0; k < n_z; ++k) {
+    const double* z = z_host + (size_t)k * dz;
+    if (ouu_status st = risk_and_grad_on(p, OUU_BACKEND_PDE, nullptr, m_dev, n_samples, risks, n_risks, z,
+                                         r0.data(), g0.data(), t0.data(), nullptr, nullptr))
+      return st;
+    if (ouu_status st = risk_and_grad_on(p, OUU_BACKEND_DINO, d, m_dev, n_samples, risks, n_risks, z, r1.data(),
+                                         g1.data(), t1.data(), nullptr, nullptr))
+      return st;
+    for (int r = 0; r < n_risks; ++r) {
+      const double e = rel_err(r1[r], r0[r]);
+      if (!(e <= er)) er = e;   // a NaN error sticks
+      double dd = 0.0, nn = 0.0;
+      for (int j = 0; j < dz; ++j) {
+        const double a = g1[(size_t)r * dz + j], b = g0[(size_t)r * dz + j];
+        dd += (a - b) * (a - b);
+        nn += b * b;
+      }
+      const double eg_r = nn > 0 ? std::sqrt(dd / nn) : (dd == 0 ? 0.0 : INFINITY);
+      if (!(eg_r <= eg)) eg = eg_r;
+    }
+  }
+  const bool passed = er <= risk_tol && eg <= grad_tol;
+  if (passed) {
+    d->val_ok = 1;
+    d->val_serial = p->serial;
+  }
+  if (risk_err_out) *risk_err_out = er;
+  if (grad_err_out) *grad_err_out = eg;
+  if (passed_out) *passed_out = passed ? 1 : 0;
   return OUU_OK;
 }
 

@@ -517,6 +517,7 @@ static void refresh_bf16_weights(ouu_dino* d) {
 extern "C" ouu_status ouu_dino_set_params(ouu_dino_t d, const float* params_host, size_t n) {
   OUU_CHECK_ARG(d && params_host, "null argument");
   OUU_CHECK_ARG(n == d->n_params, "parameter count mismatch");
+  d->val_ok = 0;   // another network: its held-out check is to be done again
   OUU_CUDA_TRY(cudaMemcpyAsync(d->d_params, params_host, n * 4, cudaMemcpyHostToDevice, d->stream));
   OUU_CUDA_TRY(cudaMemsetAsync(d->d_adam_m, 0, n * 4, d->stream));
   OUU_CUDA_TRY(cudaMemsetAsync(d->d_adam_v, 0, n * 4, d->stream));
@@ -536,6 +537,7 @@ extern "C" ouu_status ouu_dino_get_params(ouu_dino_t d, float* params_host, size
 
 // Installs Phi (FP64 copy already in d_phi64) and ubar: FP32 copy, c and the constant.
 ouu_status dino_install_bases(ouu_dino* d) {
+  d->val_ok = 0;
   const int64_t cnt = (int64_t)d->ru * d->nn;
   k_phi_to_f32<<<grid_for(cnt), 256, 0, d->stream>>>(d->d_phi64, cnt, d->d_phi);
   k_reduced_qoi_terms<<<d->ru + 1, 256, 0, d->stream>>>(d->d_phi64, d->d_ubar, d->d_ut, d->n, d->ru, d->d_c,
@@ -751,6 +753,7 @@ extern "C" ouu_status ouu_dino_train_step(ouu_dino_t d, const float* xi_dev, con
                                           double* loss_out) {
   DINO_TRY(check_batch(d, xi_dev, z_dev, y_dev, jy_dev, idx_dev, batch));
   OUU_CHECK_ARG(lr > 0 && std::isfinite(lr), "lr must be positive");
+  d->val_ok = 0;
   DINO_TRY(loss_and_grad(d, xi_dev, z_dev, y_dev, jy_dev, idx_dev, batch));
   d->adam_t += 1;
   const double c1 = 1.0 - std::pow(0.9, d->adam_t), c2 = 1.0 - std::pow(0.999, d->adam_t);
@@ -915,6 +918,7 @@ extern "C" ouu_status ouu_kernel_dino_network(ouu_dino_t d, const float* xi_dev,
 extern "C" ouu_status ouu_dino_set_output_scale(ouu_dino_t d, const float* s_host) {
   OUU_CHECK_ARG(d && s_host, "null argument");
   for (int r = 0; r < d->ru; ++r) OUU_CHECK_ARG(s_host[r] > 0 && std::isfinite(s_host[r]), "scales must be positive");
+  d->val_ok = 0;
   OUU_CUDA_TRY(cudaMemcpyAsync(d->d_oscale, s_host, (size_t)d->ru * 4, cudaMemcpyHostToDevice, d->stream));
   OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
   return OUU_OK;

@@ -74,6 +74,10 @@ struct ouu_dino {
                                    // 128-sample tile (mlp_fused.cu), 2 one kernel over 4-CTA
                                    // clusters (mlp_cluster.cu); 1 and 2 when the sizes fit
   bool capturing = false;
+  // held-out check against the plain path (ouu_dino_validate): passed for the problem with this
+  // serial; cleared whenever parameters, bases or output scale change
+  int val_ok = 0;
+  uint64_t val_serial = 0;
 };
 
 // DINO forward/backward pieces used by the C ABI (dino.cu).

@@ -231,6 +231,8 @@ struct ouu_problem {
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // evaluation phase timers
   double* h_out = nullptr;    // pinned mirror of d_out
   int32_t* h_stat = nullptr;  // pinned: per-sample status/iters copy (max_samples * 4)
+  uint64_t serial = 0;        // unique per created problem (a network's held-out check names it)
+  int last_backend = -1;      // backend of the last ouu_risk_and_grad that returned OUU_OK
 };
 
 int ouu_num_levels(int n);

@@ -176,6 +176,21 @@ def risk_errors(P, D, n_samples, zs, risks):
     return worst_r, worst_g, rows
 
 
+def validate_surrogate(P, D, n_hold=256, n_controls=3, risk_tol=0.01, grad_tol=0.05, seed=SEED_HELDOUT,
+                       seed_z=SEED_EVAL_Z + 200):
+    """Held-out check of the trained network with the plain path as the judge: n_hold fields
+    not used for training, n_controls controls, both risks of the bench.  While it passes,
+    BACKEND_AUTO evaluations of P use the network; otherwise they fall back to the plain path.
+    Returns (largest relative risk error, largest relative gradient error, passed)."""
+    import torch
+    n = P.n
+    m = torch.empty(n_hold, n, n, dtype=torch.float64, device="cuda")
+    P.ouu_sample_fields(seed, 0, n_hold, m)
+    risks = [capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.95, eps=1e-4, t_optimal=1),
+             capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0)]
+    return D.ouu_dino_validate(P, m, n_hold, risks, controls(seed_z, n_controls, P.d_z), risk_tol, grad_tol)
+
+
 # ----------------------------------------------------------------------------- persistence
 # What defines a surrogate besides its arrays: the sizes and the prior (the KL projection rows
 # follow from n, r_m and the prior, and are rebuilt when a handle is created).
@@ -272,6 +287,8 @@ def main():
     es, ej = heldout_errors(P, D)
     rep["heldout_state_rel"] = es
     rep["heldout_jacobian_rel"] = ej
+    vr, vg, ok = validate_surrogate(P, D)
+    rep["fallback_check"] = {"risk_rel": vr, "grad_rel": vg, "network_used_by_auto": ok}
     risks = [capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.95, eps=1e-4, t_optimal=1),
              capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0)]
     zs = controls(SEED_EVAL_Z, 5, args.L * args.L)

@@ -95,6 +95,9 @@ def test_null_handles_are_rejected(lib):
     out = ctypes.c_void_p()
     assert L.ouu_batch_create(None, 0, 0, ctypes.byref(out)) == bad
     assert "problem is null" in (L.ouu_sample_fields(None, 1, 0, 4, None) and capi.last_error())
+    z4 = (ctypes.c_double * 4)()
+    assert L.ouu_dino_validate(None, None, None, 4, ctypes.byref(r), 1, z4, 1, 0.01, 0.05, None, None, None) == bad
+    assert L.ouu_last_backend(None) == -1
     # destroying nothing succeeds; queries on nothing give zero
     assert L.ouu_destroy_problem(None) == capi.OUU_OK and L.ouu_dino_destroy(None) == capi.OUU_OK
     assert L.ouu_problem_slots(None) == 0 and L.ouu_dino_num_params(None) == 0
@@ -159,3 +162,7 @@ def test_binding_refuses_short_buffers():
                         torch.zeros(2, 3, dtype=torch.float64))
     with pytest.raises(ValueError, match="xi"):
         D.ouu_kernel_dino_network(torch.zeros(2, 7), 2, np.zeros(4), 2)
+    with pytest.raises(ValueError, match="zs"):
+        D.ouu_dino_validate(P, m3, 3, [capi.risk_desc(capi.RISK_MEAN_VAR)], np.zeros((2, 5)))
+    with pytest.raises(ValueError, match="m_dev"):
+        D.ouu_dino_validate(P, m3, 4, [capi.risk_desc(capi.RISK_MEAN_VAR)], np.zeros((2, 4)))

@@ -13,8 +13,8 @@ import pytest
 
 from gpu_util import rel
 from oracle import dino, field, pde
-from synthetic_inputs import SEED_EVAL_Z, SEED_SAA, SEED_TRAIN_FIELDS, SEED_TRAIN_Z, controls, glorot_uniform_mlp, \
-    random_state_like
+from synthetic_inputs import SEED_EVAL_Z, SEED_HELDOUT, SEED_SAA, SEED_TRAIN_FIELDS, SEED_TRAIN_Z, controls, \
+    glorot_uniform_mlp, random_state_like
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -330,3 +330,42 @@ def test_cluster_network_bench_shape():
         np.testing.assert_allclose(pm, p0, rtol=1e-6, atol=1e-7 * np.abs(p0).max())
         np.testing.assert_allclose(qm, q0, rtol=1e-6)
         assert rel(gm, g0) <= 1e-6, (mode, rel(gm, g0))
+
+
+def test_auto_backend_falls_back_to_the_plain_path(setup):
+    """BACKEND_AUTO runs the plain path until the network passes its held-out check against it
+    for this problem (ouu_dino_validate), the network after that, and the plain path again for
+    another problem or once the network changes.  The untrained network here fails a 1 % / 5 %
+    check; an unbounded check passes it.  Risk values: 1e-9 relative against the plain path on
+    the same inputs, 1e-6 against the network's own evaluation."""
+    from paper_2305_20053_gb300 import capi
+    D, P, n, N = setup["D"], setup["P"], N_GRID, 40
+    m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
+    P.ouu_sample_fields(SEED_HELDOUT, 0, N, m)
+    risks = [capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0),
+             capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.9, eps=1e-4, t_optimal=1)]
+    zs = controls(SEED_EVAL_Z + 11, 2, DZ)
+    z = zs[0]
+    pde_v = P.ouu_risk_and_grad(capi.BACKEND_PDE, None, m, N, risks, z)[0]
+    dino_v = P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)[0]
+
+    def auto(prob):
+        v = prob.ouu_risk_and_grad(capi.BACKEND_AUTO, D, m, N, risks, z)[0]
+        return v, prob.ouu_last_backend()
+
+    v, b = auto(P)                          # never checked: the plain path
+    assert b == capi.BACKEND_PDE
+    np.testing.assert_allclose(v, pde_v, rtol=1e-9)
+    er, eg, ok = D.ouu_dino_validate(P, m, N, risks, zs, risk_tol=0.01, grad_tol=0.05)
+    assert not ok and np.isfinite(er) and np.isfinite(eg) and (er > 0.01 or eg > 0.05)
+    assert auto(P)[1] == capi.BACKEND_PDE
+    er2, eg2, ok = D.ouu_dino_validate(P, m, N, risks, zs, risk_tol=1e30, grad_tol=1e30)
+    assert ok and er2 == pytest.approx(er, rel=1e-3) and eg2 == pytest.approx(eg, rel=1e-3)
+    v, b = auto(P)
+    assert b == capi.BACKEND_DINO
+    np.testing.assert_allclose(v, dino_v, rtol=1e-6)
+    P2 = capi.Problem(n=n, lattice_L=L, max_samples=N)   # the check named P, not P2
+    assert auto(P2)[1] == capi.BACKEND_PDE
+    D.ouu_dino_set_params(D.ouu_dino_get_params())       # a changed network is checked again
+    assert auto(P)[1] == capi.BACKEND_PDE
+    P2.close()
