@@ -265,6 +265,17 @@ ouu_status ouu_dino_get_output_scale(ouu_dino_t d, float* s_host);
 /* Copies the installed basis out (FP64 device, layouts as in set_bases). */
 ouu_status ouu_dino_get_bases(ouu_dino_t d, double* phi_dev, double* ubar_dev);
 
+/* Checkpoint of the whole network state to the file at `path`: FP32 parameters, the Adam
+ * moments and step count (so that training resumes where it stopped), the output scale,
+ * and the POD basis with its mean state when built.  Format: the 8 bytes "OUUDINO1", a
+ * 64-byte header (int32 version = 1, n, lattice_L, r_m, r_u, width, Adam step, bases flag;
+ * double gamma, delta, m_mean; uint64 parameter count), then the arrays in that order,
+ * little-endian.  ouu_dino_load restores it into a handle created with the same sizes and
+ * prior (the KL rows are rebuilt at creation) and refuses another network's file, a
+ * truncated file or one with bytes after its last array (INVALID_ARG, message set). */
+ouu_status ouu_dino_save(ouu_dino_t d, const char* path);
+ouu_status ouu_dino_load(ouu_dino_t d, const char* path);
+
 /* Network inputs: xi_dev [n][r_m] FP32 = whitened KL coordinates of m_dev
  * [n][n*n] (BF16 tensor-core projection, FP32 accumulation). */
 ouu_status ouu_dino_project_fields(ouu_dino_t d, const double* m_dev, int n_samples, float* xi_dev);

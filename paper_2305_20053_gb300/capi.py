@@ -87,6 +87,8 @@ SIGNATURES = {
                                ctypes.POINTER(EvalStats)]),
     "ouu_pde_solve_batch_noalloc": (_i, [ctypes.POINTER(ProblemDesc), _vp, _i, _vp, _i64, _vp, _vp, _vp, _vp]),
     "ouu_last_backend": (_i, [_vp]),
+    "ouu_dino_save": (_i, [_vp, ctypes.c_char_p]),
+    "ouu_dino_load": (_i, [_vp, ctypes.c_char_p]),
     "ouu_dino_validate": (_i, [_vp, _vp, _vp, _i, ctypes.POINTER(RiskDesc), _i, _dp, _i, ctypes.c_double,
                                ctypes.c_double, _dp, _dp, ctypes.POINTER(ctypes.c_int)]),
     "ouu_default_dino_desc": (None, [ctypes.POINTER(DinoDesc)]),
@@ -440,6 +442,14 @@ class Dino:
                                        len(risks), zz.ctypes.data_as(_dp), zz.shape[0], float(risk_tol),
                                        float(grad_tol), ctypes.byref(er), ctypes.byref(eg), ctypes.byref(ok)))
         return er.value, eg.value, bool(ok.value)
+
+    def ouu_dino_save(self, path):
+        """Checkpoint of the whole network state (parameters, Adam state, output scale, bases)."""
+        check(load().ouu_dino_save(self.handle, os.fsencode(os.fspath(path))))
+
+    def ouu_dino_load(self, path):
+        """Restores a checkpoint written by ouu_dino_save for a network of these sizes and prior."""
+        check(load().ouu_dino_load(self.handle, os.fsencode(os.fspath(path))))
 
     def ouu_dino_set_fused_network(self, mode):
         """0: per-layer GEMM kernels, 1: one kernel per 128-sample tile, 2: 4-CTA clusters."""

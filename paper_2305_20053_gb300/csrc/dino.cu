@@ -9,6 +9,7 @@
 // weight gradient of the value and Jacobian terms together.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -927,6 +928,117 @@ extern "C" ouu_status ouu_dino_set_output_scale(ouu_dino_t d, const float* s_hos
 extern "C" ouu_status ouu_dino_get_output_scale(ouu_dino_t d, float* s_host) {
   OUU_CHECK_ARG(d && s_host, "null argument");
   OUU_CUDA_TRY(cudaMemcpyAsync(s_host, d->d_oscale, (size_t)d->ru * 4, cudaMemcpyDeviceToHost, d->stream));
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OUU_OK;
+}
+
+// ------------------------------------------------------------------ checkpoint
+// File: the 8 bytes "OUUDINO1", a CkptHead, then FP32 parameters, Adam first and second
+// moments [n_params] each, FP32 output scale [r_u], and with bases FP64 Phi [r_u][n n] and
+// ubar [n n]; all little-endian, as both supported hosts (x86-64, aarch64) store them.
+static const char kCkptMagic[8] = {'O', 'U', 'U', 'D', 'I', 'N', 'O', '1'};
+struct CkptHead {
+  int32_t version, n, lattice_L, r_m, r_u, width, adam_t, bases_ready;
+  double gamma, delta, m_mean;
+  uint64_t n_params;
+};
+static_assert(sizeof(CkptHead) == 64, "checkpoint header without padding");
+
+extern "C" ouu_status ouu_dino_save(ouu_dino_t d, const char* path) {
+  OUU_CHECK_ARG(d && path, "null argument");
+  const size_t np = d->n_params, ru = (size_t)d->ru, nn = (size_t)d->nn;
+  std::vector<float> prm(np), am(np), av(np), sc(ru);
+  std::vector<double> phi(d->bases_ready ? ru * nn : 0), ub(d->bases_ready ? nn : 0);
+  OUU_CUDA_TRY(cudaMemcpyAsync(prm.data(), d->d_params, np * 4, cudaMemcpyDeviceToHost, d->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(am.data(), d->d_adam_m, np * 4, cudaMemcpyDeviceToHost, d->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(av.data(), d->d_adam_v, np * 4, cudaMemcpyDeviceToHost, d->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(sc.data(), d->d_oscale, ru * 4, cudaMemcpyDeviceToHost, d->stream));
+  if (d->bases_ready) {
+    OUU_CUDA_TRY(cudaMemcpyAsync(phi.data(), d->d_phi64, ru * nn * 8, cudaMemcpyDeviceToHost, d->stream));
+    OUU_CUDA_TRY(cudaMemcpyAsync(ub.data(), d->d_ubar, nn * 8, cudaMemcpyDeviceToHost, d->stream));
+  }
+  OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  CkptHead h;
+  std::memset(&h, 0, sizeof(h));
+  h.version = 1;
+  h.n = d->n;
+  h.lattice_L = d->desc.lattice_L;
+  h.r_m = d->rm;
+  h.r_u = d->ru;
+  h.width = d->wd;
+  h.adam_t = d->adam_t;
+  h.bases_ready = d->bases_ready ? 1 : 0;
+  h.gamma = d->desc.gamma;
+  h.delta = d->desc.delta;
+  h.m_mean = d->desc.m_mean;
+  h.n_params = np;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    ouu_set_error(std::string("cannot open ") + path + " for writing");
+    return OUU_ERR_INVALID_ARG;
+  }
+  bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+            std::fwrite(prm.data(), 4, np, f) == np && std::fwrite(am.data(), 4, np, f) == np &&
+            std::fwrite(av.data(), 4, np, f) == np && std::fwrite(sc.data(), 4, ru, f) == ru &&
+            std::fwrite(phi.data(), 8, phi.size(), f) == phi.size() && std::fwrite(ub.data(), 8, ub.size(), f) == ub.size();
+  ok = std::fclose(f) == 0 && ok;
+  if (!ok) {
+    ouu_set_error(std::string("writing ") + path + " failed");
+    return OUU_ERR_INVALID_ARG;
+  }
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_load(ouu_dino_t d, const char* path) {
+  OUU_CHECK_ARG(d && path, "null argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    ouu_set_error(std::string("cannot open ") + path);
+    return OUU_ERR_INVALID_ARG;
+  }
+  char magic[8];
+  CkptHead h;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+            std::fread(&h, sizeof(h), 1, f) == 1 && h.version == 1;
+  if (!ok) {
+    std::fclose(f);
+    ouu_set_error(std::string(path) + " is not a network checkpoint");
+    return OUU_ERR_INVALID_ARG;
+  }
+  if (h.n != d->n || h.lattice_L != d->desc.lattice_L || h.r_m != d->rm || h.r_u != d->ru || h.width != d->wd ||
+      h.gamma != d->desc.gamma || h.delta != d->desc.delta || h.m_mean != d->desc.m_mean ||
+      h.n_params != (uint64_t)d->n_params || h.adam_t < 0 || (h.bases_ready != 0 && h.bases_ready != 1)) {
+    std::fclose(f);
+    ouu_set_error(std::string(path) + " holds a network of other sizes or another prior");
+    return OUU_ERR_INVALID_ARG;
+  }
+  const size_t np = d->n_params, ru = (size_t)d->ru, nn = (size_t)d->nn;
+  std::vector<float> prm(np), am(np), av(np), sc(ru);
+  std::vector<double> phi(h.bases_ready ? ru * nn : 0), ub(h.bases_ready ? nn : 0);
+  ok = std::fread(prm.data(), 4, np, f) == np && std::fread(am.data(), 4, np, f) == np &&
+       std::fread(av.data(), 4, np, f) == np && std::fread(sc.data(), 4, ru, f) == ru &&
+       std::fread(phi.data(), 8, phi.size(), f) == phi.size() && std::fread(ub.data(), 8, ub.size(), f) == ub.size() &&
+       std::fgetc(f) == EOF;   // nothing after the last array
+  std::fclose(f);
+  if (!ok) {
+    ouu_set_error(std::string(path) + " is truncated or longer than its header says");
+    return OUU_ERR_INVALID_ARG;
+  }
+  for (size_t r = 0; r < ru; ++r) OUU_CHECK_ARG(sc[r] > 0 && std::isfinite(sc[r]), "checkpoint: output scale not positive");
+  d->val_ok = 0;
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_params, prm.data(), np * 4, cudaMemcpyHostToDevice, d->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_adam_m, am.data(), np * 4, cudaMemcpyHostToDevice, d->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_adam_v, av.data(), np * 4, cudaMemcpyHostToDevice, d->stream));
+  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_oscale, sc.data(), ru * 4, cudaMemcpyHostToDevice, d->stream));
+  d->adam_t = h.adam_t;
+  refresh_bf16_weights(d);
+  OUU_CUDA_TRY(cudaGetLastError());
+  if (h.bases_ready) {
+    OUU_CUDA_TRY(cudaMemcpyAsync(d->d_phi64, phi.data(), ru * nn * 8, cudaMemcpyHostToDevice, d->stream));
+    OUU_CUDA_TRY(cudaMemcpyAsync(d->d_ubar, ub.data(), nn * 8, cudaMemcpyHostToDevice, d->stream));
+    return dino_install_bases(d);   // synchronises before the host buffers go
+  }
+  d->bases_ready = 0;   // the checkpoint was taken before the bases existed
   OUU_CUDA_TRY(cudaStreamSynchronize(d->stream));
   return OUU_OK;
 }

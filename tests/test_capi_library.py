@@ -98,6 +98,7 @@ def test_null_handles_are_rejected(lib):
     z4 = (ctypes.c_double * 4)()
     assert L.ouu_dino_validate(None, None, None, 4, ctypes.byref(r), 1, z4, 1, 0.01, 0.05, None, None, None) == bad
     assert L.ouu_last_backend(None) == -1
+    assert L.ouu_dino_save(None, b"x") == bad and L.ouu_dino_load(None, b"x") == bad
     # destroying nothing succeeds; queries on nothing give zero
     assert L.ouu_destroy_problem(None) == capi.OUU_OK and L.ouu_dino_destroy(None) == capi.OUU_OK
     assert L.ouu_problem_slots(None) == 0 and L.ouu_dino_num_params(None) == 0
