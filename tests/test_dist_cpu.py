@@ -2,7 +2,6 @@
 ranges of one Philox stream (weak scaling, no collective on the data path), the job time as
 the maximum over ranks, and the whole-job rate; each rank's risk equals the single-process
 evaluation of its own range."""
-import os
 import socket
 
 import numpy as np
