@@ -12,7 +12,8 @@
  * Sec. 2.2 (mean + kappa * variance, or the smoothed CVaR of Sec. 2.1 in its
  * Rockafellar-Uryasev form), and its gradient in z is the chain rule of Sec. 2.3
  * with one adjoint solve per sample (plain backend) or automatic differentiation
- * through the reduced-basis neural operator of Sec. 3.3 (MR-DINO backend).
+ * through the reduced-basis neural operator of Sec. 3.3 (MR-DINO backend); the AUTO backend
+ * takes the surrogate only after it passed a held-out check against the plain backend.
  *
  * Discretisation: n x n vertex grid, h = 1/(n-1), n = 2^k + 1 (5 <= n <= 1025);
  * grid arrays are row-major [iy * n + ix] over all n*n nodes (x fastest);
