@@ -162,7 +162,7 @@ ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ouu_dino_t di
  * OUU_BACKEND_DINO); -1 before any, or for p == NULL. */
 int ouu_last_backend(ouu_problem_t p);
 
-/* Held-out check of the surrogate with the plain path as the judge (the paper's accuracy
+/* Held-out check of the surrogate with the plain path as the reference (the paper's accuracy
  * study of Sec. 4 as a gate): at each of the n_z controls z_host [n_z][d_Z], both backends
  * evaluate the n_risks risks over the held-out fields m_dev [n_samples][n][n] (samples not
  * used for training); the largest relative risk error |rho_DINO - rho_PDE| / |rho_PDE| and

@@ -178,7 +178,7 @@ def risk_errors(P, D, n_samples, zs, risks):
 
 def validate_surrogate(P, D, n_hold=256, n_controls=3, risk_tol=0.01, grad_tol=0.05, seed=SEED_HELDOUT,
                        seed_z=SEED_EVAL_Z + 200):
-    """Held-out check of the trained network with the plain path as the judge: n_hold fields
+    """Held-out check of the trained network with the plain path as the reference: n_hold fields
     not used for training, n_controls controls, both risks of the bench.  While it passes,
     BACKEND_AUTO evaluations of P use the network; otherwise they fall back to the plain path.
     Returns (largest relative risk error, largest relative gradient error, passed)."""
