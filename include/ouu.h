@@ -361,7 +361,9 @@ typedef struct ouu_batch* ouu_batch_t;
 typedef struct {
   ouu_problem_t problem;
   ouu_backend backend;
-  ouu_dino_t dino;              /* OUU_BACKEND_DINO items, else NULL */
+  ouu_dino_t dino;              /* OUU_BACKEND_DINO and _AUTO items, else NULL; an AUTO item
+                                 * takes DINO at create when the network passed its held-out
+                                 * check for the item's problem, else PDE */
   const double* m_dev;
   int n_samples;
   const ouu_risk_desc* risks;   /* copied at create */

@@ -530,8 +530,8 @@ def unflatten_params(p, widths):
 
 class Batch:
     """Owns an ouu_batch_t: many problems evaluated together (one CUDA graph per batch).
-    items: sequence of dicts with keys problem (Problem), backend, dino (Dino or None),
-    m (device FP64 fields), n (samples), risks (list of RiskDesc)."""
+    items: sequence of dicts with keys problem (Problem), backend (BACKEND_PDE, _DINO or _AUTO),
+    dino (Dino or None), m (device FP64 fields), n (samples), risks (list of RiskDesc)."""
 
     def __init__(self, items, autotune=False):
         import torch
@@ -544,6 +544,7 @@ class Batch:
             arr[k].problem = it["problem"].handle
             arr[k].backend = it["backend"]
             arr[k].dino = it["dino"].handle if it.get("dino") is not None else None
+            need(it["m"], it["n"] * it["problem"].n * it["problem"].n, f"items[{k}]['m']")
             arr[k].m_dev = dev_ptr(it["m"], torch.float64)
             arr[k].n_samples = it["n"]
             arr[k].risks = rk

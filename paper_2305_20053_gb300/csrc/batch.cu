@@ -111,9 +111,18 @@ static ouu_status check_item(const ouu_batch_item& it) {
     }                                                                            \
   } while (0)
 
-extern "C" ouu_status ouu_batch_create(const ouu_batch_item* items, int n_items, int autotune, ouu_batch_t* out) {
-  OUU_CHECK_ARG(items && out && n_items >= 1, "need items and an output handle");
+extern "C" ouu_status ouu_batch_create(const ouu_batch_item* items_in, int n_items, int autotune, ouu_batch_t* out) {
+  OUU_CHECK_ARG(items_in && out && n_items >= 1, "need items and an output handle");
   *out = nullptr;
+  // AUTO items take their backend now: the network if it passed its held-out check for the
+  // item's problem, else the plain path
+  std::vector<ouu_batch_item> resolved(items_in, items_in + n_items);
+  for (ouu_batch_item& it : resolved)
+    if (it.backend == OUU_BACKEND_AUTO) {
+      it.backend = dino_trusted(it.dino, it.problem, it.n_samples) ? OUU_BACKEND_DINO : OUU_BACKEND_PDE;
+      if (it.backend == OUU_BACKEND_PDE) it.dino = nullptr;
+    }
+  const ouu_batch_item* items = resolved.data();
   for (int k = 0; k < n_items; ++k) {
     if (ouu_status st = check_item(items[k])) return st;
     for (int j = 0; j < k; ++j) {

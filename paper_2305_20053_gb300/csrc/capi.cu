@@ -612,8 +612,8 @@ static ouu_status risk_and_grad_on(ouu_problem_t p, ouu_backend backend, ouu_din
 
 // The network may stand in for the plain path: it passed its held-out check against this
 // problem and can take this many samples.
-static bool dino_trusted(const ouu_dino* d, const ouu_problem* p, int n_samples) {
-  return d && d->val_ok && d->val_serial == p->serial && d->bases_ready && n_samples <= d->maxE;
+bool dino_trusted(const ouu_dino* d, const ouu_problem* p, int n_samples) {
+  return d && p && d->val_ok && d->val_serial == p->serial && d->bases_ready && n_samples <= d->maxE;
 }
 
 extern "C" ouu_status ouu_risk_and_grad(ouu_problem_t p, ouu_backend backend, ouu_dino_t dino, const double* m_dev,

@@ -80,6 +80,10 @@ struct ouu_dino {
   uint64_t val_serial = 0;
 };
 
+// The network d may stand in for the plain path on n_samples samples of problem p: it passed
+// its held-out check against p since it last changed (capi.cu; OUU_BACKEND_AUTO).
+bool dino_trusted(const ouu_dino* d, const ouu_problem* p, int n_samples);
+
 // DINO forward/backward pieces used by the C ABI (dino.cu).
 ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad);
 
