@@ -167,3 +167,47 @@ def test_binding_refuses_short_buffers():
         D.ouu_dino_validate(P, m3, 3, [capi.risk_desc(capi.RISK_MEAN_VAR)], np.zeros((2, 5)))
     with pytest.raises(ValueError, match="m_dev"):
         D.ouu_dino_validate(P, m3, 4, [capi.risk_desc(capi.RISK_MEAN_VAR)], np.zeros((2, 4)))
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ouu.h"
+int main(void) {
+  ouu_problem_desc d;
+  ouu_default_problem_desc(&d);
+  if (d.n != 129 || d.lattice_L != 10) return 2;
+  d.n = 6;
+  ouu_problem_t p = NULL;
+  ouu_status st = ouu_create_problem(&d, NULL, &p);
+  char msg[256];
+  ouu_last_error(msg, sizeof msg);
+  printf("%d %s\n", (int)st, msg);
+  return (st == OUU_ERR_INVALID_ARG && p == NULL && strlen(msg) > 0 && ouu_last_backend(NULL) == -1) ? 0 : 1;
+}
+"""
+
+
+def test_headers_compile_as_c_and_a_c_program_links(lib, tmp_path):
+    """The boundary is a C ABI: both headers compile as C99 and C++17, and a plain C program
+    links against libouu.so and calls it (host-side calls only)."""
+    import shutil
+    import subprocess
+    gcc, gxx = shutil.which("gcc"), shutil.which("g++")
+    if not gcc or not gxx:
+        pytest.skip("gcc/g++ not available")
+    inc = os.path.join(ROOT, "include")
+    for h in glob.glob(os.path.join(inc, "*.h")):
+        for cmd in ([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", "c"],
+                    [gxx, "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-x", "c++"]):
+            r = subprocess.run(cmd + ["-I", inc, h], capture_output=True, text=True)
+            assert r.returncode == 0, r.stderr
+    src, exe = tmp_path / "t.c", tmp_path / "t"
+    src.write_text(C_PROGRAM)
+    libdir = os.path.dirname(lib._name)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-L", libdir, "-louu",
+                        "-Wl,-rpath," + libdir, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.stdout, r.stderr)
+    assert r.stdout.startswith("1 ")
