@@ -189,13 +189,18 @@ ouu_status ouu_dino_validate(ouu_problem_t p, ouu_dino_t d, const double* m_dev,
  * status_dev mean what they mean there, and all five pointers are required.
  * All scratch (tables, per-CTA solver slots, the work counter) lives in one
  * file-scope device array of 8 MiB that every GPU which loads the library holds
- * until the process exits; grids that do not fit one solver slot in it
- * (n > 257) are rejected with OUU_ERR_INVALID_ARG.  The call makes no cudaMalloc,
- * cudaFree or other allocating call.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  The array keeps the last call's
- * contents; each call clears what must start at zero.  All calls share the one
- * array, so calls whose GPU work overlaps (other streams, other threads) race:
+ * until the process exits; under lazy module loading (CUDA_MODULE_LOADING=LAZY, the
+ * default) the array may be committed only when the library's module is first used
+ * on that device, which can be this call.  Grids that do not fit one solver slot in
+ * it (n > 257) are rejected with OUU_ERR_INVALID_ARG.  Throughput: the array holds
+ * a few solver slots only (about 9 at n = 129, 2 at n = 257, one slot per CTA), so
+ * the solve runs on that many SMs rather than all of them; ouu_pde_solve_batch
+ * is the fast path.  The call makes no cudaMalloc, cudaFree or other allocating
+ * call.  Every call looks up the array's device address (cudaGetSymbolAddress,
+ * which allocates nothing) with the calling thread's current device; make the
+ * first call on a device before any stream capture.  The array keeps the last
+ * call's contents; each call clears what must start at zero.  All calls share the
+ * one array, so calls whose GPU work overlaps (other streams, other threads) race:
  * serialise them.  Synchronises `cuda_stream` (a cudaStream_t or NULL) before
  * returning, like ouu_pde_solve_batch. */
 ouu_status ouu_pde_solve_batch_noalloc(const ouu_problem_desc* desc, const double* m_dev, int n_samples,

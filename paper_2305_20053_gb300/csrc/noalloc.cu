@@ -12,38 +12,27 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "ouu_internal.cuh"
 
 // Fixed scratch: 8 MiB per device.
 #define OUU_NOALLOC_SCRATCH_BYTES (8u << 20)
 #define OUU_NOALLOC_CHUNK 4096          // samples per launch (bounds the iteration-count table)
-#define OUU_NOALLOC_MAX_DEVICES 64
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[OUU_NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch, looked up once per device.  In host code the
-// symbol name is only a host-side stand-in, never a device address.
-static unsigned char* g_scratch_addr[OUU_NOALLOC_MAX_DEVICES];
-static std::mutex g_scratch_mutex;
-
-static ouu_status scratch_address(int device, unsigned char** out) {
-  if (device < 0 || device >= OUU_NOALLOC_MAX_DEVICES) {
-    ouu_set_error("device ordinal out of range for the no-allocation scratch");
-    return OUU_ERR_INVALID_ARG;
+// Device address of g_noalloc_scratch in the current context.  In host code the symbol
+// name is only a host-side stand-in, never a device address.  The lookup is repeated on
+// every call (it allocates nothing): a cached address would go stale if the context were
+// torn down and recreated (cudaDeviceReset), since the module may then load elsewhere.
+static ouu_status scratch_address(unsigned char** out) {
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr) {
+    ouu_set_error(std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+    return OUU_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[device]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr) {
-      ouu_set_error(std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
-      return OUU_ERR_CUDA;
-    }
-    g_scratch_addr[device] = (unsigned char*)ptr;
-  }
-  *out = g_scratch_addr[device];
+  *out = (unsigned char*)ptr;
   return OUU_OK;
 }
 
@@ -84,7 +73,7 @@ extern "C" ouu_status ouu_pde_solve_batch_noalloc(const ouu_problem_desc* desc, 
   OUU_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   OUU_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
   unsigned char* base = nullptr;
-  if (ouu_status st = scratch_address(device, &base)) return st;
+  if (ouu_status st = scratch_address(&base)) return st;
 
   // Layout inside the scratch: counter | gx | ut | iteration table | slots.
   const int nlev = ouu_num_levels(n);
@@ -132,10 +121,16 @@ extern "C" ouu_status ouu_pde_solve_batch_noalloc(const ouu_problem_desc* desc, 
   lay.smem_bytes = soff;
   lay.bytes = align256(s);
   const int64_t room = (int64_t)OUU_NOALLOC_SCRATCH_BYTES - slots_off;
-  if (room < lay.bytes || lay.smem_bytes + 1024 > smem_optin) {
+  if (room < lay.bytes) {
     ouu_set_error("grid too large for the no-allocation scratch: one solver slot needs " +
                   std::to_string(slots_off + lay.bytes) + " bytes of the fixed " +
                   std::to_string(OUU_NOALLOC_SCRATCH_BYTES) + " (n <= 257 fits)");
+    return OUU_ERR_INVALID_ARG;
+  }
+  if (lay.smem_bytes + 1024 > smem_optin) {
+    ouu_set_error("grid too large for the solver's shared-memory multigrid levels: " +
+                  std::to_string(lay.smem_bytes + 1024) + " bytes per block, device limit " +
+                  std::to_string(smem_optin));
     return OUU_ERR_INVALID_ARG;
   }
   const int nslots = (int)std::min<int64_t>(std::min<int64_t>(room / lay.bytes, sms), n_samples);

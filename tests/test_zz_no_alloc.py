@@ -36,21 +36,30 @@ def _solve_both(n, L, N, per_sample):
     q_ref = torch.empty(N, dtype=torch.float64, device="cuda")
     s_ref = torch.empty(N, dtype=torch.int32, device="cuda")
     P.ouu_pde_solve_batch(m, N, z, stride, u_ref, q_ref, s_ref)
-    outs = []
-    for _ in range(2):     # two calls in a row share (and must clear) the fixed scratch
-        u = torch.full((N, n, n), float("nan"), dtype=torch.float64, device="cuda")
-        q = torch.empty(N, dtype=torch.float64, device="cuda")
-        s = torch.empty(N, dtype=torch.int32, device="cuda")
+    outs, free_bytes = [], []
+    bufs = [(torch.full((N, n, n), float("nan"), dtype=torch.float64, device="cuda"),
+             torch.empty(N, dtype=torch.float64, device="cuda"),
+             torch.empty(N, dtype=torch.int32, device="cuda")) for _ in range(2)]
+    torch.cuda.synchronize()
+    for u, q, s in bufs:   # two calls in a row share (and must clear) the fixed scratch
         capi.ouu_pde_solve_batch_noalloc(capi.problem_desc(n=n, lattice_L=L), m, N, z, stride, u, q, s)
+        torch.cuda.synchronize()
+        free_bytes.append(torch.cuda.mem_get_info()[0])
+    for u, q, s in bufs:
         outs.append((u.cpu().numpy(), q.cpu().numpy(), s.cpu().numpy()))
     P.close()
-    return (u_ref.cpu().numpy(), q_ref.cpu().numpy(), s_ref.cpu().numpy()), outs
+    return (u_ref.cpu().numpy(), q_ref.cpu().numpy(), s_ref.cpu().numpy()), outs, free_bytes
 
 
-@pytest.mark.parametrize("n,L,N,per_sample", [(33, 5, 48, True), (129, 10, 24, False)])
+# (33, 5, 4100): more samples than one launch takes (4096), so the per-launch offsets of
+# the fields, controls, outputs and statuses, and the status read-back in blocks of 1024,
+# run more than once.
+@pytest.mark.parametrize("n,L,N,per_sample", [(33, 5, 48, True), (129, 10, 24, False), (33, 5, 4100, True)])
 def test_noalloc_matches_existing_entry_point(n, L, N, per_sample):
-    (u_ref, q_ref, s_ref), outs = _solve_both(n, L, N, per_sample)
+    (u_ref, q_ref, s_ref), outs, free_bytes = _solve_both(n, L, N, per_sample)
     assert np.all(s_ref == 0)
+    # the second call found the scratch already in place: device memory did not shrink
+    assert free_bytes[1] == free_bytes[0]
     for u, q, s in outs:
         np.testing.assert_array_equal(s, s_ref)
         for i in range(N):
