@@ -13,7 +13,9 @@
 * Reduced quadratic QoI (Sec. 3.3): decoded Q equals 1/2 ||phi + c||^2 + const.
 * Jacobian data (Sec. 3.4, implicit function theorem): Phi^T M J^-1 G against
   finite differences of the projected state.
-* Adam against a hand-unrolled first step.
+* Hand-computed forward pass and forward-mode Jacobian of a 2 -> 3 -> 3 -> 3 -> 2 net whose
+  pre-activations sit where GELU has a closed form (erf(1), erf(2) written out).
+* Adam against hand-unrolled first and second steps (bias corrections at t = 2).
 """
 import numpy as np
 import pytest
@@ -213,3 +215,73 @@ def test_output_scale_is_a_reparametrisation():
     a, b = net.forward(xi, z), plain.forward(xi, z)
     np.testing.assert_allclose(a["phi"], b["phi"], rtol=1e-13)
     np.testing.assert_allclose(a["J"], b["J"], rtol=1e-13)
+
+
+# erf(1) and erf(2) to 31 digits (Abramowitz & Stegun, Table 7.1)
+ERF1 = 0.8427007929497148693412206350826
+ERF2 = 0.9953222650189527341620692563672
+SQ2 = 1.4142135623730950488016887242097
+INV_SQRT_2PI = 0.3989422804014326779399460599344
+
+
+def _hand_net():
+    """A 2 -> 3 -> 3 -> 3 -> 2 net (r_m = 1, d_z = 1) whose weights and biases put every
+    hidden pre-activation at 12, -12, 0, sqrt 2, -sqrt 2 or 2 sqrt 2 for the input
+    [xi, z] = [1, 2], where GELU(x) = x (1 + erf(x / sqrt 2)) / 2 is known in closed form:
+    GELU(12) = 12 and GELU(-12) = 0 to double precision, GELU(0) = 0,
+    GELU(+-sqrt 2) = +-(sqrt 2 / 2)(1 +- erf 1), GELU(2 sqrt 2) = sqrt 2 (1 + erf 2)."""
+    g1 = SQ2 / 2 * (1 + ERF1)                      # GELU(sqrt 2)
+    W0 = [[3.0, 1.5], [-1.0, -5.5], [1.0, 0.0]]
+    b0 = [6.0, 0.0, SQ2 - 1.0]                     # a0 = [12, -12, sqrt 2]
+    W1 = [[1.0, 5.0, 0.0], [0.5, 0.0, 0.0], [0.0, 0.0, SQ2 / g1]]
+    b1 = [-12.0, 6.0, 0.0]                         # a1 = [0, 12, sqrt 2]
+    W2 = [[7.0, 1.0, 0.0], [0.0, 0.0, -SQ2 / g1], [3.0, -1.0, 0.0]]
+    b2 = [2 * SQ2 - 12.0, 0.0, 12.0]               # a2 = [2 sqrt 2, -sqrt 2, 0]
+    W3 = [[1.0, 2.0, 5.0], [-1.0, 0.0, 3.0]]
+    b3 = [0.25, -0.5]
+    s = [2.0, 0.5]
+    return dino.MLP([W0, W1, W2, W3], [b0, b1, b2, b3], 1, out_scale=s)
+
+
+def test_forward_hand_computed():
+    """Sec. 3.3: phi = s * (W3 GELU(W2 GELU(W1 GELU(W0 [xi; z] + b0) + b1) + b2) + b3), linear
+    output layer, KL coordinates before the controls.  A dropped hidden bias, a GELU on the
+    output layer, the inputs in the order [z; xi], or a missing output scale each change phi."""
+    net = _hand_net()
+    st = net.forward(np.array([[1.0]]), np.array([2.0]))
+    g3 = SQ2 * (1 + ERF2)                          # GELU(2 sqrt 2)
+    g2 = -SQ2 / 2 * (1 - ERF1)                     # GELU(-sqrt 2)
+    # h3 = [g3, g2, 0]
+    want = [2.0 * (g3 + 2.0 * g2 + 0.25), 0.5 * (-g3 - 0.5)]
+    np.testing.assert_allclose(st["phi"][0], want, rtol=1e-14)
+    np.testing.assert_allclose(st["a"][0][0], [12.0, -12.0, SQ2], rtol=1e-15)
+    np.testing.assert_allclose(st["a"][1][0], [0.0, 12.0, SQ2], atol=1e-14)
+    np.testing.assert_allclose(st["a"][2][0], [2 * SQ2, -SQ2, 0.0], atol=1e-14)
+
+
+def test_forward_tangent_hand_computed():
+    """Sec. 3.2: the forward-mode control Jacobian d phi / d z through the same net.
+    GELU'(x) = Phi(x) + x phi(x): 1 at 12, 0 at -12, 1/2 at 0, and
+    (1 + erf 2)/2 + 2 sqrt 2 e^-4 / sqrt(2 pi) at 2 sqrt 2.  With d a0/dz = W0[:, 1] = [1.5, -5.5, 0]:
+    d h1 = [1.5, 0, 0], d a1 = [1.5, 0.75, 0], d h2 = [0.75, 0.75, 0], d a2 = [6, 0, 1.5],
+    d h3 = [6 GELU'(2 sqrt 2), 0, 0.75], J = s * (W3 d h3)."""
+    net = _hand_net()
+    J = net.forward(np.array([[1.0]]), np.array([2.0]))["J"][0, :, 0]
+    gp = (1 + ERF2) / 2 + 2 * SQ2 * np.exp(-4.0) * INV_SQRT_2PI
+    want = [2.0 * (6 * gp + 5 * 0.75), 0.5 * (-6 * gp + 3 * 0.75)]
+    np.testing.assert_allclose(J, want, rtol=1e-13)
+
+
+def test_adam_second_step():
+    """Adam's bias corrections at t = 2: m2 = 0.9 (0.1 g1) + 0.1 g2, v2 = 0.999 (0.001 g1^2) + 0.001 g2^2,
+    divided by 1 - 0.9^2 = 0.19 and 1 - 0.999^2 = 0.001999.  With g1 = 3, g2 = -1:
+    m_hat = 0.17 / 0.19 = 17/19 and v_hat = 0.009991 / 0.001999 = 9991/1999."""
+    lr = 1e-3
+    p0 = [np.array([0.5])]
+    opt = dino.Adam(p0)
+    p1 = opt.step(p0, [np.array([3.0])], lr)
+    np.testing.assert_allclose(p1[0], [0.5 - lr * 3.0 / (3.0 + 1e-8)], rtol=1e-15)
+    p2 = opt.step(p1, [np.array([-1.0])], lr)
+    want = p1[0][0] - lr * (17.0 / 19.0) / (np.sqrt(9991.0 / 1999.0) + 1e-8)
+    np.testing.assert_allclose(p2[0], [want], rtol=1e-14)
+    assert opt.t == 2
