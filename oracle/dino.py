@@ -133,7 +133,7 @@ class MLP:
                 if l == 0:
                     Ad = np.broadcast_to(Ws[0][:, self.r_m:], (B,) + Ws[0][:, self.r_m:].shape)
                 else:
-                    Ad = np.einsum("oi,bij->boj", Ws[l], rnd(Hd))
+                    Ad = np.matmul(Ws[l], rnd(Hd))            # (o, i) @ (b, i, j) -> (b, o, j)
             if l < nl - 1:
                 st["a"].append(a)
                 h = gelu(a)

@@ -56,8 +56,8 @@ def synthesize(xi: np.ndarray, n: int, gamma: float = 0.1, delta: float = 1.0,
     lam = kl_eigenvalues(n, gamma, delta)
     V = dct2_basis(n)
     coef = xi / lam
-    # m[iy, ix] = n * sum_{k2,k1} V[k2, iy] coef[k2, k1] V[k1, ix]
-    return m_mean + n * np.einsum("ai,sab,bj->sij", V, coef, V)
+    # m[iy, ix] = n * sum_{k2,k1} V[k2, iy] coef[k2, k1] V[k1, ix], as two matrix products
+    return m_mean + n * (V.T @ coef @ V)
 
 
 def sample_fields(seed: int, first: int, count: int, n: int, gamma: float = 0.1,
