@@ -167,13 +167,7 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle timing
-def _single_thread_env():
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[k] = "1"
-
-
 def _oracle_pde_worker(args):
-    _single_thread_env()
     idx, seed, n, L, z = args
     from oracle import field, pde
     prob = pde.Problem(n=n, L=L)
@@ -186,28 +180,22 @@ def _oracle_pde_worker(args):
     return time.perf_counter() - t0
 
 
-def _oracle_dino_worker(args):
-    """The oracle's surrogate evaluation (FP64): KL projection, MLP with forward-mode
-    control Jacobian, reduced QoI, for `count` fields; weights and basis are seeded
-    (timing does not depend on their values)."""
-    _single_thread_env()
-    first, count, seed, n, L = args
-    from oracle import dino, field
-    from synthetic_inputs import SEED_EVAL_Z, SEED_NET, controls, glorot_uniform_mlp, random_state_like
-    dz = L * L
-    Wkl, _ = dino.kl_projection_matrix(n, R_M)
-    Ws, bs = glorot_uniform_mlp([R_M + dz, WIDTH, WIDTH, WIDTH, R_U], seed=SEED_NET)
-    net = dino.MLP(Ws, bs, R_M)
-    d = (n - 2) ** 2
-    Phi = np.linalg.qr(random_state_like(77, (d, R_U)))[0] * (n - 1)
-    ubar = np.zeros(d)
-    ut = field.target_state(n)[1:-1, 1:-1].ravel()
-    z = controls(SEED_EVAL_Z, 1, dz)[0]
-    m = field.sample_fields(seed, first, count, n).reshape(count, -1)
-    t0 = time.perf_counter()
-    xi = dino.project_fields(m, Wkl)
-    dino.eval_surrogate(net, xi, z, Phi, ubar, ut, 1.0 / (n - 1), decode=False)
-    return time.perf_counter() - t0, count
+class _SingleThreaded:
+    """Children spawned inside this block start with one BLAS / OpenMP thread each (the
+    variables are read when a child imports numpy; this process's numpy is unaffected)."""
+    KEYS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+    def __enter__(self):
+        self.saved = {k: os.environ.get(k) for k in self.KEYS}
+        for k in self.KEYS:
+            os.environ[k] = "1"
+
+    def __exit__(self, *exc):
+        for k, v in self.saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 def cpu_oracle_pde_rate(per_core=1, cores=None):
@@ -218,48 +206,142 @@ def cpu_oracle_pde_rate(per_core=1, cores=None):
     cores = cores or max(1, os.cpu_count() or 1)
     z = controls(SEED_EVAL_Z, 1, L_LAT * L_LAT)[0]
     jobs = [(list(range(c * per_core, (c + 1) * per_core)), SEED_SAA, N_GRID, L_LAT, z) for c in range(cores)]
-    with mp.get_context("spawn").Pool(cores) as pool:
+    with _SingleThreaded(), mp.get_context("spawn").Pool(cores) as pool:
         wall = max(pool.map(_oracle_pde_worker, jobs))   # workers run concurrently: slowest one's compute time
     return cores * per_core / wall / N_SAMPLES, cores * per_core, cores, wall
 
 
-def cpu_oracle_dino_rate(per_core=16, cores=None):
-    """Evals/s of the oracle's MR-DINO evaluation on `cores` spawned single-threaded processes,
-    each evaluating `per_core` fields, scaled to the N-field workload."""
-    import multiprocessing as mp
-    from synthetic_inputs import SEED_SAA
-    cores = cores or max(1, os.cpu_count() or 1)
-    jobs = [(c * per_core, per_core, SEED_SAA, N_GRID, L_LAT) for c in range(cores)]
-    with mp.get_context("spawn").Pool(cores) as pool:
-        wall = max(t for t, _ in pool.map(_oracle_dino_worker, jobs))
-    return cores * per_core / wall / N_SAMPLES, cores * per_core, cores, wall
+def _oracle_dino_loop(conn, first, count, seed, n, L):
+    """Worker of OracleDinoPool: builds its share of the fields, the KL rows, the seeded
+    network and POD basis once, then per request evaluates Q_i and grad_z Q_i of its fields
+    at the received control (FP64 projection, MLP with forward-mode control Jacobian,
+    reduced QoI) and sends them back with its compute time."""
+    from oracle import dino, field
+    from synthetic_inputs import SEED_NET, glorot_uniform_mlp, random_state_like
+    dz, d, h = L * L, (n - 2) ** 2, 1.0 / (n - 1)
+    Wkl, _ = dino.kl_projection_matrix(n, R_M)
+    Ws, bs = glorot_uniform_mlp([R_M + dz, WIDTH, WIDTH, WIDTH, R_U], seed=SEED_NET)
+    net = dino.MLP(Ws, bs, R_M, out_scale=np.linspace(0.05, 0.01, R_U))
+    Phi = np.linalg.qr(random_state_like(77, (d, R_U)))[0] / h
+    ubar = np.zeros(d)
+    ut = field.target_state(n)[1:-1, 1:-1].ravel()
+    m = field.sample_fields(seed, first, count, n).reshape(count, -1)
+    conn.send("ready")
+    while True:
+        z = conn.recv()
+        if z is None:
+            break
+        t0 = time.perf_counter()
+        Q, G = [], []
+        for s in range(0, count, 64):
+            xi = dino.project_fields(m[s:s + 64], Wkl)
+            q, g, _, _ = dino.eval_surrogate(net, xi, z, Phi, ubar, ut, h, decode=False)
+            Q.append(q)
+            G.append(g)
+        conn.send((np.concatenate(Q), np.concatenate(G), time.perf_counter() - t0))
+    conn.close()
+
+
+class OracleDinoPool:
+    """The oracle's MR-DINO SAA risk + gradient evaluation on the host cores, over the whole
+    N-field workload: `cores` spawned single-threaded processes, each holding a contiguous
+    share of the fields and the network, built once at start (outside any timed region).
+    step(z) = every worker evaluates its share, then this process forms the smoothed
+    CVaR_0.95 (t = t*) and mean + variance and their z-gradients; returns the wall time."""
+
+    def __init__(self, n_fields=N_SAMPLES, cores=None, seed=None):
+        import multiprocessing as mp
+        from synthetic_inputs import SEED_SAA
+        self.cores = cores or max(1, os.cpu_count() or 1)
+        self.n_fields = n_fields
+        ctx = mp.get_context("spawn")
+        share = -(-n_fields // self.cores)
+        self.conns, self.procs = [], []
+        with _SingleThreaded():
+            for c in range(self.cores):
+                first, cnt = c * share, min(share, n_fields - c * share)
+                if cnt <= 0:
+                    break
+                a, b = ctx.Pipe()
+                p = ctx.Process(target=_oracle_dino_loop, args=(b, first, cnt, SEED_SAA if seed is None else seed,
+                                                                N_GRID, L_LAT), daemon=True)
+                p.start()
+                self.conns.append(a)
+                self.procs.append(p)
+        for a in self.conns:
+            assert a.recv() == "ready"
+
+    def step(self, z):
+        from oracle import risk
+        t0 = time.perf_counter()
+        for a in self.conns:
+            a.send(z)
+        parts = [a.recv() for a in self.conns]
+        Q = np.concatenate([p[0] for p in parts])
+        G = np.concatenate([p[1] for p in parts])
+        out = (risk.cvar(Q, G, 0.95, 1e-4), risk.mean_var(Q, G, 1.0))
+        return time.perf_counter() - t0, out
+
+    def close(self):
+        for a in self.conns:
+            a.send(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+    SAMPLE = ("all {n} fields per step ({cores} spawned single-threaded processes, each a fixed contiguous share "
+              "built before timing), FP64: KL projection + MLP with forward-mode control Jacobian + reduced QoI, "
+              "then smoothed CVaR_0.95 (t*) and mean+variance with their gradients")
+
+
+def cpu_oracle_dino_rate(steps=3, warmup=1, cores=None):
+    """Evals/s of the oracle's MR-DINO SAA evaluation on the whole workload (OracleDinoPool),
+    the mean over `steps` timed steps after `warmup` untimed ones."""
+    from synthetic_inputs import SEED_EVAL_Z, controls
+    z = controls(SEED_EVAL_Z, 1, L_LAT * L_LAT)[0]
+    pool = OracleDinoPool(cores=cores)
+    try:
+        for _ in range(warmup):
+            pool.step(z)
+        walls = [pool.step(z)[0] for _ in range(steps)]
+    finally:
+        pool.close()
+    return float(np.mean([1.0 / w for w in walls])), pool.cores, walls
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    backend = args.backend
-    fn = cpu_oracle_dino_rate if backend == "dino" else cpu_oracle_pde_rate
-    per = 16 if backend == "dino" else 1
-    for _ in range(args.warmup):
-        fn(per)
-    rates = []
+    from synthetic_inputs import SEED_EVAL_Z, controls
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r, samples, cores, wall = fn(per)
-        rates.append(r)
+    z = controls(SEED_EVAL_Z, 1, L_LAT * L_LAT)[0]
+    rates = []
+    if args.backend == "dino":
+        pool = OracleDinoPool()
+        cores = pool.cores
+        try:
+            for _ in range(args.warmup):
+                pool.step(z)
+            for _ in range(args.steps):
+                rates.append(1.0 / pool.step(z)[0])
+        finally:
+            pool.close()
+        sample = OracleDinoPool.SAMPLE.format(n=N_SAMPLES, cores=cores)
+    else:
+        for _ in range(args.warmup):
+            cpu_oracle_pde_rate(1)
+        for _ in range(args.steps):
+            r, samples, cores, _ = cpu_oracle_pde_rate(1)
+            rates.append(r)
+        sample = (f"{samples} of the {N_SAMPLES} fields per step (1 per core on {cores} spawned single-threaded "
+                  f"processes), FP64 Newton + banded Cholesky state and adjoint solves, scaled to N={N_SAMPLES}")
     value = float(np.mean(rates))
-    sample = (f"{samples} of the {N_SAMPLES} fields per step ({per} per core on {cores} spawned single-threaded "
-              f"processes), FP64, scaled to N={N_SAMPLES}: "
-              + ("KL projection + MLP with forward-mode Jacobian + reduced QoI" if backend == "dino"
-                 else "Newton + banded Cholesky state and adjoint solves"))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"saa-risk-grad {N_GRID}x{N_GRID} N={N_SAMPLES} d_z={L_LAT * L_LAT}",
-                   "n": N_GRID, "n_samples": N_SAMPLES, "d_z": L_LAT * L_LAT, "backend": f"oracle-{backend}"},
+                   "n": N_GRID, "n_samples": N_SAMPLES, "d_z": L_LAT * L_LAT, "backend": f"oracle-{args.backend}"},
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t0,
@@ -442,12 +524,11 @@ def run_ours(args):
         ms_step = ms / args.steps
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            rate, samples, cores, wall = cpu_oracle_dino_rate(16)
+            rate, cores, walls = cpu_oracle_dino_rate(steps=2, warmup=1)
             prate, psamples, pcores, pwall = cpu_oracle_pde_rate(1)
             cpu = {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{samples} of the {N} fields ({cores} spawned single-threaded processes, 16 each, "
-                             f"{wall:.1f} s): FP64 KL projection + MLP with forward-mode Jacobian + reduced QoI, "
-                             f"scaled to N={N}",
+                   "sample": OracleDinoPool.SAMPLE.format(n=N, cores=cores)
+                             + f"; 2 timed steps ({', '.join(f'{w:.1f}' for w in walls)} s)",
                    "pde": {"value": prate, "unit": "evals/s", "cores": pcores,
                            "sample": f"{psamples} fields, FP64 Newton + banded Cholesky state and adjoint, "
                                      f"{pwall:.1f} s, scaled to N={N}"}}

@@ -20,14 +20,22 @@ def _args(**kw):
 @pytest.fixture
 def stub(monkeypatch):
     calls = []
-    rates = iter([9.0, 9.0, 2.0, 4.0, 6.0])   # two warm-up steps, then three timed
+    walls = iter([1 / 9.0, 1 / 9.0, 1 / 2.0, 1 / 4.0, 1 / 6.0])   # two warm-up steps, then three timed
 
-    def fake(per_core=1, cores=None):
-        calls.append(per_core)
-        return next(rates), 8 * per_core, 8, 0.01
+    class FakePool:
+        SAMPLE = bench.OracleDinoPool.SAMPLE
 
-    monkeypatch.setattr(bench, "cpu_oracle_dino_rate", fake)
-    monkeypatch.setattr(bench, "cpu_oracle_pde_rate", fake)
+        def __init__(self, *a, **k):
+            self.cores = 8
+
+        def step(self, z):
+            calls.append(len(z))
+            return next(walls), None
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(bench, "OracleDinoPool", FakePool)
     return calls
 
 
