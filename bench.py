@@ -20,9 +20,10 @@ training by the library's kernels); its recipe is reported in `config`.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--backend dino|pde]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
-Multi-GPU (torchrun): each rank evaluates its own independent sample set (a
-disjoint index range of the same Philox stream), no collective on the data path;
-value = steps of all ranks / max time over ranks ("scaling": "weak").
+Multi-GPU (torchrun): the one sample set of N = 4096 fields is spread over the ranks in
+contiguous blocks; each evaluation gathers the QoIs (8 N bytes) and sums the per-rank
+gradient parts (an FP64 all-reduce of 2 x d_Z values) over NCCL; value = evaluations of
+the whole set per second of the slowest rank ("scaling": "strong").
 """
 from __future__ import annotations
 
@@ -40,6 +41,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "risk+gradient evals/s: MR-DINO vs batched PDE SAA, 1 GB300, <=1% rel err"
+# DRAM bytes (read + write) of one k_kl_project launch over 1024 fields at 129 x 129, from an
+# ncu capture of that kernel; a launch streams each field once, so traffic scales with N
+KL_PROJECT_DRAM_BYTES_N1024 = 144.396544e6 + 3.240448e6
 N_GRID, L_LAT, N_SAMPLES = 129, 10, 4096
 R_M = R_U = 200
 WIDTH = 400
@@ -81,17 +85,6 @@ def dist_init(world, backend="nccl"):
         dist.init_process_group(backend=backend)
         return dist
     return None
-
-
-def rank_samples(rank, n_per_rank):
-    """Weak scaling: rank r evaluates its own sample set, the Philox index range
-    [r n, (r + 1) n) of the same field stream; no collective touches the data path."""
-    return rank * n_per_rank, n_per_rank
-
-
-def job_rate(world, steps, max_ms):
-    """Whole-job throughput: the steps of all ranks over the slowest rank's time."""
-    return world * steps / (max_ms / 1000.0)
 
 
 def barrier(dist):
@@ -374,11 +367,35 @@ def pde_bytes(n, cg_total, newton_total, refine_total, n_samples, adj_samples):
     return pts * (184 * cg_total + 72 * (newton_total + refine_total) + 32 * (n_samples + adj_samples))
 
 
+def split_samples(n_total, world):
+    """Contiguous blocks of one sample set over `world` ranks: [(first, count)] in rank order."""
+    counts = [n_total // world + (1 if r < n_total % world else 0) for r in range(world)]
+    firsts = [sum(counts[:r]) for r in range(world)]
+    return list(zip(firsts, counts))
+
+
+def broadcast_surrogate(dist, D, n, r_u, dev):
+    """Every rank takes rank 0's trained network (parameters, output scale, POD basis), so that
+    all ranks evaluate the same surrogate over their blocks of the one sample set."""
+    import torch
+    prm = torch.tensor(D.ouu_dino_get_params(), device=dev)
+    sc = torch.tensor(D.ouu_dino_get_output_scale(), device=dev)
+    phi = torch.empty(r_u, n, n, dtype=torch.float64, device=dev)
+    ub = torch.empty(n, n, dtype=torch.float64, device=dev)
+    D.ouu_dino_get_bases(phi, ub)
+    for t in (prm, sc, phi, ub):
+        dist.broadcast(t, src=0)
+    D.ouu_dino_set_params(prm.cpu().numpy())
+    D.ouu_dino_set_bases(phi, ub)
+    D.ouu_dino_set_output_scale(sc.cpu().numpy())
+    torch.cuda.synchronize()
+
+
 def run_ours(args):
     import torch
-    from paper_2305_20053_gb300 import capi
+    from paper_2305_20053_gb300 import capi, shard
     from paper_2305_20053_gb300 import train as T
-    from synthetic_inputs import SEED_EVAL_Z, SEED_SAA, controls
+    from synthetic_inputs import SEED_EVAL_Z, SEED_HELDOUT, SEED_SAA, controls
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -389,11 +406,13 @@ def run_ours(args):
     dz = L * L
     stream = torch.cuda.current_stream()
     use_dino = args.backend == "dino"
-    P = capi.Problem(n=n, lattice_L=L, max_samples=max(N, args.train if use_dino else 0))
-    m = torch.empty(N, n, n, dtype=torch.float64, device=dev)
-    first, _ = rank_samples(rank, N)
-    P.ouu_sample_fields(SEED_SAA, first, N, m)
-    z = controls(SEED_EVAL_Z, 1, dz)[0]
+    first, n_loc = split_samples(N, world)[rank]
+    P = capi.Problem(n=n, lattice_L=L, max_samples=max(n_loc, 256, args.train if use_dino else 0))
+    m = torch.empty(n_loc, n, n, dtype=torch.float64, device=dev)
+    P.ouu_sample_fields(SEED_SAA, first, n_loc, m)
+    plan = shard.ShardedSAA(n_loc, dev) if world > 1 else None
+    zs = controls(SEED_EVAL_Z, 5, dz)
+    z = zs[0]
     risks = [capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.95, eps=1e-4, t_optimal=1),
              capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0)]
     peaks = {}
@@ -405,13 +424,20 @@ def run_ours(args):
     tc = peaks.get("bf16_tflops", 1900.0)
     src = "measured" if peaks else "fallback"
 
-    def pde_step():
-        return P.ouu_risk_and_grad(capi.BACKEND_PDE, None, m, N, risks, z)
+    def evaluate(backend, D, zz):
+        """One risk + gradient evaluation over the whole sample set: one call on one GPU, the
+        two phases around the two exchanges when the set is spread over ranks."""
+        if plan is None:
+            return P.ouu_risk_and_grad(backend, D, m, N, risks, zz)
+        return (*shard.risk_and_grad(P, backend, D, m, risks, zz, plan), None)
 
-    # ---- surrogate construction (untimed)
-    D, recipe = None, None
+    def pde_step():
+        return evaluate(capi.BACKEND_PDE, None, z)
+
+    # ---- surrogate construction and its held-out check (untimed)
+    D, recipe, gate = None, None, None
     if use_dino:
-        D = T.make_dino(n, L, r=R_M, width=WIDTH, max_batch=256, max_eval=N)
+        D = T.make_dino(n, L, r=R_M, width=WIDTH, max_batch=256, max_eval=max(n_loc, 256))
         T.init_params(D)
         data = T.generate_training_data(P, D, args.train)
         lr_final = args.lr_final if args.lr_final > 0 else None
@@ -423,6 +449,16 @@ def run_ours(args):
                   "construction_s": {**{k: round(v, 3) for k, v in data.times.items()}, "train_s": round(train_s, 3)},
                   "final_loss": losses[-1][1] if losses else None}
         del data
+        if dist is not None:
+            broadcast_surrogate(dist, D, n, R_U, dev)
+        # the library's fallback gate: 256 held-out fields (not used for training), 5 controls,
+        # 1 % risk and 5 % gradient error against the plain path
+        mh = torch.empty(256, n, n, dtype=torch.float64, device=dev)
+        P.ouu_sample_fields(SEED_HELDOUT, 0, 256, mh)
+        er, eg, ok = D.ouu_dino_validate(P, mh, 256, risks, zs, risk_tol=0.01, grad_tol=0.05)
+        gate = {"heldout_fields": 256, "controls": 5, "risk_tol": 0.01, "grad_tol": 0.05,
+                "max_rel_risk": er, "max_rel_grad": eg, "passed": bool(ok)}
+        del mh
 
     # ---- plain path beside it
     for _ in range(1 if use_dino else max(3, args.warmup)):
@@ -435,60 +471,76 @@ def run_ours(args):
     barrier(dist)
     pde_ms, pde_outs = time_steps(pde_step, pde_k, stream, "pde_timed" if use_dino else "timed")
     pde_ms = max_over_ranks(dist, pde_ms, dev)
-    pde_rate = job_rate(world, pde_k, pde_ms)
-    st = [o[4] for o in pde_outs]
-    cg_total = float(np.mean([s.cg_total for s in st]))
-    pde_info = {"evals_per_s": pde_rate, "ms_per_eval": pde_ms / pde_k,
-                "ms_state": float(np.mean([s.ms_state for s in st])),
-                "ms_adjoint": float(np.mean([s.ms_adjoint for s in st])),
-                "ms_weights": float(np.mean([s.ms_weights for s in st])),
-                "newton_mean": float(np.mean([s.newton_mean for s in st])), "cg_per_sample": cg_total / N,
-                "adjoint_solves": float(np.mean([s.adjoint_solves for s in st]))}
+    pde_rate = pde_k / (pde_ms / 1000.0)
+    pde_info = {"evals_per_s": pde_rate, "ms_per_eval": pde_ms / pde_k}
+    st = [o[4] for o in pde_outs if o[4] is not None]
+    cg_total = None
+    if st:
+        cg_total = float(np.mean([s.cg_total for s in st]))
+        pde_info.update({"ms_state": float(np.mean([s.ms_state for s in st])),
+                         "ms_adjoint": float(np.mean([s.ms_adjoint for s in st])),
+                         "ms_weights": float(np.mean([s.ms_weights for s in st])),
+                         "newton_mean": float(np.mean([s.newton_mean for s in st])), "cg_per_sample": cg_total / N,
+                         "adjoint_solves": float(np.mean([s.adjoint_solves for s in st]))})
 
     if use_dino:
         net_mode = 2 if args.network_mode is None else args.network_mode   # the library default is 2
         D.ouu_dino_set_fused_network(net_mode)
+        # through AUTO when the network passed the gate (the call then runs the network), else
+        # the network directly, with the failed gate in the line
+        backend = capi.BACKEND_AUTO if gate["passed"] else capi.BACKEND_DINO
 
         def step():
-            return P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)
+            return evaluate(backend, D, z)
         for _ in range(max(3, args.warmup)):
             step()
         torch.cuda.synchronize()
+        if backend == capi.BACKEND_AUTO and P.ouu_last_backend() != capi.BACKEND_DINO:
+            raise RuntimeError("AUTO did not take the network after its held-out check passed")
         clocks.start()
         barrier(dist)
         ms, outs = time_steps(step, args.steps, stream)
         barrier(dist)
         clk = clocks.stop()
         ms = max_over_ranks(dist, ms, dev)
-        value = job_rate(world, args.steps, ms)
-        # per-phase device times: the same evaluation enqueued eagerly (the timed steps replay a graph)
+        value = args.steps / (ms / 1000.0)
+        # per-phase device times: this rank's block evaluated eagerly (the timed steps replay a graph)
         D.ouu_dino_set_graphs(0)
-        ds = [step()[4] for _ in range(5)][2:]
+        ds = [P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, n_loc, risks, z)[4] for _ in range(5)][2:]
         D.ouu_dino_set_graphs(1)
         ph = {k: float(np.mean([getattr(s, k) for s in ds]))
               for k in ("ms_project", "ms_network", "ms_weights", "ms_reduce", "ms_total")}
-        ph["ms_total_graph"] = float(np.mean([o[4].ms_total for o in outs]))
-        v0, g0 = pde_outs[-1][0], pde_outs[-1][1]
-        v1, g1 = outs[-1][0], outs[-1][1]
-        acc = {"rel_risk": (np.abs(v1 - v0) / np.abs(v0)).tolist(),
-               "rel_grad": (np.linalg.norm(g1 - g0, axis=1) / np.linalg.norm(g0, axis=1)).tolist(),
-               "risks": ["cvar0.95", "mean+var"], "reference": "plain GPU path (matches the FP64 oracle to 1e-8)"}
+        if outs[-1][4] is not None:
+            ph["ms_total_graph"] = float(np.mean([o[4].ms_total for o in outs]))
+        # accuracy against the plain path over the SAA set, at the 5 seeded controls
+        rows = []
+        for zk in zs:
+            v0, g0 = evaluate(capi.BACKEND_PDE, None, zk)[:2]
+            v1, g1 = evaluate(capi.BACKEND_DINO, D, zk)[:2]
+            rows.append(((np.abs(v1 - v0) / np.abs(v0)).tolist(),
+                         (np.linalg.norm(g1 - g0, axis=1) / np.linalg.norm(g0, axis=1)).tolist()))
+        acc = {"rel_risk_max": np.max([r[0] for r in rows], axis=0).tolist(),
+               "rel_grad_max": np.max([r[1] for r in rows], axis=0).tolist(),
+               "per_control": [{"rel_risk": a, "rel_grad": b} for a, b in rows],
+               "risks": ["cvar0.95", "mean+var"], "controls": 5,
+               "reference": "plain GPU path (matches the FP64 oracle to 1e-8)"}
         nnp = (n * n + 63) // 64 * 64
         in0 = R_M + dz
         net_kernel = {0: "k_build_x0 + k_gemm_bf16 x 8 (MLP forward + reverse-mode gradient)",
                       1: "k_mlp_eval (whole MLP per 128-sample tile)",
                       2: "k_mlp_cluster (whole MLP, 4-CTA clusters per 128-sample tile)"}[net_mode]
-        flops_net = 2 * N * (in0 * WIDTH + 2 * WIDTH * WIDTH + WIDTH * R_U) + 2 * N * (R_U * WIDTH + 2 * WIDTH * WIDTH + WIDTH * dz)
+        flops_net = 2 * n_loc * (in0 * WIDTH + 2 * WIDTH * WIDTH + WIDTH * R_U) + \
+            2 * n_loc * (R_U * WIDTH + 2 * WIDTH * WIDTH + WIDTH * dz)
         # algorithmic bytes of the fused projection: the FP64 fields once, the BF16 KL basis,
         # the FP32 coordinates written (the atomic partial sums of the K split come on top)
         kern = {
             "project": ("k_kl_project (fused FP64 read + BF16 tcgen05 KL projection)", "hbm",
-                        N * n * n * 8 + R_M * nnp * 2 + N * R_M * 4, ph["ms_project"]),
+                        n_loc * n * n * 8 + R_M * nnp * 2 + n_loc * R_M * 4, ph["ms_project"]),
             "network": (net_kernel, "tensor", flops_net, ph["ms_network"]),
         }
-        # DRAM bytes per launch from the committed ncu capture of the same kernel
-        # (profiles/kl_project_129x129_N1024_ncu.md: N = 1024, scaled by the 4x samples)
-        traffic = {"project": 4 * (144.396544e6 + 3.240448e6)}
+        # DRAM bytes of the projection per launch, from an ncu capture of the same kernel at
+        # N = 1024 samples, scaled by the samples of this launch (each sample is streamed once)
+        traffic = {"project": n_loc / 1024.0 * KL_PROJECT_DRAM_BYTES_N1024}
         key = max(kern, key=lambda k: kern[k][3])
         name, bound, work, kms = kern[key]
         achieved = work / (kms / 1000.0) / (1e9 if bound == "hbm" else 1e12)
@@ -516,8 +568,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             e_ms, _ = time_steps(e2e_step, args.steps, stream, "e2e")
             e_ms = max_over_ranks(dist, e_ms, dev)
-            e2e = {"value": job_rate(world, args.steps, e_ms), "unit": "evals/s",
-                   "h2d_bytes_per_step": int(m.numel() * 8 + dz * 8),
+            e2e = {"value": args.steps / (e_ms / 1000.0), "unit": "evals/s",
+                   "h2d_bytes_per_step": int(N * n * n * 8 + dz * 8),
                    "d2h_bytes_per_step": int(len(risks) * (3 + dz) * 8)}
         workload = f"saa-risk-grad mr-dino {n}x{n} N={N} d_z={dz}"
         dtype = "bf16"
@@ -535,12 +587,14 @@ def run_ours(args):
     else:
         clk = clocks.stop()
         value, ms_step, ph, acc, D = pde_rate, pde_ms / pde_k, None, None, None
-        nb = pde_bytes(n, cg_total, 0, 0, N, 0)
-        phase_ms = pde_info["ms_state"] + pde_info["ms_adjoint"]
-        achieved = nb / (phase_ms / 1000.0) / 1e9
-        roof = {"kernel": "k_pde_state + k_pde_adjoint", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "peak_source": f"{src} (burst)",
-                "note": "per-CTA solver working sets are L2-resident; bytes as streamed by each executed pass"}
+        roof = None
+        if cg_total is not None:
+            nb = pde_bytes(n, cg_total, 0, 0, N, 0)
+            phase_ms = pde_info["ms_state"] + pde_info["ms_adjoint"]
+            achieved = nb / (phase_ms / 1000.0) / 1e9
+            roof = {"kernel": "k_pde_state + k_pde_adjoint", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "peak_source": f"{src} (burst)",
+                    "note": "per-CTA solver working sets are L2-resident; bytes as streamed by each executed pass"}
         launches = 5 * args.steps
         workload = f"saa-risk-grad pde {n}x{n} N={N} d_z={dz}"
         dtype = "f64"
@@ -552,8 +606,9 @@ def run_ours(args):
                 m.copy_(m_host, non_blocking=True)
                 return pde_step()
             e_ms, _ = time_steps(e2e_step, args.steps, stream, "e2e")
-            e2e = {"value": job_rate(world, args.steps, e_ms), "unit": "evals/s",
-                   "h2d_bytes_per_step": int(m.numel() * 8 + dz * 8),
+            e_ms = max_over_ranks(dist, e_ms, dev)
+            e2e = {"value": args.steps / (e_ms / 1000.0), "unit": "evals/s",
+                   "h2d_bytes_per_step": int(N * n * n * 8 + dz * 8),
                    "d2h_bytes_per_step": int(len(risks) * (3 + dz) * 8)}
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             rate, samples, cores, wall = cpu_oracle_pde_rate(1)
@@ -564,13 +619,16 @@ def run_ours(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": workload, "n": n, "n_samples": N, "d_z": dz,
                        "risks": ["cvar_smooth beta=0.95 eps=1e-4 t=t*", "mean+var kappa=1"],
-                       "backend": args.backend, "sample_evals_per_s": value * N,
+                       "backend": ("auto (network after its held-out check)" if use_dino and gate["passed"]
+                                   else args.backend),
+                       "sample_evals_per_s": value * N,
+                       "samples_per_rank": [c for _, c in split_samples(N, world)],
                        "l2": "inputs larger than L2 (545 MB of FP64 fields per step)",
-                       "surrogate": recipe,
+                       "surrogate": recipe, "gate": gate,
                        "network_mode": {0: "per-layer kernels", 1: "one kernel per tile",
                                         2: "4-CTA clusters"}[net_mode] if use_dino else None},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,

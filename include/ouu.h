@@ -177,6 +177,39 @@ ouu_status ouu_dino_validate(ouu_problem_t p, ouu_dino_t d, const double* m_dev,
                              double risk_tol, double grad_tol, double* risk_err_out, double* grad_err_out,
                              int* passed_out);
 
+/* ---------------------------------------------------------------------------------------
+ * One sample average spread over ranks (one process per GPU).  Sec. 2.2 defines the risk over
+ * ONE fixed sample set and Sec. 2.3 its gradient as ONE weighted sum over it; rank k holds the
+ * contiguous block [first_k, first_k + n_k) of the n_total samples.  The weights need the
+ * mean and, for CVaR, t* of ALL the QoIs, so one evaluation takes two exchanges, both done by
+ * the caller (e.g. NCCL through torch.distributed):
+ *   1. ouu_shard_qoi on every rank: the QoIs of its block, q_local_dev [n_k] (device FP64);
+ *   2. all-gather: q_all_dev [n_total] = the ranks' q_local in rank order (8 n_total bytes);
+ *   3. ouu_shard_risk_partial on every rank: risk values, d rho / dt and t from all QoIs
+ *      (the same on every rank), and this rank's gradient part
+ *      grad_part_out[r][j] = sum over its samples of w_r,i (grad_z Q_i)_j;
+ *   4. all-reduce (sum, FP64) of grad_part_out over ranks: grad_z rho (n_risks * d_Z values).
+ * With one rank (n_total = n_k, first = 0) this gives ouu_risk_and_grad's results up to the
+ * order of the final sums. */
+
+/* Phase 1: the QoIs of this rank's n_local fields m_dev [n_local][n][n] at z_host [d_Z]
+ * (backend PDE: Newton state solves, kept in the problem's workspace for phase 2; DINO: the
+ * network with its reverse-mode gradients, kept in the network's buffers; AUTO as in
+ * ouu_risk_and_grad).  Output q_local_dev [n_local] (device FP64).  Synchronises.  Errors as
+ * ouu_risk_and_grad. */
+ouu_status ouu_shard_qoi(ouu_problem_t p, ouu_backend backend, ouu_dino_t dino, const double* m_dev, int n_local,
+                         const double* z_host, double* q_local_dev);
+/* Phase 2, after the all-gather: q_all_dev [n_total] (device FP64) holds every rank's QoIs and
+ * this rank's block starts at first_local.  Outputs (host): risk_out[n_risks],
+ * grad_part_out[n_risks][d_Z] (this rank's part of the gradient; the plain backend solves the
+ * adjoints of its samples with a nonzero weight here), grad_t_out[n_risks], t_out[n_risks]
+ * (nullable).  `dino` must be the network of the pending phase 1 (NULL for the plain path).
+ * Errors: STATE without a pending ouu_shard_qoi on p (each phase 1 serves one phase 2),
+ * INVALID_ARG for a block outside [0, n_total). */
+ouu_status ouu_shard_risk_partial(ouu_problem_t p, ouu_dino_t dino, const double* q_all_dev, int n_total,
+                                  int64_t first_local, const ouu_risk_desc* risks, int n_risks, double* risk_out,
+                                  double* grad_part_out, double* grad_t_out, double* t_out);
+
 /* Allocation-free variant of ouu_pde_solve_batch.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory when
  * they call in -- code under a device-memory budget or pool that forbids new

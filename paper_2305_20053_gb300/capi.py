@@ -86,6 +86,8 @@ SIGNATURES = {
     "ouu_risk_and_grad": (_i, [_vp, _i, _vp, _vp, _i, ctypes.POINTER(RiskDesc), _i, _dp, _dp, _dp, _dp, _dp,
                                ctypes.POINTER(EvalStats)]),
     "ouu_pde_solve_batch_noalloc": (_i, [ctypes.POINTER(ProblemDesc), _vp, _i, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "ouu_shard_qoi": (_i, [_vp, _i, _vp, _vp, _i, _dp, _vp]),
+    "ouu_shard_risk_partial": (_i, [_vp, _vp, _vp, _i, _i64, ctypes.POINTER(RiskDesc), _i, _dp, _dp, _dp, _dp]),
     "ouu_last_backend": (_i, [_vp]),
     "ouu_dino_save": (_i, [_vp, ctypes.c_char_p]),
     "ouu_dino_load": (_i, [_vp, ctypes.c_char_p]),
@@ -276,6 +278,32 @@ class Problem:
                                        p["grad"], p["gt"], p["t"], c["st_ref"]))
         return (c["risk"].copy(), c["grad"].copy(), c["gt"].copy(), c["t"].copy(),
                 EvalStats.from_buffer_copy(c["st"]))
+
+
+    def ouu_shard_qoi(self, backend, dino, m_dev, n_local, z_host, q_local_dev):
+        """Phase 1 of a sample set spread over ranks: this rank's QoIs into q_local_dev [n_local]."""
+        import torch
+        need(m_dev, n_local * self.n * self.n, "m_dev")
+        need(q_local_dev, n_local, "q_local_dev")
+        z = np.ascontiguousarray(z_host, dtype=np.float64)
+        need(z, self.d_z, "z_host")
+        check(load().ouu_shard_qoi(self.handle, backend, dino.handle if dino is not None else None,
+                                   dev_ptr(m_dev, torch.float64), n_local, z.ctypes.data_as(_dp),
+                                   dev_ptr(q_local_dev, torch.float64)))
+
+    def ouu_shard_risk_partial(self, dino, q_all_dev, n_total, first_local, risks):
+        """Phase 2: (risk[n_risks], grad_part[n_risks, d_Z], grad_t[n_risks], t[n_risks]) from the
+        gathered QoIs q_all_dev [n_total]; summing grad_part over ranks gives the gradient."""
+        import torch
+        need(q_all_dev, n_total, "q_all_dev")
+        nr = len(risks)
+        arr = (RiskDesc * nr)(*risks)
+        risk, grad, gt, t = np.zeros(nr), np.zeros((nr, self.d_z)), np.zeros(nr), np.zeros(nr)
+        check(load().ouu_shard_risk_partial(self.handle, dino.handle if dino is not None else None,
+                                            dev_ptr(q_all_dev, torch.float64), n_total, first_local, arr, nr,
+                                            risk.ctypes.data_as(_dp), grad.ctypes.data_as(_dp),
+                                            gt.ctypes.data_as(_dp), t.ctypes.data_as(_dp)))
+        return risk, grad, gt, t
 
 
 def ouu_pde_solve_batch_noalloc(desc, m_dev, n_samples, z_dev, z_stride, u_dev, q_dev, status_dev, stream=None):

@@ -391,6 +391,30 @@ ouu_status ouu_check_risks(const ouu_risk_desc* risks, int n_risks) {
   return OUU_OK;
 }
 
+void ouu_risk_dev(const ouu_risk_desc* risks, int n_risks, int N, RiskDev* rd) {
+  std::memset(rd, 0, sizeof(RiskDev) * OUU_MAX_RISKS);   // padding too: descriptors are compared bytewise
+  for (int r = 0; r < n_risks; ++r) {
+    rd[r].kind = risks[r].kind;
+    rd[r].kappa = risks[r].kappa;
+    rd[r].beta = risks[r].beta;
+    rd[r].eps = risks[r].eps;
+    rd[r].t = risks[r].t;
+    rd[r].t_optimal = risks[r].t_optimal;
+    risk_dev_finish(rd[r], N);
+  }
+}
+
+ouu_status ouu_upload_risks(ouu_problem* p, const RiskDev* rd, int n_risks, cudaStream_t us) {
+  if (n_risks != p->rd_n || us != p->rd_stream || std::memcmp(rd, p->rd_last, sizeof(RiskDev) * n_risks) != 0) {
+    p->rd_n = -1;   // stays invalid if the upload fails
+    OUU_CUDA_TRY(cudaMemcpyAsync(p->d_risks, rd, sizeof(RiskDev) * n_risks, cudaMemcpyHostToDevice, us));
+    std::memcpy(p->rd_last, rd, sizeof(RiskDev) * n_risks);
+    p->rd_n = n_risks;
+    p->rd_stream = us;
+  }
+  return OUU_OK;
+}
+
 // The MR-DINO risk evaluation as one stream-ordered sequence on dino->stream: projection +
 // network + reduced QoI + reverse-mode gradient, risk weights with the weighted gradient
 // sum, results (and the GEMM error flag) to the problem's pinned host mirror.  The risk
@@ -424,16 +448,7 @@ static ouu_status risk_and_grad_on(ouu_problem_t p, ouu_backend backend, ouu_din
   if (ouu_status st = ouu_check_risks(risks, n_risks)) return st;
   for (int j = 0; j < p->dz; ++j) OUU_CHECK_ARG(std::isfinite(z_host[j]), "z has a non-finite entry");
   RiskDev rd[OUU_MAX_RISKS];
-  std::memset(rd, 0, sizeof(rd));   // padding too: the descriptors are compared bytewise below
-  for (int r = 0; r < n_risks; ++r) {
-    rd[r].kind = risks[r].kind;
-    rd[r].kappa = risks[r].kappa;
-    rd[r].beta = risks[r].beta;
-    rd[r].eps = risks[r].eps;
-    rd[r].t = risks[r].t;
-    rd[r].t_optimal = risks[r].t_optimal;
-    risk_dev_finish(rd[r], n_samples);
-  }
+  ouu_risk_dev(risks, n_risks, n_samples, rd);
   const int dz = p->dz;
   double* d_res = p->d_out;                         // [n_risks][3]
   double* d_grad = p->d_out + 3 * OUU_MAX_RISKS;    // [n_risks][dz]
@@ -453,13 +468,7 @@ static ouu_status risk_and_grad_on(ouu_problem_t p, ouu_backend backend, ouu_din
   // which the results overwrite only later in the same stream); the MR-DINO evaluation copies
   // it itself.  No synchronisation before the work is enqueued.
   cudaStream_t us = backend == OUU_BACKEND_DINO ? dino->stream : p->stream;
-  if (n_risks != p->rd_n || us != p->rd_stream || std::memcmp(rd, p->rd_last, sizeof(RiskDev) * n_risks) != 0) {
-    p->rd_n = -1;   // stays invalid if the upload fails
-    OUU_CUDA_TRY(cudaMemcpyAsync(p->d_risks, rd, sizeof(RiskDev) * n_risks, cudaMemcpyHostToDevice, us));
-    std::memcpy(p->rd_last, rd, sizeof(RiskDev) * n_risks);
-    p->rd_n = n_risks;
-    p->rd_stream = us;
-  }
+  if (ouu_status st = ouu_upload_risks(p, rd, n_risks, us)) return st;
   if (backend != OUU_BACKEND_DINO) {
     std::memcpy(p->h_out, z_host, (size_t)dz * 8);
     OUU_CUDA_TRY(cudaMemcpyAsync(p->d_z, p->h_out, (size_t)dz * 8, cudaMemcpyHostToDevice, p->stream));

@@ -190,11 +190,15 @@ inline void risk_dev_finish(RiskDev& r, int N) {
 // Per-risk weights w[r][i], value[r], dt[r], t[r] from q[N] (moments on many CTAs, t*
 // selection on one, weights on many).  out layout: value[r], dt[r], t[r] at out[3r+0..2].
 // With per-sample gradients gq [N][ldg] (FP32), also grad_out[r][j] = sum_i w[r][i] gq[i][j].
+// A window (wfirst, wcount >= 0) restricts the weights written and the gradient sum to the
+// samples [wfirst, wfirst + wcount): w then holds [n_risks][wcount] and gq has wcount rows
+// (one rank's block of a sample set spread over ranks); the risk values, t and d rho / dt
+// still come from all N QoIs.  wcount < 0: the whole set.
 // scratch: OUU_RISK_SCRATCH doubles of device memory.
 #define OUU_RISK_SCRATCH 2048
 void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
                          double* scratch, cudaStream_t s, const float* gq = nullptr, int ldg = 0, int dz = 0,
-                         double* grad_out = nullptr);
+                         double* grad_out = nullptr, int wfirst = 0, int wcount = -1);
 
 // ------------------------------------------------------------------ fields
 void launch_sample_fields(int n, uint64_t seed, int64_t first, int count, const double* invlam,
@@ -233,6 +237,17 @@ struct ouu_problem {
   int32_t* h_stat = nullptr;  // pinned: per-sample status/iters copy (max_samples * 4)
   uint64_t serial = 0;        // unique per created problem (a network's held-out check names it)
   int last_backend = -1;      // backend of the last ouu_risk_and_grad that returned OUU_OK
+  // phase 1 of a sharded evaluation (ouu_shard_qoi) that phase 2 continues
+  int shard_backend = -1;     // -1: none pending
+  const double* shard_m = nullptr;
+  int shard_n = 0;
+  const ouu_dino* shard_dino = nullptr;
 };
+
+// Uploads the risk descriptors to p->d_risks on stream `us` unless they equal the last ones
+// sent there (every call ends synchronised, so an earlier upload on the same stream is done).
+ouu_status ouu_upload_risks(ouu_problem* p, const RiskDev* rd, int n_risks, cudaStream_t us);
+// Device form of the descriptors for a sample average over N samples.
+void ouu_risk_dev(const ouu_risk_desc* risks, int n_risks, int N, RiskDev* rd);
 
 int ouu_num_levels(int n);

@@ -601,12 +601,13 @@ static __device__ __forceinline__ void ff_add_prod(float& sh, float& sl, float w
 
 // Thread (g, jl) of the gradient sum: column j of samples s0 + kg + g + 2k, k < 16 (one batch of
 // loads in flight instead of one round trip per sample).
+// Rows of gq are the samples of the window [wlo, whi); samples outside it load 0.
 static __device__ __forceinline__ void load_grad_group(float (&gv)[16], const float* __restrict__ gq, int ldg, int dz,
-                                                       int s0, int s1, int kg, int g, int j) {
+                                                       int s0, int s1, int kg, int g, int j, int wlo, int whi) {
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     const int i = s0 + kg + g + 2 * k;
-    gv[k] = (i < s1 && j < dz) ? __ldg(gq + (int64_t)i * ldg + j) : 0.f;
+    gv[k] = (i < s1 && i >= wlo && i < whi && j < dz) ? __ldg(gq + (int64_t)(i - wlo) * ldg + j) : 0.f;
   }
 }
 
@@ -615,7 +616,7 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
                                                     const double* __restrict__ params, double* __restrict__ w,
                                                     double* __restrict__ part, unsigned* __restrict__ arrivals,
                                                     double* __restrict__ out, const float* __restrict__ gq, int ldg,
-                                                    int dz, double* __restrict__ grad_out) {
+                                                    int dz, double* __restrict__ grad_out, int wlo, int whi) {
   __shared__ bool last;
   __shared__ float wsh[OUU_MAX_RISKS][APPLY_W], wsl[OUU_MAX_RISKS][APPLY_W];
   __shared__ double gsum[OUU_MAX_RISKS][128];
@@ -629,8 +630,9 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
   for (int r = 0; r < OUU_MAX_RISKS; ++r) sv[r] = sd[r] = 0.0;
   for (int s0 = i0; s0 < i1; s0 += APPLY_W) {
     const int s1 = min(i1, s0 + APPLY_W), ns = s1 - s0;
+    const bool gsub = gq && s1 > wlo && s0 < whi;   // uniform over the block
     float gv[16];
-    if (gq) load_grad_group(gv, gq, ldg, dz, s0, s1, 0, g, jl);   // in flight during the weights
+    if (gsub) load_grad_group(gv, gq, ldg, dz, s0, s1, 0, g, jl, wlo, whi);   // in flight during the weights
     const int i = s0 + threadIdx.x;
     if (i < s1) {
       const double qi = q[i];
@@ -649,15 +651,15 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
           sv[r] += splus(x, R.eps, R.inv_eps);
           sd[r] += d1;
         }
-        w[(int64_t)r * N + i] = wi;
-        if (gq) {
+        if (i >= wlo && i < whi) w[(int64_t)r * (whi - wlo) + (i - wlo)] = wi;
+        if (gsub) {
           const float wh = (float)wi;
           wsh[r][threadIdx.x] = wh;
           wsl[r][threadIdx.x] = (float)(wi - (double)wh);
         }
       }
     }
-    if (gq) {
+    if (gsub) {
       __syncthreads();   // the weights of the sub-range are in shared memory
       for (int jb = 0; jb < dz; jb += 128) {
         const int j = jb + jl;
@@ -665,7 +667,7 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
 #pragma unroll
         for (int r = 0; r < OUU_MAX_RISKS; ++r) sh[r] = sl[r] = 0.f;
         for (int kg = 0; kg < ns; kg += 32) {
-          if (jb > 0 || kg > 0) load_grad_group(gv, gq, ldg, dz, s0, s1, kg, g, j);
+          if (jb > 0 || kg > 0) load_grad_group(gv, gq, ldg, dz, s0, s1, kg, g, j, wlo, whi);
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int ii = kg + g + 2 * k;
@@ -741,7 +743,9 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
 }
 
 void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
-                         double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out) {
+                         double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out,
+                         int wfirst, int wcount) {
+  const int wlo = wcount < 0 ? 0 : wfirst, whi = wcount < 0 ? N : wfirst + wcount;
   static_assert(OUU_RISK_SCRATCH >= 3 * OUU_MAX_RISKS + 2 * OUU_MAX_RISKS * RISK_BLOCKS + 1, "risk scratch size");
   double* params = scratch;
   double* part = scratch + 3 * OUU_MAX_RISKS;
@@ -750,7 +754,7 @@ void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n
              params, gq ? grad_out : nullptr, n_risks * dz);
   unsigned* arrivals = (unsigned*)(scratch + OUU_RISK_SCRATCH - 1);   // zeroed at problem creation
   launch_pdl(k_risk_apply, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, risks_dev, n_risks, (const double*)params, w,
-             part, arrivals, out, gq, ldg, dz, grad_out);
+             part, arrivals, out, gq, ldg, dz, grad_out, wlo, whi);
 }
 
 // Kernel-level entry used by the risk-weight numerics test (declared in include/ouu_kernels.h).
