@@ -342,9 +342,21 @@ ouu_status ouu_dino_loss_grad(ouu_dino_t d, const float* xi_dev, const float* z_
  * [n_samples][n][n]: KL projection, network, reduced QoI.  Outputs (device, each
  * nullable): phi_dev [n][r_u] FP32, jphi_dev [n][d_Z][r_u] FP32 (forward-mode
  * d_z phi), q_dev [n] FP64 (Q(u_w) by the reduced form), gradq_dev [n][d_Z]
- * FP64 (grad_z Q by reverse mode through the network).  Synchronises. */
+ * FP64 (grad_z Q by reverse mode through the network), u_dev [n][n][n] FP32 (the
+ * decoded states u_w = Phi phi + ubar of Sec. 3.3, as ouu_dino_decode).  Synchronises. */
 ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_samples, const double* z_host, float* phi_dev,
-                         float* jphi_dev, double* q_dev, double* gradq_dev);
+                         float* jphi_dev, double* q_dev, double* gradq_dev, float* u_dev);
+
+/* POD decode of Sec. 3.3: u_w = Phi phi + ubar for the reduced coefficients phi_dev
+ * [n_samples][r_u] (FP32 device, e.g. ouu_dino_eval's phi_dev) into u_dev [n_samples][n][n]
+ * (FP32 device; zero on the boundary), and the QoI of the decoded states,
+ * q_dev[i] = 1/2 h^2 sum over the interior of (u_w - u_t)^2 (FP64 device, nullable), which
+ * equals the reduced form 1/2 ||phi + c||^2 + const of ouu_dino_eval up to rounding.  One
+ * tensor-core GEMM (K = 3 r_u: phi and Phi each split into two BF16 parts, three of the four
+ * cross products kept, FP32 accumulation, about 16 significant bits) with the sum of squares
+ * fused into its epilogue.  Synchronises.  Errors: STATE before the bases are installed,
+ * INVALID_ARG for n_samples outside [1, max_eval]. */
+ouu_status ouu_dino_decode(ouu_dino_t d, const float* phi_dev, int n_samples, float* u_dev, double* q_dev);
 
 /* DINO risk evaluations in ouu_risk_and_grad are replayed from a CUDA graph that is
  * captured (on a private stream, after one eager evaluation) for each new combination

@@ -221,6 +221,17 @@ def reduced_qoi_constant(Phi, ubar, ut_int, h):
     return c, const
 
 
+def decode_states(phi, Phi, ubar):
+    """Decoded interior states u_w = Phi phi + ubar (Sec. 3.3) of coefficient rows phi (B, r_u)."""
+    return phi @ Phi.T + ubar
+
+
+def decoded_qoi(u_int, ut_int, h):
+    """Q(u) = 1/2 h^2 sum over the interior nodes of (u - u_t)^2 (the tracking QoI of Sec. 4.2)."""
+    diff = u_int - ut_int
+    return 0.5 * h * h * np.sum(diff * diff, axis=-1)
+
+
 def eval_surrogate(net: MLP, xi, z, Phi, ubar, ut_int, h, decode=True, bf16=False):
     """Per-sample Q_i and grad_z Q_i of the surrogate.  With decode=True the state
     u_w = Phi phi + ubar is formed and Q, dQ/du are taken on it (the chain rule of
@@ -228,10 +239,9 @@ def eval_surrogate(net: MLP, xi, z, Phi, ubar, ut_int, h, decode=True, bf16=Fals
     st = net.forward(xi, z, jacobian=True, bf16=bf16)
     phi, J = st["phi"], st["J"]
     if decode:
-        uw = phi @ Phi.T + ubar
-        diff = uw - ut_int
-        Q = 0.5 * h * h * np.sum(diff * diff, axis=1)
-        dq_red = h * h * (diff @ Phi)                 # (dQ/du) Phi
+        uw = decode_states(phi, Phi, ubar)
+        Q = decoded_qoi(uw, ut_int, h)
+        dq_red = h * h * ((uw - ut_int) @ Phi)         # (dQ/du) Phi
     else:
         c, const = reduced_qoi_constant(Phi, ubar, ut_int, h)
         Q = 0.5 * np.sum((phi + c) ** 2, axis=1) + const

@@ -109,7 +109,8 @@ SIGNATURES = {
     "ouu_dino_jacobian_data": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "ouu_dino_train_step": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, ctypes.c_float, _dp]),
     "ouu_dino_loss_grad": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(ctypes.c_float), _dp]),
-    "ouu_dino_eval": (_i, [_vp, _vp, _i, _dp, _vp, _vp, _vp, _vp]),
+    "ouu_dino_eval": (_i, [_vp, _vp, _i, _dp, _vp, _vp, _vp, _vp, _vp]),
+    "ouu_dino_decode": (_i, [_vp, _vp, _i, _vp, _vp]),
     "ouu_dino_set_graphs": (_i, [_vp, _i]),
     "ouu_dino_set_fused_network": (_i, [_vp, _i]),
     "ouu_kernel_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _i, _i, _vp, _i, _i,
@@ -524,7 +525,7 @@ class Dino:
                                         g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), loss.ctypes.data_as(_dp)))
         return float(loss[0]), g
 
-    def ouu_dino_eval(self, m_dev, n, z_host, phi_dev=None, jphi_dev=None, q_dev=None, gradq_dev=None):
+    def ouu_dino_eval(self, m_dev, n, z_host, phi_dev=None, jphi_dev=None, q_dev=None, gradq_dev=None, u_dev=None):
         import torch
         z = np.ascontiguousarray(z_host, dtype=np.float64)
         if z.size != self.d_z:
@@ -532,11 +533,21 @@ class Dino:
         d, nn = self.desc, self.desc.n * self.desc.n
         for t, count, name in ((m_dev, n * nn, "m_dev"), (phi_dev, n * d.r_u, "phi_dev"),
                                (jphi_dev, n * self.d_z * d.r_u, "jphi_dev"), (q_dev, n, "q_dev"),
-                               (gradq_dev, n * self.d_z, "gradq_dev")):
+                               (gradq_dev, n * self.d_z, "gradq_dev"), (u_dev, n * nn, "u_dev")):
             need(t, count, name)
         check(load().ouu_dino_eval(self.handle, dev_ptr(m_dev, torch.float64), n, z.ctypes.data_as(_dp),
                                    dev_ptr(phi_dev, torch.float32), dev_ptr(jphi_dev, torch.float32),
-                                   dev_ptr(q_dev, torch.float64), dev_ptr(gradq_dev, torch.float64)))
+                                   dev_ptr(q_dev, torch.float64), dev_ptr(gradq_dev, torch.float64),
+                                   dev_ptr(u_dev, torch.float32)))
+
+    def ouu_dino_decode(self, phi_dev, n, u_dev, q_dev=None):
+        """u_w = Phi phi + ubar (FP32 [n][n][n]) and the decoded QoI (FP64 [n], optional)."""
+        import torch
+        nn = self.desc.n * self.desc.n
+        for t, count, name in ((phi_dev, n * self.desc.r_u, "phi_dev"), (u_dev, n * nn, "u_dev"), (q_dev, n, "q_dev")):
+            need(t, count, name)
+        check(load().ouu_dino_decode(self.handle, dev_ptr(phi_dev, torch.float32), n, dev_ptr(u_dev, torch.float32),
+                                     dev_ptr(q_dev, torch.float64)))
 
 
 def flatten_params(Ws, bs):

@@ -318,7 +318,7 @@ static void free_dino(ouu_dino* d) {
                   d->d_c, d->d_cf, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
                   d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
                   d->Ge, d->GQe, d->Qe, d->Qpart, d->d_zf, d->d_err, d->d_klp_ctr, d->d_gov, d->d_oscale,
-                  d->d_klbias};
+                  d->d_klbias, d->d_dec_b, d->d_dec_a, d->d_ubarf, d->d_utf, d->d_qdec};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < 4; ++l) {
     cudaFree(d->A[l]);
@@ -414,6 +414,11 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   al((void**)&d->d_c, (size_t)d->ru * 8 + 16);
   al((void**)&d->d_cf, (size_t)d->ru * 4 + 16);
   al((void**)&d->d_oscale, (size_t)d->ru * 4);
+  al((void**)&d->d_dec_b, (size_t)d->nn * 3 * rup * 2);
+  al((void**)&d->d_dec_a, E * 3 * rup * 2);
+  al((void**)&d->d_ubarf, (size_t)d->nn * 4);
+  al((void**)&d->d_utf, (size_t)d->nn * 4);
+  al((void**)&d->d_qdec, E * 8);
   al((void**)&d->d_wkl, (size_t)d->rm * d->nnp * 2);
   al((void**)&d->d_kl_order, (size_t)d->rm * 4);
   al((void**)&d->d_klbias, (size_t)d->rm * 4);
@@ -536,11 +541,90 @@ extern "C" ouu_status ouu_dino_get_params(ouu_dino_t d, float* params_host, size
   return OUU_OK;
 }
 
-// Installs Phi (FP64 copy already in d_phi64) and ubar: FP32 copy, c and the constant.
+// x = hi + lo with hi, lo BF16 (round to nearest): hi x hi' + hi x lo' + lo x hi' carries about
+// 16 significant bits of a product of two such splits.
+static __device__ __forceinline__ void bf16_split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Basis side of the decode GEMM: b[p][k] = Phi_hi, b[p][rup + k] = Phi_lo, b[p][2 rup + k] =
+// Phi_hi of mode k at node p (zero for k >= ru); ubar and the target state in FP32, the latter
+// zero on the boundary (the QoI sums over the interior, where Phi and ubar live).
+__global__ void k_decode_basis(const double* __restrict__ phi64, const double* __restrict__ ubar,
+                               const double* __restrict__ ut, int n, int ru, int rup, __nv_bfloat16* __restrict__ b,
+                               float* __restrict__ ubarf, float* __restrict__ utf) {
+  const int nn = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)nn * rup;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / rup), k = (int)(e - (int64_t)p * rup);
+    __nv_bfloat16 hi = __float2bfloat16_rn(0.f), lo = hi;
+    if (k < ru) bf16_split((float)phi64[(int64_t)k * nn + p], hi, lo);
+    __nv_bfloat16* row = b + (int64_t)p * 3 * rup;
+    row[k] = hi;
+    row[rup + k] = lo;
+    row[2 * rup + k] = hi;
+    if (k == 0) {
+      const int ix = p % n, iy = p / n;
+      const bool interior = ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1;
+      ubarf[p] = (float)ubar[p];
+      utf[p] = interior ? (float)ut[p] : 0.f;
+    }
+  }
+}
+
+// Coefficient side: a[i][k] = a[i][rup + k] = phi_hi, a[i][2 rup + k] = phi_lo (zero for k >= ru).
+__global__ void k_decode_coeffs(const float* __restrict__ phi, int ldphi, int N, int ru, int rup,
+                                __nv_bfloat16* __restrict__ a) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)N * rup;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / rup), k = (int)(e - (int64_t)i * rup);
+    __nv_bfloat16 hi = __float2bfloat16_rn(0.f), lo = hi;
+    if (k < ru) bf16_split(phi[(int64_t)i * ldphi + k], hi, lo);
+    __nv_bfloat16* row = a + (int64_t)i * 3 * rup;
+    row[k] = hi;
+    row[rup + k] = hi;
+    row[2 * rup + k] = lo;
+  }
+}
+
+ouu_status dino_decode(ouu_dino* d, const float* phi, int ldphi, int N, float* u, double* q) {
+  const int rup = pad8(d->ru), K = 3 * rup;
+  k_decode_coeffs<<<grid_for((int64_t)N * rup), 256, 0, d->stream>>>(phi, ldphi, N, d->ru, rup, d->d_dec_a);
+  OUU_CUDA_TRY(cudaGetLastError());
+  OUU_CUDA_TRY(cudaMemsetAsync(q, 0, (size_t)N * 8, d->stream));
+  EpiParams e = epi(EPI_DECODE);
+  e.out_f32 = u;
+  e.ld_f32 = d->nn;
+  e.col_add = d->d_ubarf;
+  e.col_ref = d->d_utf;
+  e.out_q = q;
+  e.qconst = 0.5 * d->h * d->h;
+  return gemm(d, d->d_dec_a, K, d->d_dec_b, K, N, d->nn, K, e);
+}
+
+static ouu_status check_err(ouu_dino* d);
+
+extern "C" ouu_status ouu_dino_decode(ouu_dino_t d, const float* phi_dev, int n_samples, float* u_dev,
+                                      double* q_dev) {
+  OUU_CHECK_ARG(d && phi_dev && u_dev, "null argument");
+  if (!d->bases_ready) {
+    ouu_set_error("bases not built");
+    return OUU_ERR_STATE;
+  }
+  OUU_CHECK_ARG(n_samples >= 1 && n_samples <= d->maxE, "n_samples outside [1, max_eval]");
+  DINO_TRY(dino_decode(d, phi_dev, d->ru, n_samples, u_dev, q_dev ? q_dev : d->d_qdec));
+  return check_err(d);
+}
+
+// Installs Phi (FP64 copy already in d_phi64) and ubar: FP32 copy, c and the constant, and
+// the basis side of the decode GEMM.
 ouu_status dino_install_bases(ouu_dino* d) {
   d->val_ok = 0;
   const int64_t cnt = (int64_t)d->ru * d->nn;
   k_phi_to_f32<<<grid_for(cnt), 256, 0, d->stream>>>(d->d_phi64, cnt, d->d_phi);
+  k_decode_basis<<<grid_for((int64_t)d->nn * pad8(d->ru)), 256, 0, d->stream>>>(
+      d->d_phi64, d->d_ubar, d->d_ut, d->n, d->ru, pad8(d->ru), d->d_dec_b, d->d_ubarf, d->d_utf);
   k_reduced_qoi_terms<<<d->ru + 1, 256, 0, d->stream>>>(d->d_phi64, d->d_ubar, d->d_ut, d->n, d->ru, d->d_c,
                                                          d->d_c + d->ru);
   OUU_CUDA_TRY(cudaGetLastError());
@@ -864,7 +948,8 @@ static ouu_status dino_network(ouu_dino* d, int N, bool want_grad) {
 }
 
 extern "C" ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_samples, const double* z_host,
-                                    float* phi_dev, float* jphi_dev, double* q_dev, double* gradq_dev) {
+                                    float* phi_dev, float* jphi_dev, double* q_dev, double* gradq_dev,
+                                    float* u_dev) {
   OUU_CHECK_ARG(d && m_dev && z_host, "null argument");
   OUU_CHECK_ARG(d->bases_ready, "bases not built");
   OUU_CHECK_ARG(n_samples >= 1 && n_samples <= d->maxE, "n_samples outside [1, max_eval]");
@@ -876,6 +961,7 @@ extern "C" ouu_status ouu_dino_eval(ouu_dino_t d, const double* m_dev, int n_sam
   if (q_dev) OUU_CUDA_TRY(cudaMemcpyAsync(q_dev, d->Qe, (size_t)n_samples * 8, cudaMemcpyDeviceToDevice, d->stream));
   if (gradq_dev)
     k_f32_to_f64<<<grid_for((int64_t)n_samples * dz), 256, 0, d->stream>>>(d->GQe, dzp, n_samples, dz, gradq_dev);
+  if (u_dev) DINO_TRY(dino_decode(d, d->OUTe, rup, n_samples, u_dev, d->d_qdec));
   if (jphi_dev) {
     // forward-mode Jacobian in chunks of max_batch samples (tangent rows go straight to jphi)
     float* zf = d->d_zf;

@@ -29,6 +29,13 @@ struct ouu_dino {
   double* d_c = nullptr;           // [ru]  c = h^2 Phi^T (ubar - ut)
   float* d_cf = nullptr;           // [ru]  c in FP32 (the output layer's QoI epilogue)
   float* d_oscale = nullptr;       // [ru]  fixed output scale: phi = s * (W3 h3 + b3)
+  // POD decode u_w = Phi phi + ubar as one GEMM over K = 3 rup with split BF16 operands:
+  // [phi_hi | phi_hi | phi_lo] x [Phi_hi | Phi_lo | Phi_hi]^T
+  __nv_bfloat16* d_dec_b = nullptr;   // [nn][3 rup]  the basis side
+  __nv_bfloat16* d_dec_a = nullptr;   // [maxE][3 rup] the coefficient side of the current call
+  float* d_ubarf = nullptr;        // [nn] ubar in FP32
+  float* d_utf = nullptr;          // [nn] target state in FP32, zero on the boundary
+  double* d_qdec = nullptr;        // [maxE] decoded QoIs when the caller passes none
   double qconst = 0.0;
   __nv_bfloat16* d_wkl = nullptr;  // [rm][nnp] KL projection rows
   int* d_kl_order = nullptr;       // [rm] flat mode index of each KL coordinate
@@ -86,6 +93,9 @@ bool dino_trusted(const ouu_dino* d, const ouu_problem* p, int n_samples);
 
 // DINO forward/backward pieces used by the C ABI (dino.cu).
 ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad);
+// Decoded states u[N][nn] (FP32) = Phi phi_i + ubar from the coefficients phi [N][ldphi] (FP32),
+// and the decoded QoI q[N] = 1/2 h^2 sum over the interior (u - u_t)^2 (FP64), on d->stream.
+ouu_status dino_decode(ouu_dino* d, const float* phi, int ldphi, int N, float* u, double* q);
 
 // The evaluation network in one fused kernel per 128-sample tile (mlp_fused.cu): layer-0
 // input from XIe and d_zf, forward with GELU (gelu' to Ae), reduced QoI (Qe, OUTe), reverse

@@ -46,6 +46,26 @@ static __device__ __forceinline__ void epi_quads(float* stage, const float* sbia
   constexpr int SROW = BN + 4, QPR = BN / 4;
   const bool vec = ep.vec != 0;
   const float alpha = ep.alpha;
+  if (MODE == EPI_DECODE) {
+    // consecutive threads on consecutive columns of a row (coalesced rows of any length or
+    // alignment); BN is a multiple of 32, so a warp's 32 elements share one row and its
+    // squared differences are summed by a warp reduction, then per row in shared memory
+    const int lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < GEMM_BM * BN; e += GEMM_THREADS) {
+      const int tr = e / BN, cc = e - tr * BN, r = m0 + tr, c = n0 + cc;
+      float d = 0.f;
+      if (r < M && c < N) {
+        const float v = stage[tr * SROW + cc] + sadd[cc];
+        ep.out_f32[(size_t)r * ep.ld_f32 + c] = v;
+        d = v - sscale[cc];   // sscale holds col_ref in this mode
+      }
+      float sq = d * d;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0 && r < M) atomicAdd(&rowsum[tr], sq);
+    }
+    return;
+  }
   if (MODE == EPI_QOI) {
     // whole rows per warp, lanes over quads, the row's quadratic by a warp reduction
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -216,7 +236,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   for (int i = threadIdx.x; i < BN; i += GEMM_THREADS) {   // per-column epilogue constants
     const int c = n0 + i;
     s_bias[i] = (c < N && ep.bias && blockIdx.z == 0) ? ep.bias[c] : 0.f;
-    s_scale[i] = (c < N && ep.col_scale) ? ep.col_scale[c] : 1.f;
+    s_scale[i] = ep.mode == EPI_DECODE ? (c < N ? ep.col_ref[c] : 0.f) : (c < N && ep.col_scale) ? ep.col_scale[c] : 1.f;
     s_add[i] = (c < N && ep.col_add) ? ep.col_add[c] : 0.f;
   }
   for (int i = threadIdx.x; i < GEMM_BM; i += GEMM_THREADS) s_rowsum[i] = 0.f;
@@ -311,6 +331,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         epi_quads<BN, EPI_SCALE>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
       else if (ep.mode == EPI_QOI)
         epi_quads<BN, EPI_QOI>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
+      else if (ep.mode == EPI_DECODE)
+        epi_quads<BN, EPI_DECODE>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, false);
       else
         epi_quads<BN, EPI_DGELU_SCALE>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
     }
@@ -318,6 +340,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       __syncthreads();
       for (int tr = threadIdx.x; tr < GEMM_BM; tr += GEMM_THREADS)
         if (m0 + tr < M) ep.out_q[m0 + tr] = ep.qconst + 0.5 * (double)s_rowsum[tr];
+    }
+    if (ep.mode == EPI_DECODE && run) {   // this tile's columns of each row's sum
+      __syncthreads();
+      for (int tr = threadIdx.x; tr < GEMM_BM; tr += GEMM_THREADS)
+        if (m0 + tr < M) atomicAdd(&ep.out_q[m0 + tr], ep.qconst * (double)s_rowsum[tr]);
     }
     if (ep.out_t_bf16 && !splitk) {
       // Epilogue C (all warps): transposed output, consecutive threads on consecutive rows.
@@ -426,7 +453,10 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   OUU_CHECK_ARG(M >= 1 && N >= 1 && K >= 1, "GEMM sizes must be positive");
   OUU_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0, "GEMM operands must be 16-byte aligned");
   OUU_CHECK_ARG(lda % 8 == 0 && ldb % 8 == 0 && lda >= K && ldb >= K, "GEMM leading dimensions: multiple of 8, >= K");
-  OUU_CHECK_ARG(ep.mode >= EPI_LINEAR && ep.mode <= EPI_QOI, "unknown epilogue mode");
+  OUU_CHECK_ARG(ep.mode >= EPI_LINEAR && ep.mode <= EPI_DECODE, "unknown epilogue mode");
+  OUU_CHECK_ARG(ep.mode != EPI_DECODE || (ep.out_f32 && ep.out_q && ep.col_add && ep.col_ref && splits == 1 &&
+                                          !ep.accumulate && !ep.out_bf16 && !ep.out_t_bf16 && !ep.out2_bf16),
+                "EPI_DECODE needs out_f32, out_q, col_add and col_ref, one FP32 output and no split-K");
   OUU_CHECK_ARG(ep.mode != EPI_QOI || (N <= 256 && ep.out_q && ep.col_scale && ep.col_add && splits == 1 &&
                                        !ep.accumulate && !ep.out_t_bf16),
                 "EPI_QOI needs N <= 256, out_q, col_scale and col_add, and no split-K");
@@ -469,6 +499,7 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
     cudaEventCreate(&e1);
     for (int bn : {256, 208, 128, 112, 80, 64}) {
       if (ep.mode == EPI_QOI && bn < N) continue;
+      if (ep.mode == EPI_DECODE && bn % 32) continue;   // a warp's 32 columns must share a row
       if (launch_by_bn(bn, ta, B, ldb, M, N, K, e2, err, s, splits) != OUU_OK) continue;   // warm-up
       cudaEventRecord(e0, s);
       for (int r = 0; r < 3; ++r) launch_by_bn(bn, ta, B, ldb, M, N, K, e2, err, s, splits);
@@ -504,6 +535,7 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   const long mt = (long)((M + GEMM_BM - 1) / GEMM_BM) * splits;
   for (int bn : cands) {
     if (ep.mode == EPI_QOI && bn < N) continue;   // whole rows in one tile
+    if (ep.mode == EPI_DECODE && bn % 32) continue;   // a warp's 32 columns must share a row
     const long tiles = mt * ((N + bn - 1) / bn);
     const long cost = ((tiles + sms - 1) / sms) * (bn + 64);
     if (cost < best_cost) {

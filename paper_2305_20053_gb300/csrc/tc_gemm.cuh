@@ -17,6 +17,8 @@ enum EpiMode {
   EPI_QOI = 5,          // phi = (acc + bias[c]) * col_scale[c] -> out_f32; v = phi + col_add[c];
                         // bf16 outputs = v * col_scale[c]; out_q[r] = qconst + 1/2 sum_c v^2
                         // (one N tile: N <= 256)
+  EPI_DECODE = 6,       // v = acc + col_add[c] -> out_f32 (coalesced rows);
+                        // out_q[r] += qconst * sum_c (v - col_ref[c])^2 (out_q zeroed beforehand)
 };
 
 struct EpiParams {
@@ -38,8 +40,9 @@ struct EpiParams {
   int aux_rdiv;
   int vec;                        // set by ouu_gemm_bf16: vector epilogue accesses are aligned
   const float* col_add;           // EPI_QOI: per-column shift c
-  double* out_q;                  // EPI_QOI: [M] per-row quadratic
-  double qconst;                  // EPI_QOI: added to every out_q
+  double* out_q;                  // EPI_QOI, EPI_DECODE: [M] per-row quadratic
+  double qconst;                  // EPI_QOI: added to every out_q; EPI_DECODE: factor of the sum
+  const float* col_ref;           // EPI_DECODE: per-column reference subtracted before squaring
 };
 
 // Tensor map of a row-major BF16 matrix [rows][ld] (K = inner, contiguous), box 64 x box_rows.

@@ -285,3 +285,22 @@ def test_adam_second_step():
     want = p1[0][0] - lr * (17.0 / 19.0) / (np.sqrt(9991.0 / 1999.0) + 1e-8)
     np.testing.assert_allclose(p2[0], [want], rtol=1e-14)
     assert opt.t == 2
+
+
+def test_decode_reconstructs_states_in_the_basis_span():
+    """Sec. 3.3: for u = ubar + Phi a (a state the POD basis represents exactly), the reduced
+    coordinates Phi^T M (u - ubar) are a (M-orthonormal Phi), and decoding them returns u; the
+    decoded QoI is 1/2 h^2 ||u - u_t||^2 written out over the interior nodes."""
+    rng = np.random.default_rng(12)
+    d, r_u, h = 30, 4, 0.25
+    Phi = np.linalg.qr(rng.standard_normal((d, r_u)))[0] / h        # h^2 Phi^T Phi = I
+    ubar = rng.standard_normal(d)
+    a = rng.standard_normal((3, r_u))
+    u = ubar + a @ Phi.T
+    y = h * h * (u - ubar) @ Phi
+    np.testing.assert_allclose(y, a, atol=1e-12)
+    np.testing.assert_allclose(dino.decode_states(y, Phi, ubar), u, atol=1e-12)
+    ut = rng.standard_normal(d)
+    q = dino.decoded_qoi(u, ut, h)
+    for i in range(3):
+        assert q[i] == pytest.approx(0.5 * h * h * sum((u[i, k] - ut[k]) ** 2 for k in range(d)), rel=1e-14)
