@@ -204,8 +204,10 @@ ouu_status ouu_shard_qoi(ouu_problem_t p, ouu_backend backend, ouu_dino_t dino, 
  * grad_part_out[n_risks][d_Z] (this rank's part of the gradient; the plain backend solves the
  * adjoints of its samples with a nonzero weight here), grad_t_out[n_risks], t_out[n_risks]
  * (nullable).  `dino` must be the network of the pending phase 1 (NULL for the plain path).
- * Errors: STATE without a pending ouu_shard_qoi on p (each phase 1 serves one phase 2),
- * INVALID_ARG for a block outside [0, n_total). */
+ * Errors: STATE without a pending ouu_shard_qoi on p (each phase 1 serves one phase 2), or
+ * when the network has evaluated other samples since (its buffers hold the per-sample
+ * gradients of phase 1: every rank needs its own network handle); INVALID_ARG for a block
+ * outside [0, n_total). */
 ouu_status ouu_shard_risk_partial(ouu_problem_t p, ouu_dino_t dino, const double* q_all_dev, int n_total,
                                   int64_t first_local, const ouu_risk_desc* risks, int n_risks, double* risk_out,
                                   double* grad_part_out, double* grad_t_out, double* t_out);

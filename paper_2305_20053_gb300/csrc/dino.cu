@@ -874,6 +874,7 @@ extern "C" ouu_status ouu_dino_loss_grad(ouu_dino_t d, const float* xi_dev, cons
 static ouu_status dino_network(ouu_dino* d, int N, bool want_grad);
 
 ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad) {
+  ++d->eval_count;   // the per-sample buffers now belong to this evaluation
   float* zh = (float*)d->h_pin;
   for (int j = 0; j < d->dz; ++j) zh[j] = (float)z_host[j];
   OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)d->dz * 4, cudaMemcpyHostToDevice, d->stream));
@@ -986,6 +987,7 @@ extern "C" ouu_status ouu_kernel_dino_network(ouu_dino_t d, const float* xi_dev,
   for (int j = 0; j < dz; ++j) zh[j] = (float)z_host[j];
   OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)dz * 4, cudaMemcpyHostToDevice, d->stream));
   OUU_CUDA_TRY(cudaMemcpyAsync(d->XIe, xi_dev, (size_t)n_samples * d->rm * 4, cudaMemcpyDeviceToDevice, d->stream));
+  ++d->eval_count;
   const int saved = d->fused_mlp;
   d->fused_mlp = mode;
   const ouu_status st = dino_network(d, n_samples, gradq_dev != nullptr);

@@ -81,6 +81,7 @@ struct ouu_dino {
                                    // 128-sample tile (mlp_fused.cu), 2 one kernel over 4-CTA
                                    // clusters (mlp_cluster.cu); 1 and 2 when the sizes fit
   bool capturing = false;
+  uint64_t eval_count = 0;         // evaluations so far (a pending ouu_shard_qoi names the one it ran)
   // held-out check against the plain path (ouu_dino_validate): passed for the problem with this
   // serial; cleared whenever parameters, bases or output scale change
   int val_ok = 0;

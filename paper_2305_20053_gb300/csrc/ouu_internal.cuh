@@ -242,6 +242,7 @@ struct ouu_problem {
   const double* shard_m = nullptr;
   int shard_n = 0;
   const ouu_dino* shard_dino = nullptr;
+  uint64_t shard_dino_eval = 0;   // the network's evaluation that phase 1 ran
 };
 
 // Uploads the risk descriptors to p->d_risks on stream `us` unless they equal the last ones

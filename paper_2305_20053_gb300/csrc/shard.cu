@@ -89,6 +89,7 @@ extern "C" ouu_status ouu_shard_qoi(ouu_problem_t p, ouu_backend backend, ouu_di
   p->shard_m = m_dev;
   p->shard_n = n_local;
   p->shard_dino = backend == OUU_BACKEND_DINO ? dino : nullptr;
+  p->shard_dino_eval = backend == OUU_BACKEND_DINO ? dino->eval_count : 0;
   return OUU_OK;
 }
 
@@ -104,6 +105,12 @@ extern "C" ouu_status ouu_shard_risk_partial(ouu_problem_t p, ouu_dino_t dino, c
   }
   const int n_local = p->shard_n, backend = p->shard_backend;
   OUU_CHECK_ARG(backend != OUU_BACKEND_DINO || dino == p->shard_dino, "not the network of the pending ouu_shard_qoi");
+  if (backend == OUU_BACKEND_DINO && dino->eval_count != p->shard_dino_eval) {
+    // its per-sample gradients now belong to a later evaluation: each rank needs its own network
+    p->shard_backend = -1;
+    ouu_set_error("the network evaluated other samples since this problem's ouu_shard_qoi");
+    return OUU_ERR_STATE;
+  }
   OUU_CHECK_ARG(n_total >= n_local && first_local >= 0 && first_local + n_local <= (int64_t)n_total,
                 "the block [first_local, first_local + n_local) must lie in [0, n_total)");
   if (ouu_status st = ouu_check_risks(risks, n_risks)) return st;

@@ -67,7 +67,8 @@ def generate_training_data(P, D, n_train, seed_fields=SEED_TRAIN_FIELDS, seed_z=
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     m = torch.empty(n_train, n, n, dtype=torch.float64, device="cuda")
-    P.ouu_sample_fields(seed_fields, 0, n_train, m)
+    for f in range(0, n_train, 65535):   # the sampling call takes up to 65535 fields
+        P.ouu_sample_fields(seed_fields, f, min(65535, n_train - f), m[f:])
     z = torch.tensor(controls(seed_z, n_train, dz), device="cuda")
     u = torch.empty(n_train, n, n, dtype=torch.float64, device="cuda")
     q = torch.empty(n_train, dtype=torch.float64, device="cuda")

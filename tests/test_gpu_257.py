@@ -43,8 +43,8 @@ def test_state_adjoint_257():
     from paper_2305_20053_gb300 import capi
     N = 2
     P = capi.Problem(n=N_GRID, lattice_L=L, max_samples=N)
-    m = torch.empty(N, N_GRID, N_GRID, dtype=torch.float64, device="cuda")
-    P.ouu_sample_fields(SEED_SAA, 0, N, m)
+    ms = field.sample_fields(SEED_SAA, 0, N, N_GRID)   # the oracle's draws on both sides
+    m = torch.tensor(ms, device="cuda")
     z = controls(SEED_EVAL_Z, 1, DZ)[0]
     u = torch.empty_like(m)
     q = torch.empty(N, dtype=torch.float64, device="cuda")
@@ -55,7 +55,7 @@ def test_state_adjoint_257():
     P.ouu_adjoint_batch(m, u, N, lam, g)
     prob = pde.Problem(n=N_GRID, L=L)
     G = field.control_sources(N_GRID, L, prob.width)
-    refs = pde.solve_batch(m.cpu().numpy(), z, G, field.target_state(N_GRID), prob, with_adjoint=True)
+    refs = pde.solve_batch(ms, z, G, field.target_state(N_GRID), prob, with_adjoint=True)
     u, q, g, st = (t.cpu().numpy() for t in (u, q, g, st))
     assert np.all(st == 0)
     for i, r in enumerate(refs):
@@ -91,15 +91,15 @@ def test_dino_eval_257():
     D.ouu_dino_set_output_scale(scale)
     D.ouu_dino_set_bases(torch.tensor(phi_full, device="cuda"), torch.tensor(ub_full, device="cuda"))
     P = capi.Problem(n=n, lattice_L=L, max_samples=N)
-    m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
-    P.ouu_sample_fields(SEED_SAA, 0, N, m)
+    mf = field.sample_fields(SEED_SAA, 0, N, n).reshape(N, -1)   # the oracle's draws on both sides
+    m = torch.tensor(mf.reshape(N, n, n), device="cuda")
     z = controls(SEED_EVAL_Z, 1, DZ)[0]
     phi = torch.empty(N, RU, dtype=torch.float32, device="cuda")
     q = torch.empty(N, dtype=torch.float64, device="cuda")
     gq = torch.empty(N, DZ, dtype=torch.float64, device="cuda")
     D.ouu_dino_eval(m, N, z, phi, None, q, gq)
     Wkl, _ = dino.kl_projection_matrix(n, RM)
-    xi = dino.project_fields(m.cpu().numpy().reshape(N, -1), Wkl, bf16=True)
+    xi = dino.project_fields(mf, Wkl, bf16=True)
     ut = field.target_state(n)[1:-1, 1:-1].ravel()
     Qbf, gbf, pbf, _ = dino.eval_surrogate(net, xi, z, Phi, ubar, ut, h, decode=False, bf16=True)
     phi, q, gq = (t.cpu().numpy() for t in (phi, q, gq))

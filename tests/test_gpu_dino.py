@@ -70,12 +70,11 @@ def setup():
 
 def test_kl_projection(setup):
     D, n, N = setup["D"], N_GRID, 40
-    m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
-    setup["P"].ouu_sample_fields(SEED_SAA, 0, N, m)
+    mf = field.sample_fields(SEED_SAA, 0, N, n).reshape(N, -1)   # the oracle's draws on both sides
+    m = torch.tensor(mf.reshape(N, n, n), device="cuda")
     xi = torch.empty(N, RM, dtype=torch.float32, device="cuda")
     D.ouu_dino_project_fields(m, N, xi)
     Wkl, order = dino.kl_projection_matrix(n, RM)
-    mf = m.cpu().numpy().reshape(N, -1)
     x64 = dino.project_fields(mf, Wkl)
     xbf = dino.project_fields(mf, Wkl, bf16=True)
     xi = xi.cpu().numpy()
@@ -88,8 +87,8 @@ def test_kl_projection(setup):
 
 def test_eval_parity(setup):
     D, n, N = setup["D"], N_GRID, 40
-    m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
-    setup["P"].ouu_sample_fields(SEED_SAA, 0, N, m)
+    mf = field.sample_fields(SEED_SAA, 0, N, n).reshape(N, -1)   # the oracle's draws on both sides
+    m = torch.tensor(mf.reshape(N, n, n), device="cuda")
     z = controls(SEED_EVAL_Z, 1, DZ)[0]
     phi = torch.empty(N, RU, dtype=torch.float32, device="cuda")
     jphi = torch.empty(N, DZ, RU, dtype=torch.float32, device="cuda")
@@ -97,7 +96,6 @@ def test_eval_parity(setup):
     gq = torch.empty(N, DZ, dtype=torch.float64, device="cuda")
     D.ouu_dino_eval(m, N, z, phi, jphi, q, gq)
     Wkl, _ = dino.kl_projection_matrix(n, RM)
-    mf = m.cpu().numpy().reshape(N, -1)
     ut_int = setup["ut"][1:-1, 1:-1].ravel()
     h = 1.0 / (n - 1)
     Q64, g64, p64, J64 = dino.eval_surrogate(setup["net"], dino.project_fields(mf, Wkl), z, setup["Phi"],
@@ -224,14 +222,14 @@ def test_dino_risk_path(setup):
     from paper_2305_20053_gb300 import capi
     from oracle import risk
     D, P, n, N = setup["D"], setup["P"], N_GRID, 40
-    m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
-    P.ouu_sample_fields(SEED_SAA, 0, N, m)
+    mf = field.sample_fields(SEED_SAA, 0, N, n).reshape(N, -1)   # the oracle's draws on both sides
+    m = torch.tensor(mf.reshape(N, n, n), device="cuda")
     z = controls(SEED_EVAL_Z, 1, DZ)[0]
     risks = [capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0),
              capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.9, eps=1e-4, t_optimal=1)]
     val, grad, gt, t, _ = P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)
     Wkl, _ = dino.kl_projection_matrix(n, RM)
-    xbf = dino.project_fields(m.cpu().numpy().reshape(N, -1), Wkl, bf16=True)
+    xbf = dino.project_fields(mf, Wkl, bf16=True)
     ut_int = setup["ut"][1:-1, 1:-1].ravel()
     Q, gQ, _, _ = dino.eval_surrogate(setup["net"], xbf, z, setup["Phi"], setup["ubar"], ut_int, 1.0 / (n - 1),
                                       decode=False, bf16=True)

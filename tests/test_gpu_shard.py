@@ -36,21 +36,22 @@ def _risks():
             capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0)]
 
 
-def _emulate(blocks, backend, dino, m, z, risks):
-    """Phases of every block in turn on its own handle; returns the merged (risk, grad, grad_t, t)."""
+def _emulate(blocks, backend, dinos, m, z, risks):
+    """Phases of every block in turn on its own problem handle and network (dinos[k], as each
+    rank holds its own); returns the merged (risk, grad, grad_t, t)."""
     from paper_2305_20053_gb300 import capi
     n, L = m.shape[1], int(round(np.sqrt(len(z))))
     handles, qs, first = [], [], 0
-    for cnt in blocks:
+    for k, cnt in enumerate(blocks):
         P = capi.Problem(n=n, lattice_L=L, max_samples=cnt)
         q = torch.empty(cnt, dtype=torch.float64, device="cuda")
-        P.ouu_shard_qoi(backend, dino, m[first:first + cnt], cnt, z, q)
-        handles.append((P, first))
+        P.ouu_shard_qoi(backend, dinos[k], m[first:first + cnt], cnt, z, q)
+        handles.append((P, first, dinos[k]))
         qs.append(q)
         first += cnt
     q_all = torch.cat(qs)
-    outs = [P.ouu_shard_risk_partial(dino, q_all, first, f, risks) for P, f in handles]
-    for P, _ in handles:
+    outs = [P.ouu_shard_risk_partial(d, q_all, first, f, risks) for P, f, d in handles]
+    for P, _, _ in handles:
         P.close()
     for o in outs[1:]:   # values, d rho / dt and t are computed from all QoIs on every rank
         np.testing.assert_array_equal(o[0], outs[0][0])
@@ -65,7 +66,7 @@ def test_plain_path_two_blocks():
     m = torch.tensor(ms, device="cuda")
     z = controls(SEED_EVAL_Z, 1, L * L)[0]
     risks = _risks()
-    rho, g, gt, t = _emulate([30, 18], capi.BACKEND_PDE, None, m, z, risks)
+    rho, g, gt, t = _emulate([30, 18], capi.BACKEND_PDE, [None, None], m, z, risks)
     P = capi.Problem(n=n, lattice_L=L, max_samples=N)
     v0, g0, gt0, t0, _ = P.ouu_risk_and_grad(capi.BACKEND_PDE, None, m, N, risks, z)
     np.testing.assert_allclose(rho, v0, rtol=1e-12)
@@ -97,25 +98,39 @@ def test_dino_two_blocks():
     dz, h = L * L, 1.0 / (n - 1)
     Ws, bs = glorot_uniform_mlp([RM + dz, W, W, W, RU], seed=301)
     bs = [0.1 * random_state_like(302 + l, b.shape) for l, b in enumerate(bs)]
-    D = capi.Dino(n=n, lattice_L=L, r_m=RM, r_u=RU, width=W, max_batch=64, max_eval=N)
-    D.ouu_dino_set_params(capi.flatten_params(Ws, bs))
-    D.ouu_dino_set_output_scale(np.linspace(0.5, 0.1, RU).astype(np.float32))
     Qm, _ = np.linalg.qr(random_state_like(307, ((n - 2) ** 2, RU)))
     phi = np.zeros((RU, n, n))
     phi[:, 1:-1, 1:-1] = (Qm / h).T.reshape(RU, n - 2, n - 2)
     ub = np.zeros((n, n))
     ub[1:-1, 1:-1] = 0.05 * random_state_like(308, (n - 2, n - 2))
-    D.ouu_dino_set_bases(torch.tensor(phi, device="cuda"), torch.tensor(ub, device="cuda"))
+    nets = []
+    for _ in range(3):   # one per emulated rank, and one for the whole set
+        D = capi.Dino(n=n, lattice_L=L, r_m=RM, r_u=RU, width=W, max_batch=64, max_eval=N)
+        D.ouu_dino_set_params(capi.flatten_params(Ws, bs))
+        D.ouu_dino_set_output_scale(np.linspace(0.5, 0.1, RU).astype(np.float32))
+        D.ouu_dino_set_bases(torch.tensor(phi, device="cuda"), torch.tensor(ub, device="cuda"))
+        nets.append(D)
     m = torch.tensor(field.sample_fields(SEED_SAA, 0, N, n), device="cuda")
     z = controls(SEED_EVAL_Z, 1, dz)[0]
     risks = _risks()
-    rho, g, gt, t = _emulate([128, 172], capi.BACKEND_DINO, D, m, z, risks)
+    rho, g, gt, t = _emulate([128, 172], capi.BACKEND_DINO, nets[:2], m, z, risks)
+    D = nets[2]
     P = capi.Problem(n=n, lattice_L=L, max_samples=N)
     v0, g0, _, t0, _ = P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)
     np.testing.assert_allclose(rho, v0, rtol=1e-6)
     assert rel(g[0], g0[0]) <= 1e-5 and rel(g[1], g0[1]) <= 1e-5
+    # a network that evaluated other samples between the phases is refused
+    q = torch.empty(128, dtype=torch.float64, device="cuda")
+    P1 = capi.Problem(n=n, lattice_L=L, max_samples=128)
+    P1.ouu_shard_qoi(capi.BACKEND_DINO, D, m[:128], 128, z, q)
+    P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)
+    with pytest.raises(capi.OuuError) as e:
+        P1.ouu_shard_risk_partial(D, q, 128, 0, risks)
+    assert e.value.status == 6
+    P1.close()
     P.close()
-    D.close()
+    for D in nets:
+        D.close()
 
 
 def test_phase_order_and_block_checks():
