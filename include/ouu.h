@@ -322,12 +322,17 @@ ouu_status ouu_dino_load(ouu_dino_t d, const char* path);
 ouu_status ouu_dino_project_fields(ouu_dino_t d, const double* m_dev, int n_samples, float* xi_dev);
 /* Output targets: y_dev [n][r_u] FP32 = Phi^T M (u_i - ubar) (FP32). */
 ouu_status ouu_dino_project_states(ouu_dino_t d, const double* u_dev, int n_samples, float* y_dev);
-/* Jacobian targets (Sec. 3.4, implicit function theorem, forward route since
- * d_Z < r_u): jy_dev [n][d_Z][r_u] FP32, jy[i][j] = Phi^T M J(u_i)^-1 g_j, by d_Z
- * linearised solves per sample sharing one operator set-up (MG-PCG, FP32,
- * relative residual cg_rtol of `p`).  u_dev: states of (m_dev, z_i). */
+/* Jacobian targets (Sec. 3.4, implicit function theorem): jy_dev [n][d_Z][r_u] FP32,
+ * jy[i][j] = Phi^T M J(u_i)^-1 g_j, by min(d_Z, r_u) linearised solves per sample sharing
+ * one operator set-up (MG-PCG, FP32, relative residual cg_rtol of `p`): the forward route
+ * solves J x = g_j for each control j and projects on the POD modes; the adjoint route
+ * (d_Z > r_u) solves J lam_r = M Phi_r for each mode r (J is symmetric) and takes
+ * g_j . lam_r.  u_dev: states of (m_dev, z_i). */
 ouu_status ouu_dino_jacobian_data(ouu_problem_t p, ouu_dino_t d, const double* m_dev, const double* u_dev,
                                   int n_samples, float* jy_dev);
+/* Route of ouu_dino_jacobian_data: 0 (default) the one with fewer solves, 1 forward, 2 adjoint.
+ * Errors: INVALID_ARG for another value. */
+ouu_status ouu_dino_set_jacobian_route(ouu_dino_t d, int route);
 
 /* One Adam step on the minibatch idx_dev[0..batch-1] (device int32 indices into
  * the data arrays): xi_dev [*][r_m], z_dev [*][d_Z], y_dev [*][r_u],

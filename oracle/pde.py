@@ -209,3 +209,13 @@ def solve_batch(ms, z, G, u_t, prob: Problem, with_adjoint=True, z_per_sample=Fa
 def state_jacobian_columns(chol, G_int, n):
     """du/dz = J^{-1} G (the linearised solves of Sec. 3.4, forward route), (d, d_z)."""
     return cho_solve_banded((chol, False), G_int)
+
+
+def projected_jacobian(chol, G_int, Phi, h, route="forward"):
+    """Y = Phi^T M J^{-1} G (M = h^2 I), the reduced control Jacobian of Sec. 3.4, (r_u, d_z).
+    Forward route: the d_z solves J X = G, then Phi^T M X.  Adjoint route: the r_u solves
+    J Lam = M Phi (J symmetric), then Lam^T G."""
+    if route == "forward":
+        return h * h * (Phi.T @ cho_solve_banded((chol, False), G_int))
+    lam = cho_solve_banded((chol, False), h * h * Phi)
+    return lam.T @ G_int

@@ -107,6 +107,7 @@ SIGNATURES = {
     "ouu_dino_project_fields": (_i, [_vp, _vp, _i, _vp]),
     "ouu_dino_project_states": (_i, [_vp, _vp, _i, _vp]),
     "ouu_dino_jacobian_data": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "ouu_dino_set_jacobian_route": (_i, [_vp, _i]),
     "ouu_dino_train_step": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, ctypes.c_float, _dp]),
     "ouu_dino_loss_grad": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(ctypes.c_float), _dp]),
     "ouu_dino_eval": (_i, [_vp, _vp, _i, _dp, _vp, _vp, _vp, _vp, _vp]),
@@ -500,6 +501,10 @@ class Dino:
         import torch
         check(load().ouu_dino_project_states(self.handle, dev_ptr(u_dev, torch.float64), n,
                                              dev_ptr(y_dev, torch.float32)))
+
+    def ouu_dino_set_jacobian_route(self, route):
+        """0: the route with fewer solves (default), 1: forward, 2: adjoint."""
+        check(load().ouu_dino_set_jacobian_route(self.handle, route))
 
     def ouu_dino_jacobian_data(self, problem, m_dev, u_dev, n, jy_dev):
         import torch

@@ -708,8 +708,17 @@ extern "C" ouu_status ouu_dino_jacobian_data(ouu_problem_t p, ouu_dino_t d, cons
   a.m = m_dev;
   a.u = const_cast<double*>(u_dev);
   OUU_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, 4, p->stream));
-  launch_pde_jacobian_data(a, solver_grid(p, n_samples), d->d_phi, d->ru, jy_dev, p->stream);
+  // Sec. 3.4: the forward route takes d_Z linearised solves per sample, the adjoint route r_u
+  const int route = d->jac_route == 1 ? 0 : d->jac_route == 2 ? 1 : (d->dz <= d->ru ? 0 : 1);
+  launch_pde_jacobian_data(a, solver_grid(p, n_samples), d->d_phi, d->ru, jy_dev, route, p->stream);
   OUU_CUDA_TRY(cudaGetLastError());
   OUU_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return OUU_OK;
+}
+
+extern "C" ouu_status ouu_dino_set_jacobian_route(ouu_dino_t d, int route) {
+  OUU_CHECK_ARG(d != nullptr, "null argument");
+  OUU_CHECK_ARG(route >= 0 && route <= 2, "route: 0 the cheaper, 1 forward, 2 adjoint");
+  d->jac_route = route;
   return OUU_OK;
 }

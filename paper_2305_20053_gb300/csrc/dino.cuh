@@ -82,6 +82,7 @@ struct ouu_dino {
                                    // clusters (mlp_cluster.cu); 1 and 2 when the sizes fit
   bool capturing = false;
   uint64_t eval_count = 0;         // evaluations so far (a pending ouu_shard_qoi names the one it ran)
+  int jac_route = 0;               // Jacobian data: 0 the cheaper of the two, 1 forward, 2 adjoint
   // held-out check against the plain path (ouu_dino_validate): passed for the problem with this
   // serial; cleared whenever parameters, bases or output scale change
   int val_ok = 0;
@@ -127,4 +128,6 @@ ouu_status dino_install_bases(ouu_dino* d);
 ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W, int ldw, int rm, const float* bias,
                           float* xi, int* err, int* ctr, int num_sms, cudaStream_t s);
 
-void launch_pde_jacobian_data(const PdeArgs& a, int nslots, const float* phi, int ru, float* jy, cudaStream_t s);
+// route 0: forward (d_Z solves per sample), 1: adjoint (r_u solves per sample).
+void launch_pde_jacobian_data(const PdeArgs& a, int nslots, const float* phi, int ru, float* jy, int route,
+                              cudaStream_t s);

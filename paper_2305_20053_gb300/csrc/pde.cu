@@ -317,8 +317,13 @@ void launch_reduce_slots_and_gradient(const char* slots, const SlotLayout& lay, 
 // ------------------------------------------------------------------ Jacobian data (Sec. 3.4)
 // For each sample: one operator set-up J(u_i), then d_Z forward linearised solves
 // J w_j = g_j (MG-PCG, FP32) and their projections jy[i][j][r] = h^2 Phi_r . w_j.
+// Projected control Jacobians (Sec. 3.4): jy[i][j][r] = h^2 Phi_r . J(u_i)^-1 g_j.  Forward
+// route (route 0): one linearised solve per control, J x = g_j, then the r_u projections.
+// Adjoint route (route 1): one solve per POD mode, J lam_r = h^2 Phi_r (J is symmetric), then
+// jy[i][j][r] = g_j . lam_r by the separable sources: t[jy][ix] = sum_iy gy[jy][iy] lam[iy][ix],
+// g_j . lam = gscale sum_ix gx[jx][ix] t[jy][ix].  min(d_Z, r_u) solves per sample either way.
 __global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1)
-    k_pde_jacobian_data(PdeArgs a, const float* __restrict__ phi, int ru, float* __restrict__ jy) {
+    k_pde_jacobian_data(PdeArgs a, const float* __restrict__ phi, int ru, float* __restrict__ jy, int route) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[40];
   __shared__ int s_idx;
@@ -343,7 +348,39 @@ __global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1)
     setup_coarse_coeffs(c, H);
     setup_jacobian(c, H, a.rr, a.u + (int64_t)i * nn);
     int cg_total = 0;
-    for (int j = 0; j < dz; ++j) {
+    if (route == 1) {
+      float* t = (float*)(slot + a.lay.tmp);   // [L][n] partial contractions
+      for (int r = 0; r < ru; ++r) {
+        const float* pr = phi + (int64_t)r * nn;
+        double acc = 0.0;
+        OUU_FOR_INTERIOR(c, n, iy, ix) {
+          const float v = h2 * pr[iy * n + ix];
+          H.lev[0].b[iy * n + ix] = v;
+          acc = fma((double)v, (double)v, acc);
+        }
+        const double bnorm = sqrt(c.sum_d(acc));
+        CgResult cg = pcg_solve(c, H, x, p, q, bnorm, a.cg_rtol, a.cg_maxit);
+        cg_total += cg.iters;
+        c.sync();
+        for (int jyy = warp; jyy < L; jyy += nwarps)
+          for (int ix = lane; ix < n; ix += 32) {
+            float sum = 0.f;
+            for (int iy = 1; iy < n - 1; ++iy) sum = fmaf((float)a.gy[jyy * n + iy], x[iy * n + ix], sum);
+            t[jyy * n + ix] = sum;
+          }
+        c.sync();
+        const float sc = (float)(a.gscale * cg.scale);
+        for (int j = warp; j < dz; j += nwarps) {
+          const int jx = j % L, jyy = j / L;
+          float sum = 0.f;
+          for (int ix = lane; ix < n; ix += 32) sum = fmaf((float)a.gx[jx * n + ix], t[jyy * n + ix], sum);
+          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          if (lane == 0) jy[((int64_t)i * dz + j) * ru + r] = sc * sum;
+        }
+        c.sync();
+      }
+    }
+    for (int j = 0; j < (route == 1 ? 0 : dz); ++j) {
       const int jx = j % L, jyy = j / L;
       float acc = 0.f;
       OUU_FOR_INTERIOR(c, n, iy, ix) {
@@ -369,7 +406,8 @@ __global__ void __launch_bounds__(OUU_SOLVER_THREADS, 1)
   }
 }
 
-void launch_pde_jacobian_data(const PdeArgs& a, int nslots, const float* phi, int ru, float* jy, cudaStream_t s) {
+void launch_pde_jacobian_data(const PdeArgs& a, int nslots, const float* phi, int ru, float* jy, int route,
+                              cudaStream_t s) {
   set_smem((const void*)k_pde_jacobian_data, a.lay.smem_bytes);
-  k_pde_jacobian_data<<<nslots, OUU_SOLVER_THREADS, (size_t)a.lay.smem_bytes, s>>>(a, phi, ru, jy);
+  k_pde_jacobian_data<<<nslots, OUU_SOLVER_THREADS, (size_t)a.lay.smem_bytes, s>>>(a, phi, ru, jy, route);
 }

@@ -184,20 +184,21 @@ __device__ void mg_vcycle(const C& c, Hierarchy& H) {
 }
 
 // ------------------------------------------------------------------ CG on level 0
-// q = J p and returns (p, q).
+// q = J p and returns (p, q).  Inner products of the CG iteration are FP64 sums of the
+// FP32 entries' products (a product of two FP32 numbers is exact in FP64).
 template <class C>
 __device__ double op_apply_dot(const C& c, const MgLevel& L, const float* p, float* q) {
   const int n = L.n;
   const float ih2 = L.inv_h2;
-  float acc = 0.f;
+  double acc = 0.0;
   OUU_FOR_INTERIOR(c, n, iy, ix) {
     const int k = iy * n + ix;
     const float v = L.D[k] * p[k] - ih2 * (L.kx[k] * p[k + 1] + L.kx[k - 1] * p[k - 1] +
                                            L.ky[k] * p[k + n] + L.ky[k - n] * p[k - n]);
     q[k] = v;
-    acc += p[k] * v;
+    acc = fma((double)p[k], (double)v, acc);
   }
-  return c.sum_f(acc);
+  return c.sum_d(acc);
 }
 
 struct CgResult {
@@ -208,8 +209,8 @@ struct CgResult {
 
 // Solves J x = b for x (x overwritten) with the V-cycle as preconditioner.  On entry
 // H.lev[0].b holds b (it becomes the CG residual); H.lev[0].x and H.lev[0].r are the
-// preconditioner's output and scratch; p, q are work vectors.  FP32 vectors, sums
-// accumulated per member in FP32 and across members in FP64.
+// preconditioner's output and scratch; p, q are work vectors.  FP32 vectors; the inner
+// products are accumulated in FP64 (per member and across members).
 template <class C>
 __device__ CgResult pcg_solve(const C& c, Hierarchy& H, float* x, float* p, float* q,
                               double bnorm, double rtol, int maxit) {
@@ -234,37 +235,37 @@ __device__ CgResult pcg_solve(const C& c, Hierarchy& H, float* x, float* p, floa
   res.scale = bnorm;
   bnorm = 1.0;
   mg_vcycle(c, H);
-  float acc = 0.f;
+  double acc = 0.0;
   OUU_FOR_INTERIOR(c, n, iy, ix) {
     const int k = iy * n + ix;
     p[k] = z[k];
-    acc += r[k] * z[k];
+    acc = fma((double)r[k], (double)z[k], acc);
   }
-  double rz = c.sum_f(acc);
+  double rz = c.sum_d(acc);
   for (int it = 1; it <= maxit; ++it) {
     const double pq = op_apply_dot(c, L, p, q);
     if (!(pq > 0.0)) break;   // breakdown (exact solution reached, or not SPD): keep x
     const double alpha = rz / pq;
     const float af = (float)alpha;
-    float rr = 0.f;
+    double rr = 0.0;
     OUU_FOR_INTERIOR(c, n, iy, ix) {
       const int k = iy * n + ix;
       x[k] += af * p[k];
       const float rv = r[k] - af * q[k];
       r[k] = rv;
-      rr += rv * rv;
+      rr = fma((double)rv, (double)rv, rr);
     }
-    const double rnorm = sqrt(c.sum_f(rr));
+    const double rnorm = sqrt(c.sum_d(rr));
     res.iters = it;
     res.rel = rnorm / bnorm;
     if (!(res.rel > rtol) || it == maxit) break;   // also stops on NaN
     mg_vcycle(c, H);
-    acc = 0.f;
+    acc = 0.0;
     OUU_FOR_INTERIOR(c, n, iy, ix) {
       const int k = iy * n + ix;
-      acc += r[k] * z[k];
+      acc = fma((double)r[k], (double)z[k], acc);
     }
-    const double rz_new = c.sum_f(acc);
+    const double rz_new = c.sum_d(acc);
     const float beta = (float)(rz_new / rz);
     rz = rz_new;
     OUU_FOR_INTERIOR(c, n, iy, ix) {

@@ -304,3 +304,29 @@ def test_decode_reconstructs_states_in_the_basis_span():
     q = dino.decoded_qoi(u, ut, h)
     for i in range(3):
         assert q[i] == pytest.approx(0.5 * h * h * sum((u[i, k] - ut[k]) ** 2 for k in range(d)), rel=1e-14)
+
+
+def test_projected_jacobian_routes_agree():
+    """Sec. 3.4: Phi^T M J^-1 G by d_z forward solves equals (J^-1 M Phi)^T G by r_u adjoint
+    solves (J symmetric), and both equal the projection of finite differences of the state."""
+    n = 13
+    prob = pde.Problem(n=n, L=2)
+    G = field.control_sources(n, prob.L, prob.width)
+    m = field.sample_fields(3, 5, 1, n)[0]
+    z = controls(4, 1, prob.d_z)[0]
+    kx, ky = pde.face_coefficients(m)
+    u, chol = pde.newton_solve(kx, ky, (G @ z).reshape(n, n), prob.r, prob.h)
+    G_int = pde.interior_rows(G, n)
+    rng = np.random.default_rng(2)
+    Phi = rng.standard_normal(((n - 2) ** 2, 6))
+    Yf = pde.projected_jacobian(chol, G_int, Phi, prob.h, "forward")
+    Ya = pde.projected_jacobian(chol, G_int, Phi, prob.h, "adjoint")
+    np.testing.assert_allclose(Ya, Yf, rtol=1e-11, atol=1e-13 * np.abs(Yf).max())
+    step = 1e-5
+    for k in range(prob.d_z):
+        e = np.zeros(prob.d_z)
+        e[k] = step
+        up = pde.newton_solve(kx, ky, (G @ (z + e)).reshape(n, n), prob.r, prob.h)[0]
+        um = pde.newton_solve(kx, ky, (G @ (z - e)).reshape(n, n), prob.r, prob.h)[0]
+        fd = ((up - um) / (2 * step))[1:-1, 1:-1].ravel()
+        np.testing.assert_allclose(Yf[:, k], prob.h ** 2 * Phi.T @ fd, rtol=1e-6, atol=1e-10)
