@@ -68,6 +68,11 @@ def parse():
                     help="the uneven batch: 64 problems (grids 65/129/257, N 256-8192 log-uniform, d_Z 25-400), "
                          "half MR-DINO where a network for (n, d_Z) exists, one CUDA graph; per-problem and "
                          "aggregate evals/s")
+    ap.add_argument("--config4", action="store_true",
+                    help="the 257 x 257 workload: network retrained on 257 x 257 data, MR-DINO SAA over "
+                         "N = 16384 fields, error over 256 held-out fields at 5 controls")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the training-recipe measurement (1024 samples, 200 epochs, batch 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clocks-log", default=None, help="file for the nvidia-smi clock samples of the timed region")
@@ -574,6 +579,7 @@ def run_ours(args):
         workload = f"saa-risk-grad mr-dino {n}x{n} N={N} d_z={dz}"
         dtype = "bf16"
         ms_step = ms / args.steps
+        config3 = config3_training(P, n, L) if (rank == 0 and world == 1 and not args.no_config3) else None
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             rate, cores, walls = cpu_oracle_dino_rate(steps=2, warmup=1)
@@ -596,6 +602,7 @@ def run_ours(args):
                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "peak_source": f"{src} (burst)",
                     "note": "per-CTA solver working sets are L2-resident; bytes as streamed by each executed pass"}
         launches = 5 * args.steps
+        config3 = None
         workload = f"saa-risk-grad pde {n}x{n} N={N} d_z={dz}"
         dtype = "f64"
         e2e, cpu = None, None
@@ -633,7 +640,7 @@ def run_ours(args):
                                         2: "4-CTA clusters"}[net_mode] if use_dino else None},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "pde": pde_info, "speedup_vs_pde": value / pde_rate if use_dino else 1.0,
-            "accuracy": acc, "phases_ms": ph,
+            "accuracy": acc, "phases_ms": ph, "training_config": config3,
         }
         print(json.dumps(line), flush=True)
     if D is not None:
@@ -709,9 +716,120 @@ def run_batch(args):
     B.close()
 
 
+def config3_training(P, n, L):
+    """The training recipe of the 129 x 129 training configuration: 1024 PDE-generated samples,
+    r_M = r_U = 200, widths 300-400-400-400-200, batch 256, 200 epochs (the rate 1e-3, then
+    2.5e-4 from epoch 100), timed by phase; steps/s of the library's train step (forward,
+    backward through the Jacobian loss, Adam) and the held-out reduced state / Jacobian errors."""
+    import torch
+    from paper_2305_20053_gb300 import train as T
+    D = T.make_dino(n, L, r=R_M, width=WIDTH, max_batch=256, max_eval=256)
+    T.init_params(D)
+    data = T.generate_training_data(P, D, 1024)
+    T.train(D, data, epochs=2, batch=256)          # warm-up (kernel loading, tuner-free shapes)
+    T.init_params(D)
+    secs, losses = T.train(D, data, epochs=200, batch=256, log_every=100)
+    steps = 200 * (1024 // 256)
+    es, ej = T.heldout_errors(P, D, n_hold=64)
+    torch.cuda.synchronize()
+    out = {"recipe": "1024 samples, r_m = r_u = 200, 300-400-400-400-200 GELU, batch 256, 200 epochs, "
+                     "lr 1e-3 then 2.5e-4 from epoch 100",
+           "data_s": {k: round(v, 3) for k, v in data.times.items()}, "train_s": secs, "steps": steps,
+           "steps_per_s": steps / secs, "time_to_200_epochs_s": secs,
+           "final_loss": losses[-1][1] if losses else None,
+           "heldout_rel_state": es, "heldout_rel_jacobian": ej, "heldout_pairs": 64}
+    D.close()
+    return out
+
+
+def run_config4(args):
+    """257 x 257 fields, N = 16384, d_Z = 100: the network retrained on 257 x 257 data with the
+    benchmark's recipe, MR-DINO SAA risk + gradient timed (one call per step, graph replay),
+    the plain path timed beside it, and the error against the plain path over 256 held-out
+    fields at 5 controls (the largest relative risk and gradient errors)."""
+    import torch
+    from paper_2305_20053_gb300 import capi
+    from paper_2305_20053_gb300 import train as T
+    from synthetic_inputs import SEED_EVAL_Z, SEED_HELDOUT, SEED_SAA, controls
+    torch.cuda.set_device(0)
+    capi.load()
+    n, L, N = 257, L_LAT, 16384
+    dz = L * L
+    stream = torch.cuda.current_stream()
+    P = capi.Problem(n=n, lattice_L=L, max_samples=max(N, args.train))
+    D = T.make_dino(n, L, r=R_M, width=WIDTH, max_batch=256, max_eval=N)
+    T.init_params(D)
+    data = T.generate_training_data(P, D, args.train)
+    train_s, losses = T.train(D, data, epochs=args.epochs, batch=256, lr_final=args.lr_final or None)
+    times = {k: round(v, 3) for k, v in data.times.items()}
+    del data
+    mh = torch.empty(256, n, n, dtype=torch.float64, device="cuda")
+    P.ouu_sample_fields(SEED_HELDOUT, 0, 256, mh)
+    risks = [capi.risk_desc(capi.RISK_CVAR_SMOOTH, beta=0.95, eps=1e-4, t_optimal=1),
+             capi.risk_desc(capi.RISK_MEAN_VAR, kappa=1.0)]
+    zs = controls(SEED_EVAL_Z, 5, dz)
+    er, eg, ok = D.ouu_dino_validate(P, mh, 256, risks, zs, risk_tol=0.01, grad_tol=0.05)
+    del mh
+    m = torch.empty(N, n, n, dtype=torch.float64, device="cuda")
+    for f in range(0, N, 8192):
+        P.ouu_sample_fields(SEED_SAA, f, min(8192, N - f), m[f:])
+    z = zs[0]
+    backend = capi.BACKEND_AUTO if ok else capi.BACKEND_DINO
+
+    def step():
+        return P.ouu_risk_and_grad(backend, D, m, N, risks, z)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0, args.clocks_log)
+    clocks.start()
+    ms, _ = time_steps(step, args.steps, stream)
+    clk = clocks.stop()
+    pde_step = lambda: P.ouu_risk_and_grad(capi.BACKEND_PDE, None, m, N, risks, z)   # noqa: E731
+    pde_step()
+    torch.cuda.synchronize()
+    pde_ms, _ = time_steps(pde_step, 2, stream, "pde_timed")
+    D.ouu_dino_set_graphs(0)
+    st = [P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)[4] for _ in range(3)][1:]
+    D.ouu_dino_set_graphs(1)
+    ms_proj = float(np.mean([x.ms_project for x in st]))
+    nnp = (n * n + 63) // 64 * 64
+    pbytes = N * n * n * 8 + R_M * nnp * 2 + N * R_M * 4
+    value = args.steps / (ms / 1000.0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"saa-risk-grad mr-dino {n}x{n} N={N} d_z={dz}", "n": n, "n_samples": N, "d_z": dz,
+                   "risks": ["cvar_smooth beta=0.95 eps=1e-4 t=t*", "mean+var kappa=1"],
+                   "backend": "auto (network after its held-out check)" if ok else "dino",
+                   "l2": "inputs larger than L2 (8.7 GB of FP64 fields per step)",
+                   "surrogate": {"train_pairs": args.train, "epochs": args.epochs, "construction_s": {
+                       **times, "train_s": round(train_s, 3)}, "final_loss": losses[-1][1] if losses else None}},
+        "accuracy": {"heldout_fields": 256, "controls": 5, "max_rel_risk": er, "max_rel_grad": eg,
+                     "gate_passed": bool(ok), "reference": "plain GPU path"},
+        "roofline": {"kernel": "k_kl_project", "bound": "hbm", "achieved": pbytes / (ms_proj / 1000.0) / 1e9,
+                     "peak": hbm, "unit": "GB/s", "frac": pbytes / (ms_proj / 1000.0) / 1e9 / hbm, "traffic": None,
+                     "algorithmic_bytes": pbytes},
+        "pde": {"evals_per_s": 2 / (pde_ms / 1000.0), "ms_per_eval": pde_ms / 2},
+        "speedup_vs_pde": value / (2 / (pde_ms / 1000.0)), "clocks": clk, "gpu_launches": 5 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    D.close()
+    P.close()
+
+
 def main():
     args = parse()
-    if args.batch:
+    if args.config4:
+        run_config4(args)
+    elif args.batch:
         run_batch(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -373,6 +373,7 @@ extern "C" ouu_status ouu_batch_run(ouu_batch_t b, const double* const* z_hosts,
       return OUU_ERR_CUDA;
     }
   }
+  for (int k : b->dino) ++b->items[k].it.dino->eval_count;   // their per-sample buffers are rewritten
   OUU_CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
   OUU_CUDA_TRY(cudaStreamSynchronize(b->stream));
   int worst = 0;

@@ -475,6 +475,7 @@ static ouu_status risk_and_grad_on(ouu_problem_t p, ouu_backend backend, ouu_din
   }
   if (backend == OUU_BACKEND_DINO) {
     cudaStream_t ds = dino->stream;
+    ++dino->eval_count;   // a graph replay, too, overwrites the network's per-sample buffers
     auto enqueue = [&]() -> ouu_status { return dino_enqueue_risk(p, dino, m_dev, n_samples, n_risks, z_host); };
     const bool replay = dino->use_graphs && dino->gexec && dino->gkey_p == p && dino->gkey_m == m_dev &&
                         dino->gkey_N == n_samples && dino->gkey_nr == n_risks;
