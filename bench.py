@@ -57,8 +57,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--backend", default="dino", choices=["dino", "pde"])
     ap.add_argument("--pde-steps", type=int, default=3)
-    ap.add_argument("--train", type=int, default=32768, help="training pairs for the surrogate")
-    ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--train", type=int, default=262144, help="training pairs for the surrogate")
+    ap.add_argument("--epochs", type=int, default=150)
     ap.add_argument("--network-mode", type=int, default=None, choices=[0, 1, 2],
                     help="evaluation network (default: the library's, 2): 0 per-layer GEMM kernels, "
                          "1 one kernel per tile, 2 4-CTA clusters")
@@ -412,7 +412,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     use_dino = args.backend == "dino"
     first, n_loc = split_samples(N, world)[rank]
-    P = capi.Problem(n=n, lattice_L=L, max_samples=max(n_loc, 256, args.train if use_dino else 0))
+    P = capi.Problem(n=n, lattice_L=L, max_samples=max(n_loc, 1024))
     m = torch.empty(n_loc, n, n, dtype=torch.float64, device=dev)
     P.ouu_sample_fields(SEED_SAA, first, n_loc, m)
     plan = shard.ShardedSAA(n_loc, dev) if world > 1 else None
@@ -444,7 +444,10 @@ def run_ours(args):
     if use_dino:
         D = T.make_dino(n, L, r=R_M, width=WIDTH, max_batch=256, max_eval=max(n_loc, 256))
         T.init_params(D)
-        data = T.generate_training_data(P, D, args.train)
+        Pt = capi.Problem(n=n, lattice_L=L, max_samples=args.train)   # training data only
+        data = T.generate_training_data(Pt, D, args.train)
+        Pt.close()
+        torch.cuda.empty_cache()
         lr_final = args.lr_final if args.lr_final > 0 else None
         train_s, losses = T.train(D, data, epochs=args.epochs, batch=256, log_every=max(1, args.epochs // 4),
                                   lr_final=lr_final)

@@ -47,22 +47,29 @@ static __device__ __forceinline__ void epi_quads(float* stage, const float* sbia
   const bool vec = ep.vec != 0;
   const float alpha = ep.alpha;
   if (MODE == EPI_DECODE) {
-    // consecutive threads on consecutive columns of a row (coalesced rows of any length or
-    // alignment); BN is a multiple of 32, so a warp's 32 elements share one row and its
-    // squared differences are summed by a warp reduction, then per row in shared memory
-    const int lane = threadIdx.x & 31;
-    for (int e = threadIdx.x; e < GEMM_BM * BN; e += GEMM_THREADS) {
-      const int tr = e / BN, cc = e - tr * BN, r = m0 + tr, c = n0 + cc;
-      float d = 0.f;
-      if (r < M && c < N) {
-        const float v = stage[tr * SROW + cc] + sadd[cc];
-        ep.out_f32[(size_t)r * ep.ld_f32 + c] = v;
-        d = v - sscale[cc];   // sscale holds col_ref in this mode
+    // whole rows per warp, lanes over consecutive columns (coalesced rows of any length or
+    // alignment); the row's squared differences summed per lane, then once per row by a warp
+    // reduction
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int tr = warp; tr < GEMM_BM; tr += GEMM_THREADS / 32) {
+      const int r = m0 + tr;
+      if (r >= M) break;
+      float* orow = ep.out_f32 + (size_t)r * ep.ld_f32;
+      const float* srow = stage + tr * SROW;
+      float sq = 0.f;
+#pragma unroll 4
+      for (int cc = lane; cc < BN; cc += 32) {
+        const int c = n0 + cc;
+        if (c < N) {
+          const float v = srow[cc] + sadd[cc];
+          orow[c] = v;
+          const float d = v - sscale[cc];   // sscale holds col_ref in this mode
+          sq = fmaf(d, d, sq);
+        }
       }
-      float sq = d * d;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      if (lane == 0 && r < M) atomicAdd(&rowsum[tr], sq);
+      if (lane == 0) rowsum[tr] = sq;
     }
     return;
   }
@@ -499,7 +506,6 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
     cudaEventCreate(&e1);
     for (int bn : {256, 208, 128, 112, 80, 64}) {
       if (ep.mode == EPI_QOI && bn < N) continue;
-      if (ep.mode == EPI_DECODE && bn % 32) continue;   // a warp's 32 columns must share a row
       if (launch_by_bn(bn, ta, B, ldb, M, N, K, e2, err, s, splits) != OUU_OK) continue;   // warm-up
       cudaEventRecord(e0, s);
       for (int r = 0; r < 3; ++r) launch_by_bn(bn, ta, B, ldb, M, N, K, e2, err, s, splits);
@@ -535,7 +541,6 @@ ouu_status ouu_gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B
   const long mt = (long)((M + GEMM_BM - 1) / GEMM_BM) * splits;
   for (int bn : cands) {
     if (ep.mode == EPI_QOI && bn < N) continue;   // whole rows in one tile
-    if (ep.mode == EPI_DECODE && bn % 32) continue;   // a warp's 32 columns must share a row
     const long tiles = mt * ((N + bn - 1) / bn);
     const long cost = ((tiles + sms - 1) / sms) * (bn + 64);
     if (cost < best_cost) {
