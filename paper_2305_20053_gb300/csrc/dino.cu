@@ -297,6 +297,21 @@ static ouu_status gemm(ouu_dino* d, const __nv_bfloat16* A, int lda, const __nv_
   return ouu_gemm_bf16(A, lda, B, ldb, M, N, K, ep, d->d_err, d->stream);
 }
 
+// out [M][N] (leading dimension N) = A B^T with K split over CTAs so that the few output tiles of
+// a weight gradient (M, N <= 400, K = batch x (1 + d_Z)) fill the GPU: the slices' FP32 partial
+// products are added atomically into the zeroed output.
+static ouu_status gemm_wgrad(ouu_dino* d, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
+                             int N, int K, float* out) {
+  const int tiles = ((M + 127) / 128) * ((N + 127) / 128), kb = (K + 63) / 64;
+  int splits = std::max(1, std::min(std::min(64, kb), d->num_sms / std::max(1, tiles)));
+  while (splits > 1 && (splits - 1) * ((kb + splits - 1) / splits) >= kb) --splits;   // no empty slice
+  EpiParams e = epi(EPI_LINEAR);
+  e.out_f32 = out;
+  e.ld_f32 = N;
+  if (splits > 1) OUU_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)M * N * 4, d->stream));
+  return ouu_gemm_bf16(A, lda, B, ldb, M, N, K, e, d->d_err, d->stream, splits);
+}
+
 extern "C" void ouu_default_dino_desc(ouu_dino_desc* d) {
   if (!d) return;
   d->n = 129;
@@ -784,10 +799,7 @@ static ouu_status loss_and_grad(ouu_dino* d, const float* xi, const float* z, co
   transpose_bf16(d->GO, rup, BR, ru, d->GOT, BR, d->stream);
   float* g = d->d_grad;
   {  // output layer: dW3 = GO^T [h3; hdot3], db3 = sum_b g_phi, GH = GO W3
-    EpiParams e = epi(EPI_LINEAR);
-    e.out_f32 = g + d->offW[3];
-    e.ld_f32 = wd;
-    DINO_TRY(gemm(d, d->GOT, BR, d->HST[3], BR, ru, wd, BR, e));
+    DINO_TRY(gemm_wgrad(d, d->GOT, BR, d->HST[3], BR, ru, wd, BR, g + d->offW[3]));
     k_colsum<<<grid_for(ru), 256, 0, d->stream>>>(d->d_gov, B, ru, ru, g + d->offb[3]);
     EpiParams h = epi(EPI_LINEAR);
     h.out_f32 = d->GH;
@@ -798,10 +810,7 @@ static ouu_status loss_and_grad(ouu_dino* d, const float* xi, const float* z, co
     k_bwd_layer<<<grid_for((int64_t)BR * wd), 256, 0, d->stream>>>(d->GH, d->A[l], d->AD[l], wdp, nullptr, 0, 0, dz,
                                                                    wd, B, d->GA, d->GAv);
     transpose_bf16(d->GA, wdp, BR, wd, d->GAT, BR, d->stream);
-    EpiParams e = epi(EPI_LINEAR);
-    e.out_f32 = g + d->offW[l - 1];
-    e.ld_f32 = wd;
-    DINO_TRY(gemm(d, d->GAT, BR, d->HST[l - 1], BR, wd, wd, BR, e));
+    DINO_TRY(gemm_wgrad(d, d->GAT, BR, d->HST[l - 1], BR, wd, wd, BR, g + d->offW[l - 1]));
     k_colsum<<<grid_for(wd), 256, 0, d->stream>>>(d->GAv, B, wd, wd, g + d->offb[l - 1]);
     EpiParams h = epi(EPI_LINEAR);
     h.out_f32 = d->GH;
