@@ -608,14 +608,14 @@ ouu_status dino_decode(ouu_dino* d, const float* phi, int ldphi, int N, float* u
   k_decode_coeffs<<<grid_for((int64_t)N * rup), 256, 0, d->stream>>>(phi, ldphi, N, d->ru, rup, d->d_dec_a);
   OUU_CUDA_TRY(cudaGetLastError());
   OUU_CUDA_TRY(cudaMemsetAsync(q, 0, (size_t)N * 8, d->stream));
-  EpiParams e = epi(EPI_DECODE);
+  EpiParams e = epi(EPI_DECODE);   // rows: the nn grid nodes; columns: the N samples
   e.out_f32 = u;
   e.ld_f32 = d->nn;
   e.col_add = d->d_ubarf;
   e.col_ref = d->d_utf;
   e.out_q = q;
   e.qconst = 0.5 * d->h * d->h;
-  return gemm(d, d->d_dec_a, K, d->d_dec_b, K, N, d->nn, K, e);
+  return gemm(d, d->d_dec_b, K, d->d_dec_a, K, d->nn, N, K, e);
 }
 
 static ouu_status check_err(ouu_dino* d);

@@ -117,10 +117,12 @@ static __device__ __forceinline__ void mlc_epi_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(MLC_EPI_WARPS * 32) : "memory");
 }
 
-// This thread's global writes ordered before later TMA (async-proxy) reads in other CTAs.
+// This thread's global writes ordered before later TMA (async-proxy) reads in the other CTAs
+// of the cluster: the proxy fence, then a release at cluster scope (every reader is in this
+// thread's cluster, and it acquires through the cluster-scope mbarrier arrival that follows).
 static __device__ __forceinline__ void mlc_publish() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
-  __threadfence();
+  asm volatile("fence.acq_rel.cluster;" ::: "memory");
 }
 
 static __device__ __forceinline__ void mlc_store_bf16x4(__nv_bfloat16* p, const float* v, int nv) {

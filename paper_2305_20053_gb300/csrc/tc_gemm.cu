@@ -1,13 +1,7 @@
-// tcgen05 + TMA BF16 GEMM with fused epilogues (see tc_gemm.cuh).
-//
-// CTA = 12 warps (384 threads), one 128 x BN output tile:
-//   warp 0 (one lane): TMA producer, 4- or 5-stage ring of 64-wide K blocks (SWIZZLE_128B)
-//   warp 1 (one lane): tcgen05.mma issuer (kind::f16, BF16 x BF16 -> FP32 in TMEM);
-//                      warp 1 also allocates / frees the tensor memory
-//   warps 2..5       : TMEM -> shared staging tile, one accumulator row (TMEM lane) per thread
-//   all 12 warps     : the fused epilogue over the staged tile, and the global stores
-// Every mbarrier wait is bounded (about 2 s of SM clock); on a timeout the CTA
-// drains its own TMA copies (bounded), frees its tensor memory and raises *err.
+// tcgen05 + TMA BF16 GEMM with fused epilogues (see tc_gemm.cuh): a persistent kernel, one CTA
+// per SM, each taking (row tile, column tile, K slice) units in turn; two tensor-memory
+// accumulators, so that the epilogue of one unit (read straight from tensor memory into
+// registers) overlaps the MMAs of the next (warp roles at k_gemm_bf16).
 #include <math.h>
 
 #include <algorithm>
@@ -28,225 +22,229 @@
 static __device__ __forceinline__ float gelu_f(float x) { return gelu_fwd(x); }
 static __device__ __forceinline__ float gelu_d1f(float x) { return gelu_d1(x); }
 
-// Pipeline depth: four stages; five for the wide tiles of long-K projections (one CTA per
-// SM) where five still fit in 227 KB of shared memory (BN = 208: 210 KB; BN = 256 would need 240).
+// Pipeline depth: as many 64-wide K stages as fit in about 200 KB of shared memory (the
+// epilogue reads the accumulator from tensor memory, so the ring holds nothing else).
 template <int BN>
 struct GemmStages {
-  static constexpr int value = (BN > 128 && 5 * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) <= 216 * 1024) ? 5 : 4;
+  static constexpr int per = GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2;
+  static constexpr int value = (200 * 1024 / per) > 8 ? 8 : (200 * 1024 / per);
 };
 
-// Epilogue B: one pass over the staged tile in quads of four consecutive columns,
-// consecutive threads on consecutive quads of a row (16-byte shared loads, 16-byte FP32
-// and 8-byte BF16 global stores when ep.vec).  One compact loop per mode keeps the code
-// that every CTA runs once small.  MODE 7 = split-K partial sums, added atomically.
-template <int BN, int MODE>
-static __device__ __forceinline__ void epi_quads(float* stage, const float* sbias, const float* sscale,
-                                                 const float* sadd, float* rowsum, int m0, int n0, int M, int N,
-                                                 const EpiParams& ep, bool keep) {
-  constexpr int SROW = BN + 4, QPR = BN / 4;
-  const bool vec = ep.vec != 0;
-  const float alpha = ep.alpha;
-  if (MODE == EPI_DECODE) {
-    // whole rows per warp, lanes over consecutive columns (coalesced rows of any length or
-    // alignment); the row's squared differences summed per lane, then once per row by a warp
-    // reduction
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int tr = warp; tr < GEMM_BM; tr += GEMM_THREADS / 32) {
-      const int r = m0 + tr;
-      if (r >= M) break;
-      float* orow = ep.out_f32 + (size_t)r * ep.ld_f32;
-      const float* srow = stage + tr * SROW;
-      float sq = 0.f;
-#pragma unroll 4
-      for (int cc = lane; cc < BN; cc += 32) {
-        const int c = n0 + cc;
-        if (c < N) {
-          const float v = srow[cc] + sadd[cc];
-          orow[c] = v;
-          const float d = v - sscale[cc];   // sscale holds col_ref in this mode
-          sq = fmaf(d, d, sq);
-        }
-      }
+// Tensor-memory columns of one accumulator buffer (a power of two >= BN); two buffers.
+template <int BN>
+struct GemmAcc {
+  static constexpr uint32_t cols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+};
+
+// Named barrier of the eight epilogue warps (warps 4..11).
+static __device__ __forceinline__ void gemm_epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Row-major stores of a warp's 16-column chunk (32 rows, one per lane, rows r0 + lane)
+// through the warp's shared tile (32 rows x 20 floats): after the transpose each store
+// instruction covers 8 rows x 16 consecutive columns, full 64-byte (FP32) or 32-byte (BF16)
+// segments, instead of 32 rows x one lane's part.  Warp-collective: every lane calls it;
+// rows >= M and columns >= c0 + nv are not written.  vec: 16-byte FP32 / 8-byte BF16 stores
+// are aligned (base and leading dimension).
+#define GEMM_TROW 20
+static __device__ __forceinline__ void store_rows_f32(float* tile, float* out, int ld, int r0, int M, int c0, int nv,
+                                                      const float* v, bool vec, bool accumulate) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      if (lane == 0) rowsum[tr] = sq;
-    }
-    return;
-  }
-  if (MODE == EPI_QOI) {
-    // whole rows per warp, lanes over quads, the row's quadratic by a warp reduction
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int tr = warp; tr < GEMM_BM; tr += GEMM_THREADS / 32) {
-      const int r = m0 + tr;
-      if (r >= M) break;
-      float sq = 0.f;
-      for (int qd = lane; qd < QPR; qd += 32) {
-        const int cc = 4 * qd, c = n0 + cc;
-        if (c >= N) break;
-        const int nv = min(4, N - c);
-        const float4 a4 = *reinterpret_cast<const float4*>(stage + tr * SROW + cc);
-        const float acc[4] = {a4.x, a4.y, a4.z, a4.w};
-        float y[4], o[4];
+  for (int k = 0; k < 16; k += 4)
+    *reinterpret_cast<float4*>(tile + lane * GEMM_TROW + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+  __syncwarp();
+  const int q = lane & 3;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          y[j] = (acc[j] + sbias[cc + j]) * sscale[cc + j];
-          const float v = j < nv ? y[j] + sadd[cc + j] : 0.f;
-          o[j] = v * sscale[cc + j];
-          sq += v * v;
+  for (int i = 0; i < 4; ++i) {
+    const int rr = 8 * i + (lane >> 2), row = r0 + rr;
+    const float4 w = *reinterpret_cast<const float4*>(tile + rr * GEMM_TROW + 4 * q);
+    if (row < M) {
+      float* p = out + (size_t)row * ld + c0 + 4 * q;
+      if (vec && 4 * q + 3 < nv) {
+        float4 x = w;
+        if (accumulate) {
+          const float4 o = *reinterpret_cast<const float4*>(p);
+          x.x += o.x, x.y += o.y, x.z += o.z, x.w += o.w;
         }
-        float* of = ep.out_f32 ? ep.out_f32 + (size_t)r * ep.ld_f32 + c : nullptr;
-        __nv_bfloat16* ob = ep.out_bf16 ? ep.out_bf16 + (size_t)r * ep.ld_bf16 + c : nullptr;
-        if (vec && nv == 4) {
-          if (of) *reinterpret_cast<float4*>(of) = make_float4(y[0], y[1], y[2], y[3]);
-          if (ob) {
-            const __nv_bfloat162 p0 = __floats2bfloat162_rn(o[0], o[1]), p1 = __floats2bfloat162_rn(o[2], o[3]);
-            *reinterpret_cast<uint2*>(ob) =
-                make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
-          }
-        } else {
-          for (int j = 0; j < nv; ++j) {
-            if (of) of[j] = y[j];
-            if (ob) ob[j] = __float2bfloat16(o[j]);
-          }
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      if (lane == 0) rowsum[tr] = sq;
-    }
-    return;
-  }
-#pragma unroll 2
-  for (int e = threadIdx.x; e < GEMM_BM * QPR; e += GEMM_THREADS) {
-    const int tr = e / QPR, cc = (e - tr * QPR) * 4, r = m0 + tr, c = n0 + cc;
-    if (r >= M || c >= N) continue;
-    const int nv = min(4, N - c);
-    const bool full = vec && nv == 4;
-    float* sp = stage + tr * SROW + cc;
-    const float4 a4 = *reinterpret_cast<const float4*>(sp);
-    const float acc[4] = {a4.x, a4.y, a4.z, a4.w};
-    float y[4], o[4];
-    if (MODE == EPI_DGELU_SCALE || MODE == EPI_SCALE) {
-      const float* ap = ep.aux + (size_t)(r / ep.aux_rdiv) * ep.ld_aux + c;
-      float x[4] = {0.f, 0.f, 0.f, 0.f};
-      if (full) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(ap));
-        x[0] = t.x, x[1] = t.y, x[2] = t.z, x[3] = t.w;
+        *reinterpret_cast<float4*>(p) = x;
       } else {
-        for (int j = 0; j < nv; ++j) x[j] = ap[j];
-      }
-      if (MODE == EPI_SCALE) {
+        const float e[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) o[j] = y[j] = acc[j] * x[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) o[j] = y[j] = acc[j] * gelu_d1f(x[j]);
-      }
-    } else if (MODE == EPI_GELU_D) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) gelu_and_d1(acc[j] + sbias[cc + j], o[j], y[j]);   // one exp for both
-    } else if (MODE == EPI_GELU) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        y[j] = acc[j] + sbias[cc + j];
-        o[j] = gelu_f(y[j]);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) o[j] = y[j] = (alpha * acc[j] + sbias[cc + j]) * sscale[cc + j];
-    }
-    float* of = ep.out_f32 ? ep.out_f32 + (size_t)r * ep.ld_f32 + c : nullptr;
-    if (MODE == 7) {
-      if (full) {
-        atomicAdd(reinterpret_cast<float4*>(of), make_float4(y[0], y[1], y[2], y[3]));
-      } else {
-        for (int j = 0; j < nv; ++j) atomicAdd(of + j, y[j]);
-      }
-      continue;
-    }
-    __nv_bfloat16* ob = ep.out_bf16 ? ep.out_bf16 + (size_t)r * ep.ld_bf16 + c : nullptr;
-    __nv_bfloat16* o2 = ep.out2_bf16 ? ep.out2_bf16 + (size_t)r * ep.ld2 + c : nullptr;
-    if (full) {
-      if (of) {
-        float4 v = make_float4(y[0], y[1], y[2], y[3]);
-        if (ep.accumulate) {
-          const float4 old = *reinterpret_cast<const float4*>(of);
-          v.x += old.x, v.y += old.y, v.z += old.z, v.w += old.w;
-        }
-        *reinterpret_cast<float4*>(of) = v;
-      }
-      if (ob) {
-        const __nv_bfloat162 p0 = __floats2bfloat162_rn(o[0], o[1]), p1 = __floats2bfloat162_rn(o[2], o[3]);
-        *reinterpret_cast<uint2*>(ob) =
-            make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
-      }
-      if (o2) {
-        const __nv_bfloat162 p0 = __floats2bfloat162_rn(acc[0], acc[1]), p1 = __floats2bfloat162_rn(acc[2], acc[3]);
-        *reinterpret_cast<uint2*>(o2) =
-            make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
-      }
-    } else {
-      for (int j = 0; j < nv; ++j) {
-        if (of) of[j] = ep.accumulate ? of[j] + y[j] : y[j];
-        if (ob) ob[j] = __float2bfloat16(o[j]);
-        if (o2) o2[j] = __float2bfloat16(acc[j]);
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j < nv) p[j] = accumulate ? p[j] + e[j] : e[j];
       }
     }
-    if (keep) *reinterpret_cast<float4*>(sp) = make_float4(o[0], o[1], o[2], o[3]);
   }
+  __syncwarp();
 }
 
+static __device__ __forceinline__ void store_rows_bf16(float* tile, __nv_bfloat16* out, int ld, int r0, int M, int c0,
+                                                       int nv, const float* v, bool vec) {
+  const int lane = threadIdx.x & 31;
+  uint32_t* t32 = reinterpret_cast<uint32_t*>(tile);
+#pragma unroll
+  for (int k = 0; k < 16; k += 2) {
+    const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[k], v[k + 1]);
+    t32[lane * GEMM_TROW + k / 2] = *reinterpret_cast<const uint32_t*>(&p2);
+  }
+  __syncwarp();
+  const int q = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = 8 * i + (lane >> 2), row = r0 + rr;
+    const uint2 w = *reinterpret_cast<const uint2*>(t32 + rr * GEMM_TROW + 2 * q);
+    if (row < M) {
+      __nv_bfloat16* p = out + (size_t)row * ld + c0 + 4 * q;
+      if (vec && 4 * q + 3 < nv) {
+        *reinterpret_cast<uint2*>(p) = w;
+      } else {
+        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&w);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j < nv) p[j] = e[j];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// The fused epilogue of one 16-column chunk of one accumulator row (row r, columns c0 ..
+// c0 + nv - 1), straight from the registers the tensor-memory load filled.  rowsum: the
+// row's running quadratic (EPI_QOI).  MODE 7: split-K partial sums, added
+// atomically (the bias only from the first K slice).
+template <int MODE>
+static __device__ __forceinline__ void epi_chunk(const float (&acc)[16], int r, int M, int c0, int nv, const EpiParams& ep,
+                                                 bool first_slice, float& rowsum, float* tile) {
+  // warp-collective (the row stores go through the warp's shared tile): every lane of the warp
+  // calls it, lanes of rows >= M with their values ignored
+  const int r0 = r - (int)(threadIdx.x & 31);
+  const bool live_row = r < M;
+  float y[16], o[16];
+  float cb[16], cs[16], ca[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {   // per-column constants (the same addresses in every lane: broadcast loads)
+    const bool in = j < nv;
+    cb[j] = (in && ep.bias && first_slice) ? __ldg(ep.bias + c0 + j) : 0.f;
+    cs[j] = (in && ep.col_scale) ? __ldg(ep.col_scale + c0 + j) : 1.f;
+    ca[j] = (in && ep.col_add) ? __ldg(ep.col_add + c0 + j) : 0.f;
+  }
+  if (MODE == EPI_DGELU_SCALE || MODE == EPI_SCALE) {
+    const float* ap = ep.aux + (size_t)((live_row ? r : r0) / ep.aux_rdiv) * ep.ld_aux + c0;
+    float x[16];
+    if (ep.vec && nv == 16) {
+#pragma unroll
+      for (int j = 0; j < 16; j += 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(ap + j));
+        x[j] = t.x, x[j + 1] = t.y, x[j + 2] = t.z, x[j + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x[j] = j < nv ? ap[j] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j] = y[j] = MODE == EPI_SCALE ? acc[j] * x[j] : acc[j] * gelu_d1f(x[j]);
+  } else if (MODE == EPI_GELU_D) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) gelu_and_d1(acc[j] + cb[j], o[j], y[j]);   // one exp for both
+  } else if (MODE == EPI_GELU) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      y[j] = acc[j] + cb[j];
+      o[j] = gelu_f(y[j]);
+    }
+  } else if (MODE == EPI_QOI) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      y[j] = (acc[j] + cb[j]) * cs[j];
+      const float v = j < nv ? y[j] + ca[j] : 0.f;
+      o[j] = v * cs[j];
+      if (live_row) rowsum = fmaf(v, v, rowsum);
+    }
+  } else {   // EPI_LINEAR and the split-K partial sums
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j] = y[j] = (ep.alpha * acc[j] + cb[j]) * cs[j];
+  }
+  if (MODE == 7) {
+    if (!live_row) return;
+    float* of = ep.out_f32 + (size_t)r * ep.ld_f32 + c0;
+    if (ep.vec && nv == 16) {
+#pragma unroll
+      for (int j = 0; j < 16; j += 4) atomicAdd(reinterpret_cast<float4*>(of + j), make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < nv) atomicAdd(of + j, y[j]);
+    }
+    return;
+  }
+  if (ep.out_f32) store_rows_f32(tile, ep.out_f32, ep.ld_f32, r0, M, c0, nv, y, ep.vec != 0, ep.accumulate != 0);
+  if (ep.out_bf16) store_rows_bf16(tile, ep.out_bf16, ep.ld_bf16, r0, M, c0, nv, o, ep.vec != 0);
+  if (ep.out2_bf16) store_rows_bf16(tile, ep.out2_bf16, ep.ld2, r0, M, c0, nv, acc, ep.vec != 0);
+  if (ep.out_t_bf16 && live_row)   // transposed: consecutive lanes (rows) write consecutive addresses of a column
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < nv) ep.out_t_bf16[(size_t)(c0 + j) * ep.ld_t + r] = __float2bfloat16(o[j]);
+}
+
+// Persistent GEMM: CTA b takes units b, b + gridDim.x, ... of the (row tile, column tile,
+// K slice) grid, column tiles fastest.  Warp roles:
+//   warp 0 (one lane): TMA producer; one ring of 64-wide K stages runs across the CTA's units
+//   warp 1 (one lane): tcgen05.mma issuer into one of two tensor-memory accumulators
+//                      (alternating per unit); warp 1 also allocates / frees the tensor memory
+//   warps 4..11      : epilogue, straight from tensor memory: warp w reads the accumulator rows
+//                      (TMEM lanes) 32 (w % 4) .. + 31, warps 4..7 the even and warps 8..11
+//                      the odd 16-column chunks; a unit's epilogue overlaps the next unit's MMAs
+// Every mbarrier wait is bounded (about 2 s of SM clock); on a timeout the CTA stops issuing,
+// drains its own TMA copies and MMAs (bounded), frees its tensor memory and raises *err.
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N, int K,
-                EpiParams ep, int* err) {
-  constexpr int GEMM_STAGES = GemmStages<BN>::value;
+                int splits, EpiParams ep, int* err) {
+  constexpr int STAGES = GemmStages<BN>::value;
   constexpr uint32_t A_BYTES = GEMM_BM * GEMM_BK * 2;
   constexpr uint32_t B_BYTES = BN * GEMM_BK * 2;
-  constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  constexpr uint32_t ACC = GemmAcc<BN>::cols;
+  constexpr int NCH = (BN + 15) / 16;
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
   static_assert(B_BYTES % 1024 == 0, "stage buffers must stay 1024-byte aligned");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sa = smem;
-  uint8_t* sb = smem + GEMM_STAGES * A_BYTES;
-  uint64_t* full = (uint64_t*)(sb + GEMM_STAGES * B_BYTES);
-  uint64_t* empty = full + GEMM_STAGES;
-  uint64_t* tfull = empty + GEMM_STAGES;
-  uint32_t* tslot = (uint32_t*)(tfull + 1);
+  uint8_t* sb = smem + STAGES * A_BYTES;
+  uint64_t* full = (uint64_t*)(sb + STAGES * B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;    // [2] MMA -> epilogue
+  uint64_t* acc_empty = acc_full + 2;     // [2] epilogue -> MMA
+  uint64_t* mma_done = acc_empty + 2;
+  uint32_t* tslot = (uint32_t*)(mma_done + 1);
   __shared__ volatile int s_fail;
-  __shared__ __align__(16) float s_bias[BN], s_scale[BN], s_add[BN];
-  __shared__ float s_rowsum[GEMM_BM];
+  __shared__ float s_part[2][GEMM_BM];    // row-sum halves (EPI_QOI)
+  __shared__ float s_colsum[BN];          // column sums (EPI_DECODE)
+  __shared__ __align__(16) float s_tile[8][32 * GEMM_TROW];   // per epilogue warp: the row-store transpose
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * GEMM_BM, n0 = blockIdx.x * BN;
-  // split-K: CTA z owns K blocks [kb_lo, kb_lo + KB)
+  const int mt = (M + GEMM_BM - 1) / GEMM_BM, nt = (N + BN - 1) / BN;
+  const int units = mt * nt * splits;
   const int KB_all = (K + GEMM_BK - 1) / GEMM_BK;
-  const int per = (KB_all + gridDim.z - 1) / gridDim.z;
-  const int kb_lo = blockIdx.z * per;
-  const int KB = max(0, min(KB_all, kb_lo + per) - kb_lo);
-  const bool splitk = gridDim.z > 1;
+  const int per = (KB_all + splits - 1) / splits;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
-    for (int s = 0; s < GEMM_STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int st = 0; st < STAGES; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
     }
-    mbar_init(tfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 8);   // lane 0 of each epilogue warp
+    }
+    mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(tslot, TMEM_COLS);
+  if (warp == 1) tmem_alloc(tslot, 2 * ACC);
   if (warp == 0 && lane < 2) tmap_prefetch(lane == 0 ? &ta : &tb);
   pdl_wait();   // everything below reads or writes what earlier kernels produce or consume
-  for (int i = threadIdx.x; i < BN; i += GEMM_THREADS) {   // per-column epilogue constants
-    const int c = n0 + i;
-    s_bias[i] = (c < N && ep.bias && blockIdx.z == 0) ? ep.bias[c] : 0.f;
-    s_scale[i] = ep.mode == EPI_DECODE ? (c < N ? ep.col_ref[c] : 0.f) : (c < N && ep.col_scale) ? ep.col_scale[c] : 1.f;
-    s_add[i] = (c < N && ep.col_add) ? ep.col_add[c] : 0.f;
-  }
-  for (int i = threadIdx.x; i < GEMM_BM; i += GEMM_THREADS) s_rowsum[i] = 0.f;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -254,119 +252,189 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % GEMM_STAGES;
-        const uint32_t ph = (uint32_t)(kb / GEMM_STAGES) & 1u;
-        if (kb >= GEMM_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
-          s_fail = 1;
-          break;
+      int g = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int ntile = u % nt, rest = u / nt, mtile = rest % mt, z = rest / mt;
+        const int kb_lo = z * per, KB = max(0, min(KB_all, kb_lo + per) - kb_lo);
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int st = g % STAGES;
+          if (g >= STAGES && !mbar_wait(&empty[st], ((uint32_t)(g / STAGES) & 1u) ^ 1u)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[st], A_BYTES + B_BYTES);
+          tma_load_2d(sa + st * A_BYTES, &ta, (kb_lo + kb) * GEMM_BK, mtile * GEMM_BM, &full[st]);
+          tma_load_2d(sb + st * B_BYTES, &tb, (kb_lo + kb) * GEMM_BK, ntile * BN, &full[st]);
         }
-        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-        tma_load_2d(sa + s * A_BYTES, &ta, (kb_lo + kb) * GEMM_BK, m0, &full[s]);
-        tma_load_2d(sb + s * B_BYTES, &tb, (kb_lo + kb) * GEMM_BK, n0, &full[s]);
-        issued = kb + 1;
       }
-      // Drain: the last copy issued into every stage must have landed before exit.
-      for (int kb = std::max(0, issued - GEMM_STAGES); kb < issued; ++kb)
-        if (!mbar_wait(&full[kb % GEMM_STAGES], (uint32_t)(kb / GEMM_STAGES) & 1u)) s_fail = 1;
+      if (!ok) s_fail = 1;
+      // drain: the last copy issued into every stage has landed before exit
+      for (int f = max(0, g - STAGES); f < g; ++f)
+        if (!mbar_wait(&full[f % STAGES], (uint32_t)(f / STAGES) & 1u)) s_fail = 1;
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                              ((uint32_t)(GEMM_BM >> 4) << 24);
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % GEMM_STAGES;
-        const uint32_t ph = (uint32_t)(kb / GEMM_STAGES) & 1u;
-        if (!mbar_wait(&full[s], ph)) {
-          s_fail = 1;
+      int g = 0, j = 0;
+      bool ok = true, any = false;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++j) {
+        const int z = u / (nt * mt);
+        const int kb_lo = z * per, KB = max(0, min(KB_all, kb_lo + per) - kb_lo);
+        const int b = j & 1;
+        if (j >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)((j >> 1) - 1) & 1u)) {   // the epilogue read buffer b
+          ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_u32(sa + s * A_BYTES), b0 = smem_u32(sb + s * B_BYTES);
+        const uint32_t d = tmem + (uint32_t)b * ACC;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int st = g % STAGES;
+          if (!mbar_wait(&full[st], (uint32_t)(g / STAGES) & 1u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sa + st * A_BYTES), b0 = smem_u32(sb + st * B_BYTES);
 #pragma unroll
-        for (int k = 0; k < GEMM_BK / 16; ++k)
-          tc_mma(tmem, smem_desc_sw128(a0 + k * 32), smem_desc_sw128(b0 + k * 32), idesc, (kb | k) != 0);
-        tc_commit(&empty[s]);
+          for (int k = 0; k < GEMM_BK / 16; ++k)
+            tc_mma(d, smem_desc_sw128(a0 + k * 32), smem_desc_sw128(b0 + k * 32), idesc, (kb | k) != 0);
+          tc_commit(&empty[st]);
+          any = true;
+        }
+        if (ok) tc_commit(&acc_full[b]);   // completes once the unit's MMAs have finished
       }
-      tc_commit(tfull);   // completes once every MMA issued above has finished
+      if (!ok) s_fail = 1;
+      if (any) {
+        tc_commit(mma_done);
+        if (!mbar_wait(mma_done, 0)) s_fail = 1;
+      }
     }
-  } else if (warp < 6) {
-    // Epilogue A (warps 2..5): TMEM -> shared staging tile, one accumulator row per thread
-    // (warp w may read TMEM lanes 32 (w % 4) .. +31).  The pipeline buffers are free once
-    // every MMA has completed.
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0) ? 1 : 0);
-    tc_fence_after();
-    const int q = warp & 3;
-    // Row stride BN + 4 floats (4 x an odd number): the 16-byte stores of eight
-    // consecutive rows fall in distinct bank groups.
-    float* stage = (float*)smem;
-    constexpr int SROW = BN + 4;
-    float4* srow = reinterpret_cast<float4*>(stage + (q * 32 + lane) * SROW);
-    if (!ok && lane == 0) s_fail = 1;
-    if (ok && KB > 0) {
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+  } else if (warp >= 4) {
+    const int q = warp & 3, half = (warp - 4) >> 2;
+    int j = 0;
+    bool live = true;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++j) {
+      const int ntile = u % nt, rest = u / nt, mtile = rest % mt, z = rest / mt;
+      const int kb_lo = z * per, KB = max(0, min(KB_all, kb_lo + per) - kb_lo);
+      const int b = j & 1;
+      // after a timed-out wait a warp stops reading and writing but keeps its place in the loop:
+      // the named barriers below need all eight epilogue warps every time
+      if (live) live = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)(j >> 1) & 1u) ? 1 : 0) != 0;
+      if (!live && lane == 0) s_fail = 1;
+      tc_fence_after();
+      const int r = mtile * GEMM_BM + q * 32 + lane, n0 = ntile * BN;
+      float rowsum = 0.f;
+      if (ep.mode == EPI_DECODE) {   // rows are grid nodes, columns samples: out[c][r], column sums
+        for (int i = threadIdx.x - 128; i < BN; i += 256) s_colsum[i] = 0.f;
+        gemm_epi_sync();
+        const float radd = (r < M && live) ? __ldg(ep.col_add + r) : 0.f;
+        const float rref = (r < M && live) ? __ldg(ep.col_ref + r) : 0.f;
+        for (int k = half; k < NCH && live; k += 2) {
+          const int c0 = n0 + 16 * k;
+          if (c0 >= N) break;   // the same in every lane
+          uint32_t v[16];
+          tmem_ld16(tmem + (uint32_t)b * ACC + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * k), v);
+          const int nv = min(16, N - c0);
+          float sq[16];
 #pragma unroll
-        for (int j = 0; j < 16; j += 4)
-          srow[(c0 + j) >> 2] = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                                            __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+          for (int i = 0; i < 16; ++i) {
+            const float val = __uint_as_float(v[i]) + radd;
+            if (r < M && i < nv) ep.out_f32[(size_t)(c0 + i) * ep.ld_f32 + r] = val;   // coalesced over lanes
+            const float dd = (r < M && i < nv) ? val - rref : 0.f;
+            sq[i] = dd * dd;
+          }
+          // the 16 column sums over the warp's 32 rows by recursive halving: after the steps
+          // over lane bits 4..1 lane L holds the sum over 16 lanes of column
+          // 8 b4 + 4 b3 + 2 b2 + b1 (b_i the bits of L); the last step adds the lane pair
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const bool up = lane & 16;
+            const float send = up ? sq[i] : sq[i + 8];
+            const float got = __shfl_xor_sync(0xffffffffu, send, 16);
+            sq[i] = (up ? sq[i + 8] : sq[i]) + got;
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const bool up = lane & 8;
+            const float send = up ? sq[i] : sq[i + 4];
+            const float got = __shfl_xor_sync(0xffffffffu, send, 8);
+            sq[i] = (up ? sq[i + 4] : sq[i]) + got;
+          }
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const bool up = lane & 4;
+            const float send = up ? sq[i] : sq[i + 2];
+            const float got = __shfl_xor_sync(0xffffffffu, send, 4);
+            sq[i] = (up ? sq[i + 2] : sq[i]) + got;
+          }
+          {
+            const bool up = lane & 2;
+            const float send = up ? sq[0] : sq[1];
+            const float got = __shfl_xor_sync(0xffffffffu, send, 2);
+            sq[0] = (up ? sq[1] : sq[0]) + got;
+          }
+          sq[0] += __shfl_xor_sync(0xffffffffu, sq[0], 1);
+          const int col = 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+          if (!(lane & 1) && col < nv) atomicAdd(&s_colsum[16 * k + col], sq[0]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[b]);
+        gemm_epi_sync();
+        for (int i = threadIdx.x - 128; i < BN; i += 256)
+          if (n0 + i < N && live) atomicAdd(&ep.out_q[n0 + i], ep.qconst * (double)s_colsum[i]);
+        gemm_epi_sync();   // read before the next unit clears it
+        continue;
       }
-    } else if (ok) {   // empty K range (split-K remainder): contributes zero
-      for (int c = 0; c < BN; c += 4) srow[c >> 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (KB > 0 && live) {
+        for (int k = half; k < NCH; k += 2) {
+          const int c0 = n0 + 16 * k;
+          if (c0 >= N) break;   // the same in every lane
+          uint32_t v[16];
+          tmem_ld16(tmem + (uint32_t)b * ACC + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * k), v);
+          float acc[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[i] = __uint_as_float(v[i]);
+          {   // every lane (the row stores are warp-collective); rows >= M are not written
+            const int nv = min(16, N - c0);
+            float* tile = s_tile[warp - 4];
+            if (splits > 1)
+              epi_chunk<7>(acc, r, M, c0, nv, ep, z == 0, rowsum, tile);
+            else if (ep.mode == EPI_LINEAR)
+              epi_chunk<EPI_LINEAR>(acc, r, M, c0, nv, ep, true, rowsum, tile);
+            else if (ep.mode == EPI_GELU)
+              epi_chunk<EPI_GELU>(acc, r, M, c0, nv, ep, true, rowsum, tile);
+            else if (ep.mode == EPI_GELU_D)
+              epi_chunk<EPI_GELU_D>(acc, r, M, c0, nv, ep, true, rowsum, tile);
+            else if (ep.mode == EPI_SCALE)
+              epi_chunk<EPI_SCALE>(acc, r, M, c0, nv, ep, true, rowsum, tile);
+            else if (ep.mode == EPI_QOI)
+              epi_chunk<EPI_QOI>(acc, r, M, c0, nv, ep, true, rowsum, tile);
+            else
+              epi_chunk<EPI_DGELU_SCALE>(acc, r, M, c0, nv, ep, true, rowsum, tile);
+          }
+        }
+      }
+      // the accumulator buffer is read: the MMA issuer may reuse it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+      if (ep.mode == EPI_QOI) {   // the two halves of each row's quadratic
+        s_part[half][q * 32 + lane] = rowsum;
+        gemm_epi_sync();
+        if (half == 0 && r < M && live)
+          ep.out_q[r] = ep.qconst + 0.5 * ((double)s_part[0][q * 32 + lane] + (double)s_part[1][q * 32 + lane]);
+        gemm_epi_sync();   // read before the next unit overwrites it
+      }
     }
   }
   tc_fence_before();
-  __syncthreads();   // staging tile complete; producer and MMA roles are done
-  {
-    constexpr int SROW = BN + 4;
-    float* stage = (float*)smem;
-    const bool run = !s_fail;
-    const bool keep = ep.out_t_bf16 != nullptr && !splitk;
-    if (run) {
-      if (splitk)
-        epi_quads<BN, 7>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, false);
-      else if (ep.mode == EPI_LINEAR)
-        epi_quads<BN, EPI_LINEAR>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
-      else if (ep.mode == EPI_GELU)
-        epi_quads<BN, EPI_GELU>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
-      else if (ep.mode == EPI_GELU_D)
-        epi_quads<BN, EPI_GELU_D>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
-      else if (ep.mode == EPI_SCALE)
-        epi_quads<BN, EPI_SCALE>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
-      else if (ep.mode == EPI_QOI)
-        epi_quads<BN, EPI_QOI>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
-      else if (ep.mode == EPI_DECODE)
-        epi_quads<BN, EPI_DECODE>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, false);
-      else
-        epi_quads<BN, EPI_DGELU_SCALE>(stage, s_bias, s_scale, s_add, s_rowsum, m0, n0, M, N, ep, keep);
-    }
-    if (ep.mode == EPI_QOI && run) {   // the tile holds whole rows: finish the per-row quadratic
-      __syncthreads();
-      for (int tr = threadIdx.x; tr < GEMM_BM; tr += GEMM_THREADS)
-        if (m0 + tr < M) ep.out_q[m0 + tr] = ep.qconst + 0.5 * (double)s_rowsum[tr];
-    }
-    if (ep.mode == EPI_DECODE && run) {   // this tile's columns of each row's sum
-      __syncthreads();
-      for (int tr = threadIdx.x; tr < GEMM_BM; tr += GEMM_THREADS)
-        if (m0 + tr < M) atomicAdd(&ep.out_q[m0 + tr], ep.qconst * (double)s_rowsum[tr]);
-    }
-    if (ep.out_t_bf16 && !splitk) {
-      // Epilogue C (all warps): transposed output, consecutive threads on consecutive rows.
-      __syncthreads();
-      if (run)
-        for (int e = threadIdx.x; e < GEMM_BM * BN; e += GEMM_THREADS) {
-          const int tr = e % GEMM_BM, cc = e / GEMM_BM, r = m0 + tr, c = n0 + cc;
-          if (r < M && c < N) ep.out_t_bf16[(size_t)c * ep.ld_t + r] = __float2bfloat16(stage[tr * SROW + cc]);
-        }
-    }
-  }
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    tmem_dealloc(tmem, 2 * ACC);
   }
   if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
 }
@@ -416,19 +484,23 @@ bool ouu_tmap_bf16(CUtensorMap* map, const void* base, uint64_t k, uint64_t rows
 template <int BN>
 static ouu_status launch_bn(const CUtensorMap& ta, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                             const EpiParams& ep, int* err, cudaStream_t s, int splits) {
-  constexpr int GEMM_STAGES = GemmStages<BN>::value;
-  static_assert((size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) >= (size_t)GEMM_BM * (BN + 4) * 4,
-                "the pipeline buffers must hold the epilogue staging tile");
+  constexpr int STAGES = GemmStages<BN>::value;
   CUtensorMap tb;
   if (!ouu_tmap_bf16(&tb, B, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, BN)) {
     ouu_set_error("tensor map for GEMM operand B failed (alignment or driver entry point)");
     return OUU_ERR_INVALID_ARG;
   }
-  const size_t smem = 1024 + (size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) +
-                      (2 * GEMM_STAGES + 1) * 8 + 16;
+  const size_t smem = 1024 + (size_t)STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) + (2 * STAGES + 5) * 8 + 16;
   OUU_CUDA_TRY(ouu_smem_limit((const void*)k_gemm_bf16<BN>, smem));
-  dim3 grid((N + BN - 1) / BN, (M + GEMM_BM - 1) / GEMM_BM, splits);
-  OUU_CUDA_TRY(launch_pdl(k_gemm_bf16<BN>, grid, dim3(GEMM_THREADS), smem, s, ta, tb, M, N, K, ep, err));
+  static const int sms = [] {   // initialised once, thread-safe (one device per process)
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  const long units = (long)((N + BN - 1) / BN) * ((M + GEMM_BM - 1) / GEMM_BM) * splits;
+  const int grid = (int)std::min<long>(units, sms);
+  OUU_CUDA_TRY(launch_pdl(k_gemm_bf16<BN>, dim3(grid), dim3(GEMM_THREADS), smem, s, ta, tb, M, N, K, splits, ep, err));
   return OUU_OK;
 }
 

@@ -17,8 +17,9 @@ enum EpiMode {
   EPI_QOI = 5,          // phi = (acc + bias[c]) * col_scale[c] -> out_f32; v = phi + col_add[c];
                         // bf16 outputs = v * col_scale[c]; out_q[r] = qconst + 1/2 sum_c v^2
                         // (one N tile: N <= 256)
-  EPI_DECODE = 6,       // v = acc + col_add[c] -> out_f32 (coalesced rows);
-                        // out_q[r] += qconst * sum_c (v - col_ref[c])^2 (out_q zeroed beforehand)
+  EPI_DECODE = 6,       // rows r are grid nodes, columns c samples: v = acc + col_add[r] ->
+                        // out_f32[c * ld_f32 + r]; out_q[c] += qconst * sum_r (v - col_ref[r])^2
+                        // (out_q zeroed beforehand; col_add, col_ref indexed by row)
 };
 
 struct EpiParams {
@@ -42,7 +43,7 @@ struct EpiParams {
   const float* col_add;           // EPI_QOI: per-column shift c
   double* out_q;                  // EPI_QOI, EPI_DECODE: [M] per-row quadratic
   double qconst;                  // EPI_QOI: added to every out_q; EPI_DECODE: factor of the sum
-  const float* col_ref;           // EPI_DECODE: per-column reference subtracted before squaring
+  const float* col_ref;           // EPI_DECODE: per-row reference subtracted before squaring
 };
 
 // Tensor map of a row-major BF16 matrix [rows][ld] (K = inner, contiguous), box 64 x box_rows.
