@@ -348,9 +348,16 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
-def time_steps(step, k, stream, label="timed"):
+def time_steps(step, k, stream, label="timed", warmup=0):
+    """K steps back to back between two CUDA events on `stream`, after `warmup` untimed steps
+    issued directly before them (no idle gap between the warm-up and the timed region)."""
+    import gc
+
     import torch
+    gc.collect()   # no collection of the construction's garbage inside the timed region
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(warmup):
+        step()
     outs = []
     torch.cuda.nvtx.range_push(label)
     e0.record(stream)
@@ -469,15 +476,13 @@ def run_ours(args):
         del mh
 
     # ---- plain path beside it
-    for _ in range(1 if use_dino else max(3, args.warmup)):
-        pde_step()
-    torch.cuda.synchronize()
     pde_k = args.pde_steps if use_dino else args.steps
     clocks = ClockSampler(local, args.clocks_log)
     if not use_dino:
         clocks.start()
     barrier(dist)
-    pde_ms, pde_outs = time_steps(pde_step, pde_k, stream, "pde_timed" if use_dino else "timed")
+    pde_ms, pde_outs = time_steps(pde_step, pde_k, stream, "pde_timed" if use_dino else "timed",
+                                  warmup=1 if use_dino else max(3, args.warmup))
     pde_ms = max_over_ranks(dist, pde_ms, dev)
     pde_rate = pde_k / (pde_ms / 1000.0)
     pde_info = {"evals_per_s": pde_rate, "ms_per_eval": pde_ms / pde_k}
@@ -500,14 +505,13 @@ def run_ours(args):
 
         def step():
             return evaluate(backend, D, z)
-        for _ in range(max(3, args.warmup)):
-            step()
+        step()
         torch.cuda.synchronize()
         if backend == capi.BACKEND_AUTO and P.ouu_last_backend() != capi.BACKEND_DINO:
             raise RuntimeError("AUTO did not take the network after its held-out check passed")
         clocks.start()
         barrier(dist)
-        ms, outs = time_steps(step, args.steps, stream)
+        ms, outs = time_steps(step, args.steps, stream, warmup=max(3, args.warmup))
         barrier(dist)
         clk = clocks.stop()
         ms = max_over_ranks(dist, ms, dev)
@@ -571,10 +575,7 @@ def run_ours(args):
             def e2e_step():
                 m.copy_(m_host, non_blocking=True)
                 return step()
-            for _ in range(3):
-                e2e_step()
-            torch.cuda.synchronize()
-            e_ms, _ = time_steps(e2e_step, args.steps, stream, "e2e")
+            e_ms, _ = time_steps(e2e_step, args.steps, stream, "e2e", warmup=3)
             e_ms = max_over_ranks(dist, e_ms, dev)
             e2e = {"value": args.steps / (e_ms / 1000.0), "unit": "evals/s",
                    "h2d_bytes_per_step": int(N * n * n * 8 + dz * 8),
@@ -781,17 +782,14 @@ def run_config4(args):
 
     def step():
         return P.ouu_risk_and_grad(backend, D, m, N, risks, z)
-    for _ in range(max(3, args.warmup)):
-        step()
+    step()
     torch.cuda.synchronize()
     clocks = ClockSampler(0, args.clocks_log)
     clocks.start()
-    ms, _ = time_steps(step, args.steps, stream)
+    ms, _ = time_steps(step, args.steps, stream, warmup=max(3, args.warmup))
     clk = clocks.stop()
     pde_step = lambda: P.ouu_risk_and_grad(capi.BACKEND_PDE, None, m, N, risks, z)   # noqa: E731
-    pde_step()
-    torch.cuda.synchronize()
-    pde_ms, _ = time_steps(pde_step, 2, stream, "pde_timed")
+    pde_ms, _ = time_steps(pde_step, 2, stream, "pde_timed", warmup=1)
     D.ouu_dino_set_graphs(0)
     st = [P.ouu_risk_and_grad(capi.BACKEND_DINO, D, m, N, risks, z)[4] for _ in range(3)][1:]
     D.ouu_dino_set_graphs(1)
