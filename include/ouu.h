@@ -88,7 +88,8 @@ typedef struct {
   int adjoint_solves;           /* adjoint solves performed (samples with nonzero weight) */
   int n_not_converged;
   float ms_state;               /* PDE: batched state solve; DINO: projection + network (CUDA events) */
-  float ms_weights;             /* risk weights / t* */
+  float ms_weights;             /* risk weights / t*; DINO: the weighted pass (t* runs beside the
+                                   network's reverse mode, inside ms_network) */
   float ms_adjoint;             /* batched adjoint solve */
   float ms_reduce;              /* weighted adjoint sum and G^T */
   float ms_total;               /* whole evaluation on the device */

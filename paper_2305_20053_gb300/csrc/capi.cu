@@ -425,11 +425,26 @@ ouu_status dino_enqueue_risk(ouu_problem* p, ouu_dino* dino, const double* m_dev
   double* d_res = p->d_out;
   double* d_grad = p->d_out + 3 * OUU_MAX_RISKS;
   const size_t ob = (size_t)(OUU_MAX_RISKS * (3 + dz) + 8) * 8;
-  if (ouu_status st = dino_eval_core(dino, m_dev, n_samples, z_host, true)) return st;
+  bool split = false;
+  if (ouu_status st = dino_eval_forward(dino, m_dev, n_samples, z_host, &split)) return st;
+  if (split) {
+    // Q is complete: the moments and t* (which read only Q) on the side stream, beside the
+    // network's reverse mode on the main one; joined before the weighted sums
+    OUU_CUDA_TRY(cudaEventRecord(dino->ev_fork, dino->stream));
+    OUU_CUDA_TRY(cudaStreamWaitEvent(dino->side, dino->ev_fork, 0));
+    launch_risk_select(dino->Qe, n_samples, p->d_risks, n_risks, p->d_rscr, dino->side, d_grad, n_risks * dz);
+    OUU_CUDA_TRY(cudaEventRecord(dino->ev_join, dino->side));
+    if (ouu_status st = dino_eval_reverse(dino, n_samples)) return st;
+    OUU_CUDA_TRY(cudaStreamWaitEvent(dino->stream, dino->ev_join, 0));
+  }
   if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[1], dino->stream));
   // weights, risk values and sum_i w_i grad Q_i in one pass over the samples
-  launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream, dino->GQe,
+  if (split)
+    launch_risk_apply(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream, dino->GQe,
                       (dz + 7) / 8 * 8, dz, d_grad);
+  else
+    launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream,
+                        dino->GQe, (dz + 7) / 8 * 8, dz, d_grad);
   if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[2], dino->stream));
   OUU_CUDA_TRY(cudaGetLastError());
   OUU_CUDA_TRY(cudaMemcpyAsync(p->h_out, p->d_out, ob, cudaMemcpyDeviceToHost, dino->stream));

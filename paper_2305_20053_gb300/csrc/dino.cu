@@ -349,6 +349,9 @@ static void free_dino(ouu_dino* d) {
     if (e) cudaEventDestroy(e);
   if (d->gexec) cudaGraphExecDestroy(d->gexec);
   if (d->cap) cudaStreamDestroy(d->cap);
+  if (d->side) cudaStreamDestroy(d->side);
+  if (d->ev_fork) cudaEventDestroy(d->ev_fork);
+  if (d->ev_join) cudaEventDestroy(d->ev_join);
   delete d;
 }
 
@@ -522,6 +525,9 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   }
   for (auto& e : d->ev) OUU_CUDA_TRY(cudaEventCreate(&e));
   OUU_CUDA_TRY(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
+  OUU_CUDA_TRY(cudaStreamCreateWithFlags(&d->side, cudaStreamNonBlocking));
+  OUU_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming));
+  OUU_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming));
   OUU_CUDA_TRY(cudaDeviceSynchronize());
   *out = d;
   return OUU_OK;
@@ -882,13 +888,35 @@ extern "C" ouu_status ouu_dino_loss_grad(ouu_dino_t d, const float* xi_dev, cons
 // grad_z Q in GQe by reverse mode: seed phi + c through W3^T, GELU', ... , W0z^T.
 static ouu_status dino_network(ouu_dino* d, int N, bool want_grad);
 
-ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad) {
+// The controls to the device and the projection of the fields into XIe.
+static ouu_status dino_eval_inputs(ouu_dino* d, const double* m_dev, int N, const double* z_host) {
   ++d->eval_count;   // the per-sample buffers now belong to this evaluation
   float* zh = (float*)d->h_pin;
   for (int j = 0; j < d->dz; ++j) zh[j] = (float)z_host[j];
   OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)d->dz * 4, cudaMemcpyHostToDevice, d->stream));
   DINO_TRY(project_fields(d, m_dev, N, d->XIe, true));
+  return OUU_OK;
+}
+
+ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad) {
+  DINO_TRY(dino_eval_inputs(d, m_dev, N, z_host));
   return dino_network(d, N, want_grad);
+}
+
+ouu_status dino_eval_forward(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool* split) {
+  *split = d->fused_mlp == 2 && mlp_cluster_fits(d);
+  if (!*split) return dino_eval_core(d, m_dev, N, z_host, true);
+  DINO_TRY(dino_eval_inputs(d, m_dev, N, z_host));
+  DINO_TRY(mlp_cluster_eval(d, N, 0, 4));
+  OUU_CUDA_TRY(cudaGetLastError());
+  return OUU_OK;
+}
+
+ouu_status dino_eval_reverse(ouu_dino* d, int N) {
+  DINO_TRY(mlp_cluster_eval(d, N, 4, 8));
+  if (!d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[3], d->stream));
+  OUU_CUDA_TRY(cudaGetLastError());
+  return OUU_OK;
 }
 
 // The network from the projection coordinates in XIe and the controls in d_zf.

@@ -72,6 +72,10 @@ struct ouu_dino {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // cast | projection | network phase marks
   // CUDA graph of the risk evaluation (captured on a private stream, replayed on `stream`)
   cudaStream_t cap = nullptr;
+  // second stream of a risk evaluation: the risk selection on Q runs there beside the
+  // network's reverse mode (forked after the forward part, joined before the weighted sums)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec = nullptr;
   const void* gkey_p = nullptr;
   const double* gkey_m = nullptr;
@@ -95,6 +99,13 @@ bool dino_trusted(const ouu_dino* d, const ouu_problem* p, int n_samples);
 
 // DINO forward/backward pieces used by the C ABI (dino.cu).
 ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool want_grad);
+// dino_eval_core with the gradient, in two parts on d->stream: dino_eval_forward enqueues the
+// projection and the network up to the reduced QoI (Qe is complete once its work is), and
+// dino_eval_reverse the reverse mode (GQe).  *split = false: the network runs as one launch
+// (another network mode, or sizes beyond the cluster kernel) and the forward call enqueued
+// all of it; dino_eval_reverse is then not called.
+ouu_status dino_eval_forward(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool* split);
+ouu_status dino_eval_reverse(ouu_dino* d, int N);
 // Decoded states u[N][nn] (FP32) = Phi phi_i + ubar from the coefficients phi [N][ldphi] (FP32),
 // and the decoded QoI q[N] = 1/2 h^2 sum over the interior (u - u_t)^2 (FP64), on d->stream.
 ouu_status dino_decode(ouu_dino* d, const float* phi, int ldphi, int N, float* u, double* q);
@@ -108,8 +119,10 @@ ouu_status mlp_fused_eval(ouu_dino* d, int N);
 // quarter of every layer's columns; the layers' activations pass through the handle's
 // evaluation buffers in L2 (mlp_cluster.cu).  mlp_cluster_fits: width, r_U, r_M + d_Z <= 448,
 // d_Z <= 512, r_M % 4 == 0, width % 8 == 0.
+// The layers [l0, l1) of the eight (three GELU layers and the QoI layer forward, four reverse):
+// [0, 8) in one launch, or [0, 4) and [4, 8) as two.
 bool mlp_cluster_fits(const ouu_dino* d);
-ouu_status mlp_cluster_eval(ouu_dino* d, int N);
+ouu_status mlp_cluster_eval(ouu_dino* d, int N, int l0 = 0, int l1 = 8);
 
 // The whole MR-DINO risk evaluation enqueued on d->stream (capi.cu); the problem's risk
 // descriptors must be in p->d_risks.

@@ -19,6 +19,8 @@
 //                 MMAs are done)
 //   warp 17     : tcgen05.mma issuer (M = 128, N = the CTA's columns); allocates and frees
 //                 the tensor memory
+// The layers can run as two launches, [0, 4) (forward and reduced QoI) and [4, 8) (reverse
+// mode), so that work needing only Q can run beside the second one.
 // Every mbarrier wait is bounded; on a timeout the CTA skips the remaining work (still
 // arriving on its peers' barriers) and raises *err.  The only unbounded waits are the two
 // cluster barriers every thread reaches unconditionally: after the barriers' initialisation
@@ -69,11 +71,13 @@ struct MlcParams {
   CUtensorMap w[MLC_LAYERS];    // layer weights [N][K] BF16, 64 x nc boxes
   MlcLayer L[MLC_LAYERS];
   int M, rm, dz, in0p;
+  int l0, l1;                   // the layers [l0, l1) of this launch; l0 > 0: layer l0's input
+                                // is already in its evaluation buffer (an earlier launch)
   const float* xi;              // [M][rm]
   const float* zf;              // [dz]
   __nv_bfloat16* x0;            // [M][in0p] layer-0 input, built here
   float* qpart;                 // [M][4] per-CTA partial sums of (phi + c)^2
-  double* q_out;                // [M]
+  double* q_out;                // [M]; null when the QoI layer is not in [l0, l1)
   double qconst;
   int* err;
 };
@@ -182,8 +186,10 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
     fence_async_smem();
   }
   if (warp == MLC_MMA_WARP) tmem_alloc(tslot, MLC_NCMAX);
-  if (warp == MLC_PROD_WARP && lane < 2 * MLC_LAYERS)   // every layer's descriptors, off the critical path
-    tmap_prefetch(lane < MLC_LAYERS ? &P.a[lane] : &P.w[lane - MLC_LAYERS]);
+  if (warp == MLC_PROD_WARP && lane < 2 * MLC_LAYERS) {   // the launch's descriptors, off the critical path
+    const int ll = lane < MLC_LAYERS ? lane : lane - MLC_LAYERS;
+    if (ll >= P.l0 && ll < P.l1) tmap_prefetch(lane < MLC_LAYERS ? &P.a[ll] : &P.w[ll]);
+  }
   pdl_wait();
   tc_fence_before();
   __syncthreads();
@@ -199,8 +205,9 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
 #pragma unroll
       for (int i = 0; i < MLC_KBMAX; ++i) a_uses[i] = 0;
       bool ok = true;
-      for (int l = 0; l < MLC_LAYERS && ok; ++l) {
+      for (int l = P.l0; l < P.l1 && ok; ++l) {
         const MlcLayer& L = P.L[l];
+        const int li = l - P.l0;   // barrier bookkeeping counts the launch's own layers
         const int KB = (L.K + 63) / 64, pre = min(KB, MLC_STAGES), wrow = (int)rank * L.nc;
         const uint32_t wbytes = (uint32_t)L.nc * 128u;
         auto load_w = [&](int kb) {   // weight block kb of this layer into the ring
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
         if (!ok) break;
         // the layer's input is complete in every CTA of the cluster; on a timeout the input is
         // still loaded, so that every barrier armed here completes before the CTA exits
-        if (!mlc_wait_cluster(&layer_in[l & 1], (uint32_t)(l >> 1) & 1u)) ok = false;
+        if (!mlc_wait_cluster(&layer_in[li & 1], (uint32_t)(li >> 1) & 1u)) ok = false;
         asm volatile("fence.proxy.async.global;" ::: "memory");
         // all of the layer's input blocks at once (multicasting each block from one CTA of the
         // cluster to all four measured slower: each CTA then waits for its slowest peer)
@@ -226,7 +233,7 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
         }
         for (int kb = pre; kb < KB && ok; ++kb) ok = load_w(kb);
         gw += KB;
-        if (ok && l + 1 < MLC_LAYERS) {
+        if (ok && l + 1 < P.l1) {
           // the input blocks are overwritten only once the epilogue of this layer is done (the
           // next layer's input wait follows it), so nothing else to wait for here
         }
@@ -244,12 +251,13 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
       int gw = 0;
       uint32_t apar = 0;   // bit kb: parity of the next completion of a_full[kb]
       bool ok = true, any = false;
-      for (int l = 0; l < MLC_LAYERS && ok; ++l) {
+      for (int l = P.l0; l < P.l1 && ok; ++l) {
         const MlcLayer& L = P.L[l];
+        const int li = l - P.l0;
         const int KB = (L.K + 63) / 64;
         const uint32_t idesc =
             (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(L.nc >> 3) << 17) | ((128u >> 4) << 24);
-        if (l > 0 && !mbar_wait(acc_empty, (uint32_t)(l - 1) & 1u)) {   // previous accumulator read
+        if (li > 0 && !mbar_wait(acc_empty, (uint32_t)(li - 1) & 1u)) {   // previous accumulator read
           ok = false;
           break;
         }
@@ -281,7 +289,11 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
     // ------------------------------------------------------------------ input build + epilogues
     const int q = warp & 3, grp = warp >> 2, et = threadIdx.x;
     constexpr int NT = MLC_EPI_WARPS * 32;
-    {  // this CTA's quad-aligned quarter of the layer-0 input columns: [xi (rm); z (dz); 0]
+    if (P.l0 > 0) {   // the first layer's input came from an earlier launch (complete after pdl_wait)
+      __syncwarp();
+      if (lane == 0)
+        for (uint32_t r = 0; r < MLC_CS; ++r) mlc_arrive_remote(&layer_in[0], r);
+    } else {  // this CTA's quad-aligned quarter of the layer-0 input columns: [xi (rm); z (dz); 0]
       const int cw = ((P.in0p / 4 + MLC_CS - 1) / MLC_CS) * 4;
       const int cb = (int)rank * cw, ce = min(P.in0p, cb + cw), nq = max(0, ce - cb) / 4;
       float4 xv[MLC_QMAX];
@@ -321,8 +333,9 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
         for (uint32_t r = 0; r < MLC_CS; ++r) mlc_arrive_remote(&layer_in[0], r);
     }
     bool live = true;
-    for (int l = 0; l < MLC_LAYERS; ++l) {
+    for (int l = P.l0; l < P.l1; ++l) {
       const MlcLayer& L = P.L[l];
+      const int li = l - P.l0;
       const int c0 = (int)rank * L.nc, QPR = L.nc / 4, NQ = 128 * QPR;
       // Before acc_full of this layer every epilogue warp of this CTA finished the previous
       // layer (the input of this one waited for their arrivals): the staging tile (in the
@@ -353,7 +366,7 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
           }
         }
       }
-      if (live) live = __all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)l & 1u) ? 1 : 0) != 0;
+      if (live) live = __all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)li & 1u) ? 1 : 0) != 0;
       if (!live && lane == 0) s_fail = 1;
       tc_fence_after();
       const int nch = (L.nc + 15) / 16;
@@ -434,11 +447,11 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
           }
         }
       }
-      if (l + 1 < MLC_LAYERS) {   // this warp's part of the next layer's input is published
+      if (l + 1 < P.l1) {   // this warp's part of the next layer's input is published
         mlc_publish();
         __syncwarp();
         if (lane == 0)
-          for (uint32_t r = 0; r < MLC_CS; ++r) mlc_arrive_remote(&layer_in[(l + 1) & 1], r);
+          for (uint32_t r = 0; r < MLC_CS; ++r) mlc_arrive_remote(&layer_in[(li + 1) & 1], r);
       }
     }
   }
@@ -449,7 +462,7 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
     tmem_dealloc(tmem, MLC_NCMAX);
   }
   mlc_cluster_sync();   // no CTA leaves while a peer may arrive on its barriers; partial sums visible
-  if (rank == 0 && threadIdx.x < 128) {
+  if (P.q_out && rank == 0 && threadIdx.x < 128) {
     const int row = m0 + threadIdx.x;
     if (row < P.M) {
       const float* p = P.qpart + (size_t)row * MLC_CS;
@@ -481,10 +494,12 @@ static bool mlc_layer(MlcParams& P, int l, const __nv_bfloat16* a, int lda, cons
          ouu_tmap_bf16(&P.w[l], w, (uint64_t)K, (uint64_t)N, (uint64_t)ldw, (uint32_t)L.nc);
 }
 
-ouu_status mlp_cluster_eval(ouu_dino* d, int N) {
+ouu_status mlp_cluster_eval(ouu_dino* d, int N, int l0, int l1) {
   MlcParams P;   // kernel parameters: the launch copies them, so concurrent handles share nothing
   std::memset(&P, 0, sizeof(P));
   P.M = N;
+  P.l0 = l0;
+  P.l1 = l1;
   const int wd = d->wd, rup = (d->ru + 7) / 8 * 8, dzp = (d->dz + 7) / 8 * 8, in0p = d->inp_l[0];
   bool ok = mlc_layer(P, 0, d->X0e, in0p, d->Wb[0], d->inp_l[0], d->in0, wd, MLC_GELU_D);
   ok = ok && mlc_layer(P, 1, d->He0, wd, d->Wb[1], d->inp_l[1], wd, wd, MLC_GELU_D);
@@ -530,7 +545,7 @@ ouu_status mlp_cluster_eval(ouu_dino* d, int N) {
   P.zf = d->d_zf;
   P.x0 = d->X0e;
   P.qpart = d->Qpart;
-  P.q_out = d->Qe;
+  P.q_out = l0 <= 3 && 3 < l1 ? d->Qe : nullptr;
   P.qconst = d->qconst;
   P.err = d->d_err;
   const size_t smem = MLC_SMEM;

@@ -742,19 +742,32 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
   }
 }
 
-void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
-                         double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out,
-                         int wfirst, int wcount) {
-  const int wlo = wcount < 0 ? 0 : wfirst, whi = wcount < 0 ? N : wfirst + wcount;
+void launch_risk_select(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* scratch,
+                        cudaStream_t s, double* grad_out, int n_grad) {
   static_assert(OUU_RISK_SCRATCH >= 3 * OUU_MAX_RISKS + 2 * OUU_MAX_RISKS * RISK_BLOCKS + 1, "risk scratch size");
   double* params = scratch;
   double* part = scratch + 3 * OUU_MAX_RISKS;
   launch_pdl(k_risk_moments, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, part);
   launch_pdl(k_risk_select, dim3(1), dim3(1024), 0, s, q, N, (const double*)part, RISK_BLOCKS, risks_dev, n_risks,
-             params, gq ? grad_out : nullptr, n_risks * dz);
+             params, grad_out, grad_out ? n_grad : 0);
+}
+
+void launch_risk_apply(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
+                       double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out,
+                       int wfirst, int wcount) {
+  const int wlo = wcount < 0 ? 0 : wfirst, whi = wcount < 0 ? N : wfirst + wcount;
+  double* params = scratch;
+  double* part = scratch + 3 * OUU_MAX_RISKS;
   unsigned* arrivals = (unsigned*)(scratch + OUU_RISK_SCRATCH - 1);   // zeroed at problem creation
   launch_pdl(k_risk_apply, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, risks_dev, n_risks, (const double*)params, w,
              part, arrivals, out, gq, ldg, dz, grad_out, wlo, whi);
+}
+
+void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
+                         double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out,
+                         int wfirst, int wcount) {
+  launch_risk_select(q, N, risks_dev, n_risks, scratch, s, gq ? grad_out : nullptr, n_risks * dz);
+  launch_risk_apply(q, N, risks_dev, n_risks, w, out, scratch, s, gq, ldg, dz, grad_out, wfirst, wcount);
 }
 
 // Kernel-level entry used by the risk-weight numerics test (declared in include/ouu_kernels.h).
