@@ -244,7 +244,7 @@ extern "C" ouu_status ouu_create_problem(const ouu_problem_desc* desc, void* cud
   OUU_ALLOC(p->d_risks, sizeof(RiskDev) * OUU_MAX_RISKS);
   OUU_ALLOC(p->d_z, (size_t)p->dz * 8);
   OUU_ALLOC(p->d_rscr, (size_t)OUU_RISK_SCRATCH * 8);
-  OUU_CUDA_TRY(cudaMemset(p->d_rscr, 0, (size_t)OUU_RISK_SCRATCH * 8));   // the block-arrival counter starts at 0
+  OUU_CUDA_TRY(cudaMemset(p->d_rscr, 0, (size_t)OUU_RISK_SCRATCH * 8));
   if (cudaMallocHost((void**)&p->h_out, (size_t)(OUU_MAX_RISKS * (3 + p->dz) + 8) * 8) != cudaSuccess ||
       cudaMallocHost((void**)&p->h_stat, (size_t)N * 4 * 4 + 64) != cudaSuccess) {
     cudaGetLastError();
@@ -432,7 +432,9 @@ ouu_status dino_enqueue_risk(ouu_problem* p, ouu_dino* dino, const double* m_dev
     // network's reverse mode on the main one; joined before the weighted sums
     OUU_CUDA_TRY(cudaEventRecord(dino->ev_fork, dino->stream));
     OUU_CUDA_TRY(cudaStreamWaitEvent(dino->side, dino->ev_fork, 0));
-    launch_risk_select(dino->Qe, n_samples, p->d_risks, n_risks, p->d_rscr, dino->side, d_grad, n_risks * dz);
+    // (the moments from the forward launch's per-tile sums)
+    launch_risk_select(dino->Qe, n_samples, p->d_risks, n_risks, d_res, p->d_rscr, dino->side, d_grad, n_risks * dz,
+                       dino->Qmom, (n_samples + 127) / 128);
     OUU_CUDA_TRY(cudaEventRecord(dino->ev_join, dino->side));
     if (ouu_status st = dino_eval_reverse(dino, n_samples)) return st;
     OUU_CUDA_TRY(cudaStreamWaitEvent(dino->stream, dino->ev_join, 0));
@@ -440,7 +442,7 @@ ouu_status dino_enqueue_risk(ouu_problem* p, ouu_dino* dino, const double* m_dev
   if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[1], dino->stream));
   // weights, risk values and sum_i w_i grad Q_i in one pass over the samples
   if (split)
-    launch_risk_apply(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream, dino->GQe,
+    launch_risk_apply(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, p->d_rscr, dino->stream, dino->GQe,
                       (dz + 7) / 8 * 8, dz, d_grad);
   else
     launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream,

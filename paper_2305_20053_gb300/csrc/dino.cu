@@ -332,7 +332,7 @@ static void free_dino(ouu_dino* d) {
   void* ptrs[] = {d->d_params, d->d_grad, d->d_adam_m, d->d_adam_v, d->d_phi, d->d_phi64, d->d_ubar, d->d_ut,
                   d->d_c, d->d_cf, d->d_wkl, d->d_kl_order, d->X0, d->X0T, d->OUT, d->GO, d->GOT, d->GH, d->GA, d->GAT,
                   d->GAv, d->GA1T, d->d_loss_part, d->d_loss, d->XIe, d->X0e, d->He0, d->He1, d->OUTe,
-                  d->Ge, d->GQe, d->Qe, d->Qpart, d->d_zf, d->d_err, d->d_klp_ctr, d->d_gov, d->d_oscale,
+                  d->Ge, d->GQe, d->Qe, d->Qpart, d->Qmom, d->d_zf, d->d_err, d->d_klp_ctr, d->d_gov, d->d_oscale,
                   d->d_klbias, d->d_dec_b, d->d_dec_a, d->d_ubarf, d->d_utf, d->d_qdec};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < 4; ++l) {
@@ -469,10 +469,15 @@ extern "C" ouu_status ouu_dino_create(const ouu_dino_desc* desc, void* cuda_stre
   al((void**)&d->GQe, E * dzp * 4);
   al((void**)&d->Qe, E * 8);
   al((void**)&d->Qpart, E * 4 * 4);
+  al((void**)&d->Qmom, (E / 128 + 1) * 2 * 8);
   al((void**)&d->d_zf, std::max<size_t>(maxB, 1) * d->dz * 4 + 64);
   al((void**)&d->d_err, 16);
   al((void**)&d->d_klp_ctr, (OUU_KLP_MAX_TILES + 1) * sizeof(int));   // zeroed by al()
   if (ok && cudaMallocHost((void**)&d->h_pin, (size_t)(4 * 3 + 4 * d->dz + 64) * 8 + 4096) != cudaSuccess) ok = false;
+  if (ok && cudaHostGetDevicePointer((void**)&d->h_pin_dev, d->h_pin, 0) != cudaSuccess) {
+    d->h_pin_dev = nullptr;   // not mapped: the controls then go by a copy
+    cudaGetLastError();
+  }
   if (!ok) {
     cudaGetLastError();
     free_dino(d);
@@ -696,12 +701,14 @@ static ouu_status check_err(ouu_dino* d) {
 }
 
 // KL coordinates of `count` fields (chunked BF16 cast + tensor-core projection).
-// With mark, events ev[0] / ev[1] / ev[2] bracket the first chunk's cast and GEMM.
-static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi, bool mark = false) {
+// With mark, events ev[0] / ev[1] / ev[2] bracket the first chunk's cast and GEMM.  With
+// zstage, the projection launch also stages the controls (d_zf) from the mapped pinned buffer.
+static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi, bool mark = false,
+                                 bool zstage = false) {
   // one fused pass over the FP64 fields (kl_project.cu); the bias -W mbar carries the prior mean
   if (mark && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
   DINO_TRY(ouu_kl_project(m, count, d->nn, d->d_wkl, d->nnp, d->rm, d->d_klbias, xi, d->d_err, d->d_klp_ctr,
-                          d->num_sms, d->stream));
+                          d->num_sms, d->stream, zstage ? d->h_pin_dev : nullptr, d->d_zf, d->dz));
   if (mark && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
   return OUU_OK;
 }
@@ -888,13 +895,16 @@ extern "C" ouu_status ouu_dino_loss_grad(ouu_dino_t d, const float* xi_dev, cons
 // grad_z Q in GQe by reverse mode: seed phi + c through W3^T, GELU', ... , W0z^T.
 static ouu_status dino_network(ouu_dino* d, int N, bool want_grad);
 
-// The controls to the device and the projection of the fields into XIe.
-static ouu_status dino_eval_inputs(ouu_dino* d, const double* m_dev, int N, const double* z_host) {
+// The controls to the device and the projection of the fields into XIe.  With zstage (and the
+// pinned buffer mapped), the projection launch carries the controls over from the pinned
+// buffer instead of a copy ahead of it.
+static ouu_status dino_eval_inputs(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool zstage = false) {
   ++d->eval_count;   // the per-sample buffers now belong to this evaluation
   float* zh = (float*)d->h_pin;
   for (int j = 0; j < d->dz; ++j) zh[j] = (float)z_host[j];
-  OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)d->dz * 4, cudaMemcpyHostToDevice, d->stream));
-  DINO_TRY(project_fields(d, m_dev, N, d->XIe, true));
+  zstage = zstage && d->h_pin_dev;
+  if (!zstage) OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)d->dz * 4, cudaMemcpyHostToDevice, d->stream));
+  DINO_TRY(project_fields(d, m_dev, N, d->XIe, true, zstage));
   return OUU_OK;
 }
 
@@ -906,7 +916,7 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
 ouu_status dino_eval_forward(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool* split) {
   *split = d->fused_mlp == 2 && mlp_cluster_fits(d);
   if (!*split) return dino_eval_core(d, m_dev, N, z_host, true);
-  DINO_TRY(dino_eval_inputs(d, m_dev, N, z_host));
+  DINO_TRY(dino_eval_inputs(d, m_dev, N, z_host, true));
   DINO_TRY(mlp_cluster_eval(d, N, 0, 4));
   OUU_CUDA_TRY(cudaGetLastError());
   return OUU_OK;

@@ -65,8 +65,10 @@ struct ouu_dino {
   float* GQe = nullptr;            // [maxE][dz]
   double* Qe = nullptr;            // [maxE]
   float* Qpart = nullptr;          // [maxE][4] per-CTA partial QoI sums of the cluster network
+  double* Qmom = nullptr;          // [maxE / 128 + 1][2] per-tile sum Q, sum Q^2 of the cluster network
   float* d_zf = nullptr;           // [max(maxB, 1) * dz] FP32 controls of the current call
   double* h_pin = nullptr;         // pinned host scratch
+  const float* h_pin_dev = nullptr;   // h_pin as the device addresses it (mapped), or null
   int* d_err = nullptr;
   int* d_klp_ctr = nullptr;        // [OUU_KLP_MAX_TILES] tile counters of the KL projection
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // cast | projection | network phase marks
@@ -138,8 +140,11 @@ ouu_status dino_install_bases(ouu_dino* d);
 // unit counters and an arrival count; each launch leaves them zero); N above
 // OUU_KLP_MAX_TILES * 128 runs as several launches.
 #define OUU_KLP_MAX_TILES 512
+// zsrc / zdst / nz: the launch also copies nz floats from zsrc (device-addressable, e.g. mapped
+// pinned host memory) to zdst, for work that follows it in the stream (the network's controls).
 ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W, int ldw, int rm, const float* bias,
-                          float* xi, int* err, int* ctr, int num_sms, cudaStream_t s);
+                          float* xi, int* err, int* ctr, int num_sms, cudaStream_t s, const float* zsrc = nullptr,
+                          float* zdst = nullptr, int nz = 0);
 
 // route 0: forward (d_Z solves per sample), 1: adjoint (r_u solves per sample).
 void launch_pde_jacobian_data(const PdeArgs& a, int nslots, const float* phi, int ru, float* jy, int route,

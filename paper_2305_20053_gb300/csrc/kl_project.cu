@@ -63,6 +63,9 @@ struct KlpArgs {
   const float* bias;
   float* xi;
   int* err;
+  const float* zsrc;   // nz floats copied to zdst by block 0 (a rider for the work that follows)
+  float* zdst;
+  int nz;
 };
 
 // FP64 -> FP32, rounding to nearest even, in integer arithmetic on the two halves of the
@@ -427,6 +430,8 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
   } else {
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;
+    if (blockIdx.x == 0)   // idle until the first tile visit completes
+      for (int i = threadIdx.x - KLP_EPI_WARP0 * 32; i < a.nz; i += 4 * 32) a.zdst[i] = a.zsrc[i];
     for (int k = 0;; ++k) {
       const int acc = k & 1;
       const uint32_t ph = (uint32_t)(k >> 1) & 1u;
@@ -525,7 +530,8 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
 
 // One launch over N <= OUU_KLP_MAX_TILES * 128 samples.
 static ouu_status kl_project_launch(const double* m, int N, int nn, const CUtensorMap& tw, int BN, int rm,
-                                    const float* bias, float* xi, int* err, int* ctr, int num_sms, cudaStream_t s) {
+                                    const float* bias, float* xi, int* err, int* ctr, int num_sms, cudaStream_t s,
+                                    const float* zsrc, float* zdst, int nz) {
   // fields tensor map: sample rows (n^2 even) or sample pairs (n^2 odd)
   // A base that is not 16-byte aligned (a slice starting at an odd sample) cannot be a
   // tensor map's base: every row then goes by plain loads.
@@ -559,6 +565,9 @@ static ouu_status kl_project_launch(const double* m, int N, int nn, const CUtens
   a.bias = bias;
   a.xi = xi;
   a.err = err;
+  a.zsrc = zsrc;
+  a.zdst = zdst;
+  a.nz = zsrc && zdst ? nz : 0;
   const size_t smem = 1024 + 2 * KLP_A_STAGE + 2 * (size_t)BN * 128 + 2 * KLP_F64_STAGE + 17 * 8 + 16;
   OUU_CUDA_TRY(ouu_smem_limit((const void*)k_kl_project, smem));
   const long long U = (long long)a.T * a.KBt;
@@ -569,7 +578,8 @@ static ouu_status kl_project_launch(const double* m, int N, int nn, const CUtens
 }
 
 ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W, int ldw, int rm, const float* bias,
-                          float* xi, int* err, int* ctr, int num_sms, cudaStream_t s) {
+                          float* xi, int* err, int* ctr, int num_sms, cudaStream_t s, const float* zsrc, float* zdst,
+                          int nz) {
   OUU_CHECK_ARG(m && W && bias && xi && err && ctr, "null argument");
   OUU_CHECK_ARG(N >= 1 && nn >= 1 && rm >= 1 && rm <= 240, "KL projection sizes: N, n^2 >= 1, 1 <= r_m <= 240");
   OUU_CHECK_ARG(((uintptr_t)m & 7) == 0, "fields must be 8-byte aligned");
@@ -586,7 +596,7 @@ ouu_status ouu_kl_project(const double* m, int N, int nn, const __nv_bfloat16* W
   for (int n0 = 0; n0 < N; n0 += chunk) {
     const int nc = std::min(chunk, N - n0);
     if (ouu_status st = kl_project_launch(m + (size_t)n0 * nn, nc, nn, tw, BN, rm, bias, xi + (size_t)n0 * rm, err,
-                                          ctr, num_sms, s))
+                                          ctr, num_sms, s, n0 == 0 ? zsrc : nullptr, zdst, nz))
       return st;
   }
   return OUU_OK;

@@ -78,6 +78,7 @@ struct MlcParams {
   __nv_bfloat16* x0;            // [M][in0p] layer-0 input, built here
   float* qpart;                 // [M][4] per-CTA partial sums of (phi + c)^2
   double* q_out;                // [M]; null when the QoI layer is not in [l0, l1)
+  double* q_mom;                // with q_out: [tiles][2] the tile's sum Q and sum Q^2 (FP64)
   double qconst;
   int* err;
 };
@@ -190,6 +191,21 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
     const int ll = lane < MLC_LAYERS ? lane : lane - MLC_LAYERS;
     if (ll >= P.l0 && ll < P.l1) tmap_prefetch(lane < MLC_LAYERS ? &P.a[ll] : &P.w[ll]);
   }
+  // The first layer's weights do not come from earlier kernels: their copies start before the
+  // wait on those kernels (the ring's first stages, free at launch).
+  int wpre = 0;
+  {
+    const MlcLayer& L = P.L[P.l0];
+    wpre = min((L.K + 63) / 64, MLC_STAGES);
+  }
+  __syncthreads();   // the barriers are initialised
+  if (warp == MLC_PROD_WARP && lane == 0) {
+    const MlcLayer& L = P.L[P.l0];
+    for (int kb = 0; kb < wpre; ++kb) {
+      mbar_expect_tx(&w_full[kb], (uint32_t)L.nc * 128u);
+      tma_load_2d(sW + kb * MLC_W_BYTES, &P.w[P.l0], kb * 64, (int)rank * L.nc, &w_full[kb]);
+    }
+  }
   pdl_wait();
   tc_fence_before();
   __syncthreads();
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
   if (warp == MLC_PROD_WARP) {
     // ------------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      int gw = 0, wissued = 0;
+      int gw = 0, wissued = wpre;
       int a_uses[MLC_KBMAX];
 #pragma unroll
       for (int i = 0; i < MLC_KBMAX; ++i) a_uses[i] = 0;
@@ -218,7 +234,7 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
           wissued = f + 1;
           return true;
         };
-        for (int kb = 0; kb < pre && ok; ++kb) ok = load_w(kb);   // ahead of the layer's input
+        for (int kb = l == P.l0 ? wpre : 0; kb < pre && ok; ++kb) ok = load_w(kb);   // ahead of the layer's input
         if (!ok) break;
         // the layer's input is complete in every CTA of the cluster; on a timeout the input is
         // still loaded, so that every barrier armed here completes before the CTA exits
@@ -464,9 +480,28 @@ __global__ void __launch_bounds__(MLC_THREADS, 1) k_mlp_cluster(const __grid_con
   mlc_cluster_sync();   // no CTA leaves while a peer may arrive on its barriers; partial sums visible
   if (P.q_out && rank == 0 && threadIdx.x < 128) {
     const int row = m0 + threadIdx.x;
+    double qv = 0.0;
     if (row < P.M) {
       const float* p = P.qpart + (size_t)row * MLC_CS;
-      P.q_out[row] = P.qconst + 0.5 * (double)(((p[0] + p[1]) + p[2]) + p[3]);
+      qv = P.qconst + 0.5 * (double)(((p[0] + p[1]) + p[2]) + p[3]);
+      P.q_out[row] = qv;
+    }
+    // the tile's moments for the risk passes (the four warps' shuffle sums, then warp 0)
+    double s1 = qv, s2 = qv * qv;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    double* red = reinterpret_cast<double*>(smem);   // the input blocks are idle now
+    if (lane == 0) {
+      red[2 * warp] = s1;
+      red[2 * warp + 1] = s2;
+    }
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+    if (threadIdx.x == 0) {
+      P.q_mom[2 * (m0 / 128)] = (red[0] + red[2]) + (red[4] + red[6]);
+      P.q_mom[2 * (m0 / 128) + 1] = (red[1] + red[3]) + (red[5] + red[7]);
     }
   }
   if (threadIdx.x == 0 && s_fail) atomicExch(P.err, 1);
@@ -546,6 +581,7 @@ ouu_status mlp_cluster_eval(ouu_dino* d, int N, int l0, int l1) {
   P.x0 = d->X0e;
   P.qpart = d->Qpart;
   P.q_out = l0 <= 3 && 3 < l1 ? d->Qe : nullptr;
+  P.q_mom = d->Qmom;
   P.qconst = d->qconst;
   P.err = d->d_err;
   const size_t smem = MLC_SMEM;

@@ -199,15 +199,18 @@ inline void risk_dev_finish(RiskDev& r, int N) {
 void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
                          double* scratch, cudaStream_t s, const float* gq = nullptr, int ldg = 0, int dz = 0,
                          double* grad_out = nullptr, int wfirst = 0, int wcount = -1);
-// launch_risk_weights as its two stream-ordered parts: launch_risk_select (moments and t*,
-// reading only q; zeroes grad_out [n_grad] for the sums to come) and launch_risk_apply
-// (weights, risk values and weighted gradient sums), with the same scratch.  Work that touches
-// neither q nor the scratch may run between them, on another stream.
-void launch_risk_select(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* scratch,
-                        cudaStream_t s, double* grad_out, int n_grad);
-void launch_risk_apply(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
-                       double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out,
-                       int wfirst = 0, int wcount = -1);
+// launch_risk_weights as its two stream-ordered parts: launch_risk_select (moments, t* and
+// the risk values into out, reading only q; zeroes grad_out [n_grad] for the sums to come) and
+// launch_risk_apply (weights and weighted gradient sums), with the same scratch.  Work that
+// touches neither q, out nor the scratch may run between them, on another stream.  mom_part
+// [mom_n][2] (sum Q, sum Q^2 over disjoint parts of the samples), when given, stands in for
+// the moments pass.
+void launch_risk_select(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* out,
+                        double* scratch, cudaStream_t s, double* grad_out, int n_grad,
+                        const double* mom_part = nullptr, int mom_n = 0);
+void launch_risk_apply(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* scratch,
+                       cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out, int wfirst = 0,
+                       int wcount = -1);
 
 // ------------------------------------------------------------------ fields
 void launch_sample_fields(int n, uint64_t seed, int64_t first, int count, const double* invlam,

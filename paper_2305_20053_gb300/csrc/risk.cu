@@ -333,6 +333,89 @@ static __device__ double kth_largest_prefix(const double* q, int N, int k, const
   return cand[sel[0]];
 }
 
+// sum_i s_eps(Q_i - t) and sum_i s'_eps(Q_i - t) over the N samples; every thread gets both.
+// Only samples above t contribute.  With the key prefixes in registers (N <= 16 blockDim.x),
+// the samples whose prefix is not below t's (the contributors and a few more) are gathered
+// into list (in thread order, through a block-wide scan of their counts) and warp 0 alone
+// does the FP64 arithmetic: a warp instruction holds GB300's narrow FP64 pipe whatever its
+// number of active lanes, so FP64 work spread thinly over every warp would cost a pass of
+// the pipe per warp.  More than lmax of them, or no prefixes: every thread takes its own
+// samples and the sums go to warp 0 through list (2 blockDim.x + 2 doubles).  Fixed
+// summation order either way.
+static __device__ void cvar_sums(const double* q, int N, bool prefix_path, const uint32_t (&kr)[KEYS_PER_THREAD],
+                                 double t, double eps, double inv_eps, double* list, int lmax, int* wtot,
+                                 double* res, double& s, double& d) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  s = 0.0;
+  d = 0.0;
+  if (prefix_path) {
+    const uint32_t tp = (uint32_t)(dkey(t) >> 32);
+    uint32_t mask = 0;
+#pragma unroll
+    for (int j = 0; j < KEYS_PER_THREAD; ++j) {
+      const int i = j * blockDim.x + threadIdx.x;
+      if (i < N && kr[j] >= tp) mask |= 1u << j;
+    }
+    const int c = __popc(mask);
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) wtot[warp] = inc;
+    __syncthreads();
+    int base = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int v = wtot[w];
+      base += w < warp ? v : 0;
+      total += v;
+    }
+    if (total <= lmax) {
+      int pos = base + inc - c;
+#pragma unroll
+      for (int j = 0; j < KEYS_PER_THREAD; ++j)
+        if ((mask >> j) & 1u) list[pos++] = q[j * blockDim.x + threadIdx.x];
+      __syncthreads();
+      if (warp == 0) {
+        for (int k = lane; k < total; k += 32) {
+          const double x = list[k] - t;
+          s += splus(x, eps, inv_eps);
+          d += splus_d1(x, eps, inv_eps);
+        }
+        const int act = total < 32 ? total : 32;
+        s = warp_sum_active(s, act);
+        d = warp_sum_active(d, act);
+        if (lane == 0) {
+          res[0] = s;
+          res[1] = d;
+        }
+      }
+      __syncthreads();
+      s = res[0];
+      d = res[1];
+      __syncthreads();   // list, wtot and res may be reused at once
+      return;
+    }
+#pragma unroll
+    for (int j = 0; j < KEYS_PER_THREAD; ++j)
+      if ((mask >> j) & 1u) {
+        const double x = q[j * blockDim.x + threadIdx.x] - t;
+        s += splus(x, eps, inv_eps);
+        d += splus_d1(x, eps, inv_eps);
+      }
+  } else {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const double x = q[i] - t;
+      if (x > 0.0) {
+        s += splus(x, eps, inv_eps);
+        d += splus_d1(x, eps, inv_eps);
+      }
+    }
+  }
+  block_sum2(s, d, list, blockDim.x);
+}
+
 // Pass 2 (one CTA): moments and, per CVaR risk, t* = argmin_t rho(z, t).
 // With K = N (1 - beta), k0 = floor(K) and v the (k0 + 1)-th largest QoI (the N-th
 // when k0 = N), the root of d rho/dt = 1 - S(t)/K, S(t) = sum_i s'_eps(Q_i - t), lies
@@ -346,14 +429,16 @@ static __device__ double kth_largest_prefix(const double* q, int N, int k, const
 // [min Q - eps, max Q]: lo if d rho/dt(lo) >= 0, else hi.  Every FP64 instruction occupies
 // GB300's narrow FP64 pipe for a whole warp, so the FP64 work stays on one warp and the
 // block-wide parts are integer.  params[r] = {t, mean, var}.
+// Then the risk values from all N samples: out[3r..3r+2] = value, d rho / dt, t (mean +
+// variance: Qbar + kappa var, 0, 0; CVaR: t + sum s_eps / K, 1 - sum s'_eps / K, t).
 __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restrict__ q, int N, const double* __restrict__ part, int nparts,
                               const RiskDev* __restrict__ risks, int n_risks, double* __restrict__ params,
-                              double* __restrict__ zero_out, int n_zero) {
+                              double* __restrict__ out, double* __restrict__ zero_out, int n_zero) {
   __shared__ unsigned hist[2048];
   __shared__ unsigned sel[2 + 64 + 1];
   __shared__ double cand[32];
   __shared__ int ncand;
-  __shared__ double win[RISK_WINDOW_MAX];
+  __shared__ double win[RISK_WINDOW_MAX + 2];   // also the buffer of the value sums (2 x 1024 + 2)
   __shared__ float winf[RISK_WINDOW_MAX];
   __shared__ int nwin, s_above;
   __shared__ double s_par[6];   // qbar, var, -, v + eps, v - eps, t
@@ -570,23 +655,32 @@ __global__ void __launch_bounds__(1024, 1) k_risk_select(const double* __restric
         t = cvar_dt(br, q, N, lo, R.beta, eps) >= 0.0 ? lo : hi;
       }
     }
+    double val = qbar + R.kappa * var, dt = 0.0, tout = 0.0;
+    if (R.kind == OUU_RISK_CVAR_SMOOTH) {
+      double ssum, dsum;
+      cvar_sums(q, N, prefix_path, kr, t, R.eps, R.inv_eps, win, RISK_WINDOW_MAX, (int*)sel, red, ssum, dsum);
+      val = t + ssum * R.inv_K;
+      dt = 1.0 - dsum * R.inv_K;
+      tout = t;
+    }
     if (threadIdx.x == 0) {
       params[3 * r + 0] = t;
       params[3 * r + 1] = qbar;
       params[3 * r + 2] = var;
+      out[3 * r + 0] = val;
+      out[3 * r + 1] = dt;
+      out[3 * r + 2] = tout;
     }
     __syncthreads();
   }
 }
 
-// Pass 3 (many CTAs, each a contiguous range of samples): weights w[r][i] and per-block
-// partial sums of s_eps and s'_eps; with per-sample gradients gq [N][ldg] (FP32), also
-// grad_out[r][j] += sum_i w[r][i] gq[i][j] (per-block FP64 sums added atomically; the
-// select pass zeroed grad_out).  The products and the per-thread sums run in float-float
-// arithmetic: w = wh + wl (two FP32), wh g split exactly by an FMA, sums by the error-free
-// two-sum, so each thread's total carries about 44 bits and only the totals are FP64.
-// The last block to finish (an arrival counter, reset for the next call) combines the
-// partial sums into the risk values and d rho / dt.  out[3r..3r+2] = value, dt, t.
+// Pass 3 (many CTAs, each a contiguous range of samples): weights w[r][i]; with per-sample
+// gradients gq [N][ldg] (FP32), also grad_out[r][j] += sum_i w[r][i] gq[i][j] (per-block
+// FP64 sums added atomically; the select pass zeroed grad_out).  The products and the
+// per-thread sums run in float-float arithmetic: w = wh + wl (two FP32), wh g split exactly
+// by an FMA, sums by the error-free two-sum, so each thread's total carries about 44 bits
+// and only the totals are FP64.
 #define APPLY_W 256   // samples of a block whose weights sit in shared memory at a time
 static __device__ __forceinline__ void ff_add_prod(float& sh, float& sl, float wh, float wl, float g) {
   const float p = wh * g;
@@ -614,20 +708,14 @@ static __device__ __forceinline__ void load_grad_group(float (&gv)[16], const fl
 __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q, int N,
                                                     const RiskDev* __restrict__ risks, int n_risks,
                                                     const double* __restrict__ params, double* __restrict__ w,
-                                                    double* __restrict__ part, unsigned* __restrict__ arrivals,
-                                                    double* __restrict__ out, const float* __restrict__ gq, int ldg,
-                                                    int dz, double* __restrict__ grad_out, int wlo, int whi) {
-  __shared__ bool last;
+                                                    const float* __restrict__ gq, int ldg, int dz,
+                                                    double* __restrict__ grad_out, int wlo, int whi) {
   __shared__ float wsh[OUU_MAX_RISKS][APPLY_W], wsl[OUU_MAX_RISKS][APPLY_W];
   __shared__ double gsum[OUU_MAX_RISKS][128];
-  __shared__ double buf[2 * 256 + 2];
   pdl_wait();
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int i0 = min(N, (int)blockIdx.x * chunk), i1 = min(N, i0 + chunk);
   const int g = threadIdx.x >> 7, jl = threadIdx.x & 127;   // two sample parities x 128 columns
-  double sv[OUU_MAX_RISKS], sd[OUU_MAX_RISKS];
-#pragma unroll
-  for (int r = 0; r < OUU_MAX_RISKS; ++r) sv[r] = sd[r] = 0.0;
   for (int s0 = i0; s0 < i1; s0 += APPLY_W) {
     const int s1 = min(i1, s0 + APPLY_W), ns = s1 - s0;
     const bool gsub = gq && s1 > wlo && s0 < whi;   // uniform over the block
@@ -645,11 +733,7 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
         if (R.kind == OUU_RISK_MEAN_VAR) {
           wi = (1.0 + 2.0 * R.kappa * (qi - qbar)) * R.inv_N;
         } else {
-          const double x = qi - t;
-          const double d1 = splus_d1(x, R.eps, R.inv_eps);
-          wi = d1 * R.inv_K;
-          sv[r] += splus(x, R.eps, R.inv_eps);
-          sd[r] += d1;
+          wi = splus_d1(qi - t, R.eps, R.inv_eps) * R.inv_K;
         }
         if (i >= wlo && i < whi) w[(int64_t)r * (whi - wlo) + (i - wlo)] = wi;
         if (gsub) {
@@ -690,84 +774,38 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
       }
     }
   }
-  // threads that held samples: [0, min(range, APPLY_W))
-  const int nact = min(i1 - i0, APPLY_W);
-#pragma unroll
-  for (int r = 0; r < OUU_MAX_RISKS; ++r) {
-    if (r >= n_risks) break;
-    if (risks[r].kind == OUU_RISK_MEAN_VAR) continue;
-    double tv = sv[r], td = sd[r];
-    if (nact > 0) block_sum2(tv, td, buf, nact);
-    if (threadIdx.x == 0) {
-      part[(2 * r) * gridDim.x + blockIdx.x] = nact > 0 ? tv : 0.0;
-      part[(2 * r + 1) * gridDim.x + blockIdx.x] = nact > 0 ? td : 0.0;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(arrivals, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x < 32) {
-    for (int r = 0; r < n_risks; ++r) {
-      const RiskDev R = risks[r];
-      const double t = params[3 * r], qbar = params[3 * r + 1], var = params[3 * r + 2];
-      if (R.kind == OUU_RISK_MEAN_VAR) {
-        if (lane == 0) {
-          out[3 * r + 0] = qbar + R.kappa * var;
-          out[3 * r + 1] = 0.0;
-          out[3 * r + 2] = 0.0;
-        }
-        continue;
-      }
-      double a = 0.0, b = 0.0;
-      for (int i = lane; i < (int)gridDim.x; i += 32) {
-        a += __ldcg(&part[(2 * r) * gridDim.x + i]);
-        b += __ldcg(&part[(2 * r + 1) * gridDim.x + i]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-      }
-      if (lane == 0) {
-        out[3 * r + 0] = t + a * R.inv_K;
-        out[3 * r + 1] = 1.0 - b * R.inv_K;
-        out[3 * r + 2] = t;
-      }
-    }
-    if (lane == 0) *arrivals = 0u;
-  }
 }
 
-void launch_risk_select(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* scratch,
-                        cudaStream_t s, double* grad_out, int n_grad) {
-  static_assert(OUU_RISK_SCRATCH >= 3 * OUU_MAX_RISKS + 2 * OUU_MAX_RISKS * RISK_BLOCKS + 1, "risk scratch size");
+void launch_risk_select(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* out,
+                        double* scratch, cudaStream_t s, double* grad_out, int n_grad, const double* mom_part,
+                        int mom_n) {
+  static_assert(OUU_RISK_SCRATCH >= 3 * OUU_MAX_RISKS + 2 * RISK_BLOCKS, "risk scratch size");
   double* params = scratch;
-  double* part = scratch + 3 * OUU_MAX_RISKS;
-  launch_pdl(k_risk_moments, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, part);
-  launch_pdl(k_risk_select, dim3(1), dim3(1024), 0, s, q, N, (const double*)part, RISK_BLOCKS, risks_dev, n_risks,
-             params, grad_out, grad_out ? n_grad : 0);
+  const double* part = mom_part;
+  int nparts = mom_n;
+  if (!mom_part) {
+    double* p = scratch + 3 * OUU_MAX_RISKS;
+    launch_pdl(k_risk_moments, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, p);
+    part = p;
+    nparts = RISK_BLOCKS;
+  }
+  launch_pdl(k_risk_select, dim3(1), dim3(1024), 0, s, q, N, part, nparts, risks_dev, n_risks, params, out, grad_out,
+             grad_out ? n_grad : 0);
 }
 
-void launch_risk_apply(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
-                       double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out,
-                       int wfirst, int wcount) {
+void launch_risk_apply(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* scratch,
+                       cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out, int wfirst, int wcount) {
   const int wlo = wcount < 0 ? 0 : wfirst, whi = wcount < 0 ? N : wfirst + wcount;
-  double* params = scratch;
-  double* part = scratch + 3 * OUU_MAX_RISKS;
-  unsigned* arrivals = (unsigned*)(scratch + OUU_RISK_SCRATCH - 1);   // zeroed at problem creation
-  launch_pdl(k_risk_apply, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, risks_dev, n_risks, (const double*)params, w,
-             part, arrivals, out, gq, ldg, dz, grad_out, wlo, whi);
+  const double* params = scratch;
+  launch_pdl(k_risk_apply, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, risks_dev, n_risks, params, w, gq, ldg, dz,
+             grad_out, wlo, whi);
 }
 
 void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
                          double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out,
                          int wfirst, int wcount) {
-  launch_risk_select(q, N, risks_dev, n_risks, scratch, s, gq ? grad_out : nullptr, n_risks * dz);
-  launch_risk_apply(q, N, risks_dev, n_risks, w, out, scratch, s, gq, ldg, dz, grad_out, wfirst, wcount);
+  launch_risk_select(q, N, risks_dev, n_risks, out, scratch, s, gq ? grad_out : nullptr, n_risks * dz);
+  launch_risk_apply(q, N, risks_dev, n_risks, w, scratch, s, gq, ldg, dz, grad_out, wfirst, wcount);
 }
 
 // Kernel-level entry used by the risk-weight numerics test (declared in include/ouu_kernels.h).
