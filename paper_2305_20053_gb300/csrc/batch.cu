@@ -382,7 +382,7 @@ extern "C" ouu_status ouu_batch_run(ouu_batch_t b, const double* const* z_hosts,
     ouu_problem* p = e.it.problem;
     const int dz = p->dz;
     if (e.it.backend == OUU_BACKEND_DINO) {
-      if (p->h_stat[0]) {
+      if (p->h_out[OUU_OUT_FLAG(dz)] != 0.0) {
         cudaMemsetAsync(e.it.dino->d_err, 0, 4, b->stream);
         ouu_set_error("tensor-core GEMM pipeline wait timed out");
         return OUU_ERR_CUDA;

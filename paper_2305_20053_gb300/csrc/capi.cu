@@ -443,14 +443,14 @@ ouu_status dino_enqueue_risk(ouu_problem* p, ouu_dino* dino, const double* m_dev
   // weights, risk values and sum_i w_i grad Q_i in one pass over the samples
   if (split)
     launch_risk_apply(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, p->d_rscr, dino->stream, dino->GQe,
-                      (dz + 7) / 8 * 8, dz, d_grad);
+                      (dz + 7) / 8 * 8, dz, d_grad, 0, -1, dino->d_err, p->d_out + OUU_OUT_FLAG(dz));
   else
     launch_risk_weights(dino->Qe, n_samples, p->d_risks, n_risks, p->d_w, d_res, p->d_rscr, dino->stream,
-                        dino->GQe, (dz + 7) / 8 * 8, dz, d_grad);
+                        dino->GQe, (dz + 7) / 8 * 8, dz, d_grad, 0, -1, dino->d_err, p->d_out + OUU_OUT_FLAG(dz));
   if (!dino->capturing) OUU_CUDA_TRY(cudaEventRecord(p->ev[2], dino->stream));
   OUU_CUDA_TRY(cudaGetLastError());
+  // one read-back: the results and (in them) the network's status flag
   OUU_CUDA_TRY(cudaMemcpyAsync(p->h_out, p->d_out, ob, cudaMemcpyDeviceToHost, dino->stream));
-  OUU_CUDA_TRY(cudaMemcpyAsync(p->h_stat, dino->d_err, 4, cudaMemcpyDeviceToHost, dino->stream));
   return OUU_OK;
 }
 
@@ -536,7 +536,7 @@ static ouu_status risk_and_grad_on(ouu_problem_t p, ouu_backend backend, ouu_din
     }
     OUU_CUDA_TRY(cudaEventRecord(p->ev[3], ds));
     OUU_CUDA_TRY(cudaStreamSynchronize(ds));
-    if (p->h_stat[0]) {
+    if (p->h_out[OUU_OUT_FLAG(dz)] != 0.0) {
       cudaMemsetAsync(dino->d_err, 0, 4, ds);
       // an interrupted projection may have left its tile counters non-zero
       cudaMemsetAsync(dino->d_klp_ctr, 0, (OUU_KLP_MAX_TILES + 1) * sizeof(int), ds);

@@ -26,7 +26,9 @@
 //   warp 17      : tcgen05.mma issuer (M = 128, N = BN, K = 16 per instruction) into one of
 //                  two TMEM accumulators (one per tile visit); allocates and frees the tensor
 //                  memory; hands each visit's (tile, holds K block 0, final) to the epilogue.
-//   warps 18..21 : epilogue.  TMEM -> registers, + bias on the visit that holds K block 0 of
+//   warps 18..25 : epilogue, two groups of four (one per TMEM accumulator, so visits alternate
+//                  between them and the final visit's flush need not wait for the previous
+//                  visit's).  TMEM -> registers, + bias on the visit that holds K block 0 of
 //                  its tile, 16-byte atomic adds into xi (zeroed beforehand); the CTA's final
 //                  visit (when every CTA flushes at once) goes through the idle FP64 stages
 //                  and TMA bulk reductions of whole rows instead.
@@ -43,7 +45,8 @@
 #define KLP_PROD_WARP 16
 #define KLP_MMA_WARP 17
 #define KLP_EPI_WARP0 18
-#define KLP_THREADS (22 * 32)
+#define KLP_EPI_GROUPS 2
+#define KLP_THREADS ((KLP_EPI_WARP0 + 4 * KLP_EPI_GROUPS) * 32)
 #define KLP_RING 16                          // published units (the MMA lags the producer by < 8)
 #define KLP_ROWS_PER_WARP (128 / KLP_CONV_WARPS)
 #define KLP_ROW_BYTES 528                    // pair mode: 66 doubles per sample row
@@ -416,11 +419,14 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
         }
       }
       if (!ok) s_fail = 1;
-      // the end of the visits, in the slot whose last descriptor the epilogue has read
-      const int acc = seg & 1;
-      if (seg >= 2 && !mbar_wait(&acc_empty[acc], (uint32_t)((seg >> 1) - 1) & 1u)) s_fail = 1;
-      s_seg[acc] = make_int2(-1, 0);
-      mbar_arrive(&seg_full[acc]);
+      // the end of the visits, in both slots (one per epilogue group), each once its group has
+      // read the slot's last descriptor (visit k used slot k & 1; slot a holds (seg - a + 1) / 2)
+      for (int sl = 0; sl < 2; ++sl) {
+        const int acc = (seg + sl) & 1, na = (seg - acc + 1) / 2;
+        if (na >= 1 && !mbar_wait(&acc_empty[acc], (uint32_t)(na - 1) & 1u)) s_fail = 1;
+        s_seg[acc] = make_int2(-1, 0);
+        mbar_arrive(&seg_full[acc]);
+      }
       // every MMA issued above has completed before the tensor memory is freed
       if (any) {
         tc_commit(mma_done);
@@ -429,10 +435,10 @@ __global__ void __launch_bounds__(KLP_THREADS, 1) k_kl_project(const __grid_cons
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int q = warp & 3;
+    const int q = warp & 3, grp = (warp - KLP_EPI_WARP0) >> 2;
     if (blockIdx.x == 0)   // idle until the first tile visit completes
-      for (int i = threadIdx.x - KLP_EPI_WARP0 * 32; i < a.nz; i += 4 * 32) a.zdst[i] = a.zsrc[i];
-    for (int k = 0;; ++k) {
+      for (int i = threadIdx.x - KLP_EPI_WARP0 * 32; i < a.nz; i += 4 * KLP_EPI_GROUPS * 32) a.zdst[i] = a.zsrc[i];
+    for (int k = grp;; k += KLP_EPI_GROUPS) {   // this group's visits: accumulator grp
       const int acc = k & 1;
       const uint32_t ph = (uint32_t)(k >> 1) & 1u;
       if (!__all_sync(0xffffffffu, mbar_wait(&seg_full[acc], ph) ? 1 : 0)) {

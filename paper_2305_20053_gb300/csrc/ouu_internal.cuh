@@ -196,9 +196,13 @@ inline void risk_dev_finish(RiskDev& r, int N) {
 // still come from all N QoIs.  wcount < 0: the whole set.
 // scratch: OUU_RISK_SCRATCH doubles of device memory.
 #define OUU_RISK_SCRATCH 2048
+// The results block d_out of a problem: [OUU_MAX_RISKS][3] values, [OUU_MAX_RISKS][d_Z] gradients,
+// then 8 doubles: the plain path's solved-sample count (an int) and the network's status flag.
+#define OUU_OUT_FLAG(dz) (OUU_MAX_RISKS * (3 + (dz)) + 1)
 void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
                          double* scratch, cudaStream_t s, const float* gq = nullptr, int ldg = 0, int dz = 0,
-                         double* grad_out = nullptr, int wfirst = 0, int wcount = -1);
+                         double* grad_out = nullptr, int wfirst = 0, int wcount = -1,
+                         const int* flag_src = nullptr, double* flag_dst = nullptr);
 // launch_risk_weights as its two stream-ordered parts: launch_risk_select (moments, t* and
 // the risk values into out, reading only q; zeroes grad_out [n_grad] for the sums to come) and
 // launch_risk_apply (weights and weighted gradient sums), with the same scratch.  Work that
@@ -208,9 +212,11 @@ void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n
 void launch_risk_select(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* out,
                         double* scratch, cudaStream_t s, double* grad_out, int n_grad,
                         const double* mom_part = nullptr, int mom_n = 0);
+// flag_src / flag_dst: the weighted pass also copies an int status flag (set by earlier
+// kernels) into a double of the results, so that one read-back carries both.
 void launch_risk_apply(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* scratch,
                        cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out, int wfirst = 0,
-                       int wcount = -1);
+                       int wcount = -1, const int* flag_src = nullptr, double* flag_dst = nullptr);
 
 // ------------------------------------------------------------------ fields
 void launch_sample_fields(int n, uint64_t seed, int64_t first, int count, const double* invlam,

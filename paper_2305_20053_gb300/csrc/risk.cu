@@ -709,10 +709,12 @@ __global__ void __launch_bounds__(256) k_risk_apply(const double* __restrict__ q
                                                     const RiskDev* __restrict__ risks, int n_risks,
                                                     const double* __restrict__ params, double* __restrict__ w,
                                                     const float* __restrict__ gq, int ldg, int dz,
-                                                    double* __restrict__ grad_out, int wlo, int whi) {
+                                                    double* __restrict__ grad_out, int wlo, int whi,
+                                                    const int* __restrict__ flag_src, double* __restrict__ flag_dst) {
   __shared__ float wsh[OUU_MAX_RISKS][APPLY_W], wsl[OUU_MAX_RISKS][APPLY_W];
   __shared__ double gsum[OUU_MAX_RISKS][128];
   pdl_wait();
+  if (flag_src && blockIdx.x == 0 && threadIdx.x == 0) *flag_dst = (double)__ldcg(flag_src);
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int i0 = min(N, (int)blockIdx.x * chunk), i1 = min(N, i0 + chunk);
   const int g = threadIdx.x >> 7, jl = threadIdx.x & 127;   // two sample parities x 128 columns
@@ -794,18 +796,20 @@ void launch_risk_select(const double* q, int N, const RiskDev* risks_dev, int n_
 }
 
 void launch_risk_apply(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* scratch,
-                       cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out, int wfirst, int wcount) {
+                       cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out, int wfirst, int wcount,
+                       const int* flag_src, double* flag_dst) {
   const int wlo = wcount < 0 ? 0 : wfirst, whi = wcount < 0 ? N : wfirst + wcount;
   const double* params = scratch;
   launch_pdl(k_risk_apply, dim3(RISK_BLOCKS), dim3(256), 0, s, q, N, risks_dev, n_risks, params, w, gq, ldg, dz,
-             grad_out, wlo, whi);
+             grad_out, wlo, whi, flag_dst ? flag_src : nullptr, flag_dst);
 }
 
 void launch_risk_weights(const double* q, int N, const RiskDev* risks_dev, int n_risks, double* w, double* out,
                          double* scratch, cudaStream_t s, const float* gq, int ldg, int dz, double* grad_out,
-                         int wfirst, int wcount) {
+                         int wfirst, int wcount, const int* flag_src, double* flag_dst) {
   launch_risk_select(q, N, risks_dev, n_risks, out, scratch, s, gq ? grad_out : nullptr, n_risks * dz);
-  launch_risk_apply(q, N, risks_dev, n_risks, w, scratch, s, gq, ldg, dz, grad_out, wfirst, wcount);
+  launch_risk_apply(q, N, risks_dev, n_risks, w, scratch, s, gq, ldg, dz, grad_out, wfirst, wcount, flag_src,
+                    flag_dst);
 }
 
 // Kernel-level entry used by the risk-weight numerics test (declared in include/ouu_kernels.h).
