@@ -90,7 +90,7 @@ def test_risk_weights_parity(case):
 
 
 def test_risk_weights_repeat_calls_agree():
-    """The block-arrival counter resets itself: a second call gives the same values."""
+    """No state is carried between calls: a second call gives the same values."""
     from paper_2305_20053_gb300 import capi
     Q = 5.0 + np.random.default_rng(3).standard_normal(4096)
     q = torch.tensor(Q, device="cuda")
