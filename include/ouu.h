@@ -93,7 +93,8 @@ typedef struct {
   float ms_adjoint;             /* batched adjoint solve */
   float ms_reduce;              /* weighted adjoint sum and G^T */
   float ms_total;               /* whole evaluation on the device */
-  float ms_project;             /* DINO: fused KL projection of the FP64 fields */
+  float ms_project;             /* DINO: fused KL projection of the FP64 fields (also measured in a
+                                   replayed evaluation, by event nodes of its graph) */
   float ms_network;             /* DINO: network forward + reverse-mode gradient */
 } ouu_eval_stats;
 

@@ -701,15 +701,24 @@ static ouu_status check_err(ouu_dino* d) {
 }
 
 // KL coordinates of `count` fields (chunked BF16 cast + tensor-core projection).
-// With mark, events ev[0] / ev[1] / ev[2] bracket the first chunk's cast and GEMM.  With
-// zstage, the projection launch also stages the controls (d_zf) from the mapped pinned buffer.
+// With mark, events ev[0] / ev[2] bracket the projection: recorded in the stream, or, while a
+// graph is captured, as event nodes of the graph (ev[2] on the side stream, forked after the
+// projection, so that the next kernel on the main stream keeps its programmatic edge), which
+// every replay records.  With zstage, the projection launch also stages the controls (d_zf)
+// from the mapped pinned buffer.
 static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi, bool mark = false,
                                  bool zstage = false) {
   // one fused pass over the FP64 fields (kl_project.cu); the bias -W mbar carries the prior mean
-  if (mark && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
+  if (mark) OUU_CUDA_TRY(cudaEventRecordWithFlags(d->ev[0], d->stream, d->capturing ? cudaEventRecordExternal : 0));
   DINO_TRY(ouu_kl_project(m, count, d->nn, d->d_wkl, d->nnp, d->rm, d->d_klbias, xi, d->d_err, d->d_klp_ctr,
                           d->num_sms, d->stream, zstage ? d->h_pin_dev : nullptr, d->d_zf, d->dz));
-  if (mark && !d->capturing) OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
+  if (mark && d->capturing) {
+    OUU_CUDA_TRY(cudaEventRecord(d->ev_fork, d->stream));
+    OUU_CUDA_TRY(cudaStreamWaitEvent(d->side, d->ev_fork, 0));
+    OUU_CUDA_TRY(cudaEventRecordWithFlags(d->ev[2], d->side, cudaEventRecordExternal));
+  } else if (mark) {
+    OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
+  }
   return OUU_OK;
 }
 
