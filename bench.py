@@ -43,7 +43,7 @@ sys.path.insert(0, ROOT)
 METRIC = "risk+gradient evals/s: MR-DINO vs batched PDE SAA, 1 GB300, <=1% rel err"
 # DRAM bytes (read + write) of one k_kl_project launch over 1024 fields at 129 x 129, from an
 # ncu capture of that kernel; a launch streams each field once, so traffic scales with N
-KL_PROJECT_DRAM_BYTES_N1024 = 144.396544e6 + 3.240448e6
+KL_PROJECT_DRAM_BYTES_N1024 = 144.419328e6 + 3.440384e6
 N_GRID, L_LAT, N_SAMPLES = 129, 10, 4096
 R_M = R_U = 200
 WIDTH = 400
