@@ -553,7 +553,7 @@ static ouu_status risk_and_grad_on(ouu_problem_t p, ouu_backend backend, ouu_din
       std::memset(stats, 0, sizeof(*stats));
       cudaEventElapsedTime(&stats->ms_total, p->ev[0], p->ev[3]);
       // the projection's marks are event nodes of the graph too
-      if (replay) cudaEventElapsedTime(&stats->ms_project, dino->ev[0], dino->ev[2]);
+      if (replay && dino->graph_marks) cudaEventElapsedTime(&stats->ms_project, dino->ev[0], dino->ev[2]);
       if (!replay) {   // the other phase marks exist only for an eagerly enqueued evaluation
         cudaEventElapsedTime(&stats->ms_state, p->ev[0], p->ev[1]);
         cudaEventElapsedTime(&stats->ms_weights, p->ev[1], p->ev[2]);

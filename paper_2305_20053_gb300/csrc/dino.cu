@@ -701,23 +701,25 @@ static ouu_status check_err(ouu_dino* d) {
 }
 
 // KL coordinates of `count` fields (chunked BF16 cast + tensor-core projection).
-// With mark, events ev[0] / ev[2] bracket the projection: recorded in the stream, or, while a
-// graph is captured, as event nodes of the graph (ev[2] on the side stream, forked after the
-// projection, so that the next kernel on the main stream keeps its programmatic edge), which
-// every replay records.  With zstage, the projection launch also stages the controls (d_zf)
-// from the mapped pinned buffer.
+// With mark, events ev[0] / ev[2] bracket the projection in an eagerly enqueued call.  With
+// graph_mark as well, while a graph is captured, they become event nodes of the graph, which
+// every replay records: ev[2] on the side stream, forked after the projection so that the
+// next kernel on the main stream keeps its programmatic edge (the caller joins the side
+// stream back before the capture ends).  With zstage, the projection launch also stages the
+// controls (d_zf) from the mapped pinned buffer.
 static ouu_status project_fields(ouu_dino* d, const double* m, int count, float* xi, bool mark = false,
-                                 bool zstage = false) {
+                                 bool zstage = false, bool graph_mark = false) {
   // one fused pass over the FP64 fields (kl_project.cu); the bias -W mbar carries the prior mean
-  if (mark) OUU_CUDA_TRY(cudaEventRecordWithFlags(d->ev[0], d->stream, d->capturing ? cudaEventRecordExternal : 0));
+  const bool eager_mark = mark && !d->capturing, node_mark = mark && graph_mark && d->capturing;
+  if (eager_mark) OUU_CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
+  if (node_mark) OUU_CUDA_TRY(cudaEventRecordWithFlags(d->ev[0], d->stream, cudaEventRecordExternal));
   DINO_TRY(ouu_kl_project(m, count, d->nn, d->d_wkl, d->nnp, d->rm, d->d_klbias, xi, d->d_err, d->d_klp_ctr,
                           d->num_sms, d->stream, zstage ? d->h_pin_dev : nullptr, d->d_zf, d->dz));
-  if (mark && d->capturing) {
+  if (eager_mark) OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
+  if (node_mark) {
     OUU_CUDA_TRY(cudaEventRecord(d->ev_fork, d->stream));
     OUU_CUDA_TRY(cudaStreamWaitEvent(d->side, d->ev_fork, 0));
     OUU_CUDA_TRY(cudaEventRecordWithFlags(d->ev[2], d->side, cudaEventRecordExternal));
-  } else if (mark) {
-    OUU_CUDA_TRY(cudaEventRecord(d->ev[2], d->stream));
   }
   return OUU_OK;
 }
@@ -904,16 +906,17 @@ extern "C" ouu_status ouu_dino_loss_grad(ouu_dino_t d, const float* xi_dev, cons
 // grad_z Q in GQe by reverse mode: seed phi + c through W3^T, GELU', ... , W0z^T.
 static ouu_status dino_network(ouu_dino* d, int N, bool want_grad);
 
-// The controls to the device and the projection of the fields into XIe.  With zstage (and the
-// pinned buffer mapped), the projection launch carries the controls over from the pinned
-// buffer instead of a copy ahead of it.
-static ouu_status dino_eval_inputs(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool zstage = false) {
+// The controls to the device and the projection of the fields into XIe.  With split (the risk
+// evaluation's two-branch form): the projection launch carries the controls over from the
+// pinned buffer (when it is mapped) instead of a copy ahead of it, and a captured graph gets
+// the projection's event nodes.
+static ouu_status dino_eval_inputs(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool split = false) {
   ++d->eval_count;   // the per-sample buffers now belong to this evaluation
   float* zh = (float*)d->h_pin;
   for (int j = 0; j < d->dz; ++j) zh[j] = (float)z_host[j];
-  zstage = zstage && d->h_pin_dev;
+  const bool zstage = split && d->h_pin_dev;
   if (!zstage) OUU_CUDA_TRY(cudaMemcpyAsync(d->d_zf, zh, (size_t)d->dz * 4, cudaMemcpyHostToDevice, d->stream));
-  DINO_TRY(project_fields(d, m_dev, N, d->XIe, true, zstage));
+  DINO_TRY(project_fields(d, m_dev, N, d->XIe, true, zstage, split));
   return OUU_OK;
 }
 
@@ -924,6 +927,7 @@ ouu_status dino_eval_core(ouu_dino* d, const double* m_dev, int N, const double*
 
 ouu_status dino_eval_forward(ouu_dino* d, const double* m_dev, int N, const double* z_host, bool* split) {
   *split = d->fused_mlp == 2 && mlp_cluster_fits(d);
+  if (d->capturing) d->graph_marks = *split;   // the captured graph holds the projection's event nodes
   if (!*split) return dino_eval_core(d, m_dev, N, z_host, true);
   DINO_TRY(dino_eval_inputs(d, m_dev, N, z_host, true));
   DINO_TRY(mlp_cluster_eval(d, N, 0, 4));

@@ -78,6 +78,7 @@ struct ouu_dino {
   // network's reverse mode (forked after the forward part, joined before the weighted sums)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool graph_marks = false;        // the captured risk graph records ev[0] / ev[2] around the projection
   cudaGraphExec_t gexec = nullptr;
   const void* gkey_p = nullptr;
   const double* gkey_m = nullptr;
