@@ -370,7 +370,10 @@ ouu_status ouu_dino_decode(ouu_dino_t d, const float* phi_dev, int n_samples, fl
 /* DINO risk evaluations in ouu_risk_and_grad are replayed from a CUDA graph that is
  * captured (on a private stream, after one eager evaluation) for each new combination
  * of (problem, m_dev, n_samples, n_risks); enable = 0 turns this off (every call then
- * enqueues its kernels eagerly and reports per-phase times in ouu_eval_stats). */
+ * enqueues its kernels eagerly and reports per-phase times in ouu_eval_stats; a replayed
+ * evaluation in network mode 2 reports ms_total and ms_project).  The controls of a call
+ * travel through the network's pinned host buffer, which the captured graph reads when it
+ * runs: calls on one network do not overlap (each synchronises before returning). */
 ouu_status ouu_dino_set_graphs(ouu_dino_t d, int enable);
 
 /* How the evaluation network with a gradient (projection output -> forward layers -> reduced
@@ -381,7 +384,9 @@ ouu_status ouu_dino_set_graphs(ouu_dino_t d, int enable);
  *           layer then run on one SM per tile, slower than mode 0 at thousands of samples;
  *   mode 2 (default): one kernel, each 128-sample tile on a cluster of 4 CTAs, each computing a quarter of
  *           every layer's columns, activations passed through L2 (width, r_U, r_M + d_Z <= 448,
- *           d_Z <= 512, r_M % 4 == 0, width % 8 == 0).
+ *           d_Z <= 512, r_M % 4 == 0, width % 8 == 0).  In ouu_risk_and_grad it runs as two
+ *           launches (forward with the reduced QoI, then reverse mode), with the risk's t*
+ *           search beside the second on another branch of the evaluation's graph.
  * A mode whose size limits the network exceeds falls back to mode 0.  ouu_batch_create with
  * autotune picks per network by timing.  Returns OUU_ERR_INVALID_ARG for another mode. */
 ouu_status ouu_dino_set_fused_network(ouu_dino_t d, int mode);

@@ -1,6 +1,8 @@
-// Risk weights over the sample average (Sec. 2.1-2.2): one CTA reduces the N
-// per-sample QoIs, finds the CVaR minimiser t* when asked, and writes the weight
-// w_i of every sample, so that grad rho = sum_i w_i grad Q_i.
+// Risk values and weights over the sample average (Sec. 2.1-2.2), in three passes: the
+// moments of the N per-sample QoIs (many CTAs; or sums a caller already has), then one CTA
+// that finds the CVaR minimiser t* when asked and computes the risk values, then the weight
+// w_i of every sample (many CTAs), with sum_i w_i grad Q_i when per-sample gradients are
+// given, so that grad rho = sum_i w_i grad Q_i.
 //   mean + kappa var:  w_i = (1 + 2 kappa (Q_i - Qbar)) / N
 //   smoothed CVaR:     w_i = s'_eps(Q_i - t) / (N (1 - beta))
 #include "ouu_internal.cuh"
