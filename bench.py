@@ -337,7 +337,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"saa-risk-grad {N_GRID}x{N_GRID} N={N_SAMPLES} d_z={L_LAT * L_LAT}",
                    "n": N_GRID, "n_samples": N_SAMPLES, "d_z": L_LAT * L_LAT, "backend": f"oracle-{args.backend}"},
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
